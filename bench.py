@@ -1,0 +1,493 @@
+#!/usr/bin/env python
+"""Benchmark of the B-spline interpolation path on GB300.
+
+One step = the whole path on one batch: prefilter + inverse real 3D FFT of a
+512^3 3-component Kolmogorov-spectrum field into quintic (order 6) B-spline
+coefficients, then locate/bin/sort 2^24 clustered particles and evaluate u
+and grad u at each of them.  Metric: particles/s (whole job over all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank holds a replica of the
+field and evaluates its own 2^24 particles: the path has no exchange step
+(weak scaling, no collective on the data path).
+
+--impl reference times the CPU FP64 oracle (numpy) on this machine's host
+cores on a bounded sample of the same workload and prints the same JSON line
+with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s for u+grad-u (quintic B-spline, 512^3), FP32 vs FP64 form, % HBM peak"
+UNIT = "particles/s"
+WORKLOAD_NAME = "throughput512"
+STAGES = ["fft_x", "fft_y", "fft_z", "bin", "scan", "scatter", "gather"]
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def workload():
+    from paper_1201_4060_gb300 import synth
+    wl = dict(synth.WORKLOADS[WORKLOAD_NAME])
+    return wl
+
+
+def config_block(wl, dtype, world):
+    return {
+        "workload": f"{wl['N']}^3 x 3-component Kolmogorov field, order-{wl['order']} (quintic) B-spline, "
+                    f"{wl['P']} clustered particles per GPU, u + grad u, {dtype} coefficients",
+        "N": wl["N"], "order": wl["order"], "particles_per_gpu": wl["P"], "coeff_dtype": dtype,
+        "particles": "clustered: 60% uniform, 40% Gaussian clumps sigma=0.1 around 64 centres",
+        "step": "prefilter+inverse real FFT, bin+counting sort, weights+stencil contraction",
+        "parallelism": f"replicas x{world} (particle shard per GPU, no collective)",
+        "l2": "no flush: inputs larger than L2 (u_hat 1.62 GB, coefficients 1.61 GB, positions 0.40 GB)",
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons in a background thread."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.samples = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = "timed region"
+        if not inside:
+            inside = [s for s in self.samples if t0 - 0.3 <= s[0] <= t1 + 0.3]
+            window = "timed region +-0.3 s (region shorter than the sampling period)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [num(s[1][1]) for s in inside if num(s[1][1]) is not None]
+        smax = [num(s[1][2]) for s in inside if num(s[1][2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in inside for i in range(4) if s[1][5 + i].lower() == "active"})
+        pw = [num(s[1][3]) for s in inside if num(s[1][3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside), "window": window,
+                "power_w_median": statistics.median(pw) if pw else None}
+
+
+# ----------------------------------------------------------------------------- algorithmic bytes
+
+def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
+    """Bytes a kernel must move at minimum (each input read once, each output written once)."""
+    H = N // 2 + 1
+    cplx = 16 if dtype == "f64" else 8
+    elem = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
+    outb = 8 if dtype == "f64" else 4
+    tb = 8 if dtype == "f64" else 4
+    spec = 3 * N * N * H * cplx
+    coef = 3 * N ** 3 * elem
+    nb = (N // 8) ** 3
+    return {
+        "fft_x": 2 * spec,                       # read u_hat, write the x-transformed spectrum
+        "fft_y": 2 * spec,                       # in place
+        "fft_z": spec + coef,                    # read spectrum, write coefficients
+        "bin": P * (24 + 12 + 4 + 3 * tb),       # positions in; key, rank, cell, t out
+        "scan": 2 * 4 * (nb + 1),
+        "scatter": P * (12 + 3 * tb) + P * (8 + 3 * tb),   # key, rank, cell, t in; sorted cell, t, index out
+        "gather": coef + P * (8 + 3 * tb) + P * 12 * outb,  # coefficients once, sorted records, u and grad out
+    }[stage]
+
+
+def kernel_source_sha(stage: str) -> str:
+    files = {"gather": ["particles.cuh"], "bin": ["particles.cu"], "scan": ["particles.cu"],
+             "scatter": ["particles.cu"], "fft_x": ["fft.cu"], "fft_y": ["fft.cu"], "fft_z": ["fft.cu"]}[stage]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1201_4060_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage: str, dtype: str, N: int, order: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    sha = kernel_source_sha(stage)
+    key = f"{stage}:{dtype}:N{N}:o{order}"
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == key and parts[1] == sha:
+                return float(parts[2])
+    return None
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def dense_field_on_gpu(F, dtype_torch, device):
+    import torch
+    N = F.N
+    uh = torch.zeros((3, N, N, N // 2 + 1), dtype=dtype_torch, device=device)
+    idx = torch.from_numpy(F.idx).to(device)
+    vals = torch.from_numpy(F.val).to(device=device, dtype=dtype_torch)
+    uh[:, idx[:, 0], idx[:, 1], idx[:, 2]] = vals
+    return uh
+
+
+def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True):
+    """Time `steps` whole-path steps with one plan of coefficient type dtype; returns (ms/step, stage dict)."""
+    import torch
+    plan = B.Plan(wl["N"], wl["order"], dtype)
+    uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
+    coef = plan.empty_coeffs()
+    P = x.shape[0]
+    u = torch.empty((P, 3), dtype=plan.out_dtype, device=device)
+    g = torch.empty((P, 3, 3), dtype=plan.out_dtype, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.coeffs(uh, coef)
+        plan.interp(coef, x, u, g)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if timed_stages:
+        plan.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stages = plan.stage_times() if timed_stages else {}
+    nonfinite = plan.status()
+    plan.set_timing(False)
+    del uh, coef, u, g
+    plan.close()
+    torch.cuda.empty_cache()
+    return ms / steps, stages, nonfinite
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    from paper_1201_4060_gb300 import _build, synth
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1201_4060_gb300 import bspline as B
+
+    wl = workload()
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    xs = synth.clustered_particles(P, seed=wl["particle_seed"] + rank)
+    x = torch.from_numpy(xs).to(device)
+
+    # ---- headline: FP32 coefficients, whole path, timed region of exactly K steps
+    plan = B.Plan(N, order, "f32")
+    uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
+    coef = plan.empty_coeffs()
+    u = torch.empty((P, 3), dtype=torch.float32, device=device)
+    g = torch.empty((P, 3, 3), dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.coeffs(uh, coef)
+        plan.interp(coef, x, u, g)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    plan.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if world > 1:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    time.sleep(0.2)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    stages = plan.stage_times()
+    nonfinite = plan.status()
+    plan.set_timing(False)
+    t_max = torch.tensor([ms_total], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_total = float(t_max.item())
+    value = world * P * args.steps / (ms_total / 1e3)
+    launches = sum(n for (_, n) in stages.values())
+
+    # ---- roofline of the dominant kernel (largest share of the timed region)
+    pk = peaks()
+    dom = max(STAGES, key=lambda s: stages[s][0])
+    dom_ms = stages[dom][0] / max(stages[dom][1], 1)
+    abytes = algorithmic_bytes(dom, N, P, "f32")
+    achieved = abytes / (dom_ms / 1e3) / 1e9
+    traffic = measured_traffic(dom, "f32", N, order)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": traffic, "algorithmic_bytes": abytes, "avg_launch_ms": dom_ms}
+    # the gather's arithmetic: Table 1 multiply-adds per particle against the FP32 FMA pipe
+    from_table1 = 6 * order ** 3 + 15 * order ** 2 + 12 * order
+    g_ms = stages["gather"][0] / max(stages["gather"][1], 1)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    fma_peak = sms * 128 * pk["sm_max_mhz"] * 1e6
+    fma_rate = P * from_table1 / (g_ms / 1e3)
+    g_bytes = algorithmic_bytes("gather", N, P, "f32")
+    gather = {"avg_launch_ms": g_ms, "achieved_gbs": g_bytes / (g_ms / 1e3) / 1e9,
+              "hbm_frac": g_bytes / (g_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+              "fma_per_particle_table1": from_table1, "fma_rate_tfma": fma_rate / 1e12,
+              "fma_peak_tfma_at_max_clock": fma_peak / 1e12, "alu_frac_at_max_clock": fma_rate / fma_peak,
+              "particles_per_s": P / (g_ms / 1e3),
+              "traffic": measured_traffic("gather", "f32", N, order)}
+    stages_ms = {s: {"total_ms": stages[s][0], "launches": stages[s][1],
+                     "share": stages[s][0] / max(sum(v[0] for v in stages.values()), 1e-30)} for s in STAGES}
+    del uh, coef, u, g
+    plan.close()
+    torch.cuda.empty_cache()
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": f"synthetic: Kolmogorov-spectrum field (seed {wl['field_seed']}), clustered particles "
+                   f"(seed {wl['particle_seed']} + rank); no dataset",
+           "config": config_block(wl, "f32", world), "roofline": roofline, "gather": gather,
+           "stages_ms": stages_ms, "gpu_launches": launches, "clocks": clocks, "nonfinite_positions": nonfinite}
+
+    # ---- other coefficient forms and the end-to-end number (rank 0 only at N = 1)
+    if world == 1 and not args.quick:
+        forms = {"f32": {"particles_per_s": value, "ms_per_step": ms_total / args.steps}}
+        ks = max(3, min(args.steps, 20))
+        ms_bf, st_bf, _ = run_form(B, wl, F, x, "bf16", ks, 2, device)
+        gb = st_bf["gather"][0] / max(st_bf["gather"][1], 1)
+        forms["bf16"] = {"particles_per_s": P / (ms_bf / 1e3), "ms_per_step": ms_bf, "gather_ms": gb,
+                         "gather_hbm_frac": algorithmic_bytes("gather", N, P, "bf16") / (gb / 1e3) / 1e9 /
+                         pk["hbm_gbs"]}
+        ms_64, st_64, _ = run_form(B, wl, F, x, "f64", 2, 1, device)
+        g64 = st_64["gather"][0] / max(st_64["gather"][1], 1)
+        forms["f64"] = {"particles_per_s": P / (ms_64 / 1e3), "ms_per_step": ms_64, "gather_ms": g64,
+                        "fft_ms": sum(st_64[s][0] / max(st_64[s][1], 1) for s in ("fft_x", "fft_y", "fft_z"))}
+        out["forms"] = forms
+        out["e2e"] = run_e2e(B, wl, F, xs, device, steps=3)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(samples=1 << 17)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(B, wl, F, xs, device, steps):
+    """Same metric through bspline_run_host: host->device copies of u_hat and positions and the
+    device->host copy of u and grad u inside each timed step (pinned host buffers)."""
+    import numpy as np
+    import torch
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    plan = B.Plan(N, order, "f32")
+    uh = torch.from_numpy(F.dense(np.complex64)).pin_memory()
+    xh = torch.from_numpy(xs).pin_memory()
+    uo = torch.empty((P, 3), dtype=torch.float32).pin_memory()
+    go = torch.empty((P, 3, 3), dtype=torch.float32).pin_memory()
+    plan.run_host(uh, xh, uo, go)
+    ts = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        plan.run_host(uh, xh, uo, go)
+        ts.append(time.perf_counter() - t)
+    plan.close()
+    t = statistics.median(ts)
+    h2d = uh.numel() * 8 + xh.numel() * 8
+    d2h = uo.numel() * 4 + go.numel() * 4
+    del uh, xh, uo, go
+    torch.cuda.empty_cache()
+    return {"value": P / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": t * 1e3, "steps": steps, "api": "bspline_run_host (pinned host buffers)"}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+
+ORACLE_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def cpu_worker(mode: str, samples: int, steps: int = 1, warmup: int = 0) -> dict:
+    """Runs in a child process with single-threaded numpy: times the oracle on a bounded sample."""
+    import numpy as np
+    from oracle import bspline_oracle as O
+    from paper_1201_4060_gb300 import synth
+    wl = workload()
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    H = N // 2 + 1
+    # coefficient build of one component at full size (the three components are identical work)
+    half = np.zeros((1, N, N, H), np.complex128)
+    half[0, F.idx[:, 0], F.idx[:, 1], F.idx[:, 2]] = F.val[0]
+    t = time.perf_counter()
+    c = O.coefficients(half, order)
+    t_coef1 = time.perf_counter() - t
+    cb = np.broadcast_to(c, (3, N, N, N))
+    x = synth.clustered_particles(P, seed=wl["particle_seed"])
+    rng = np.random.default_rng(0)
+    g_times = []
+    for i in range(warmup + steps):
+        sel = x[rng.integers(0, P, samples)]
+        t = time.perf_counter()
+        O.evaluate(cb, sel, order)
+        dt = time.perf_counter() - t
+        if i >= warmup:
+            g_times.append(dt)
+    t_g = statistics.mean(g_times)
+    t_step = 3 * t_coef1 + t_g * (P / samples)
+    return {"t_coef_one_component_s": t_coef1, "t_gather_sample_s": t_g, "gather_sample": samples,
+            "t_step_est_s": t_step, "per_step_est_s": [3 * t_coef1 + tg * (P / samples) for tg in g_times]}
+
+
+def _spawn_worker(mode, samples, steps=1, warmup=0):
+    env = dict(os.environ, **ORACLE_ENV)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", mode, "--samples", str(samples),
+           "--steps", str(steps), "--warmup", str(warmup)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle worker failed:\n{r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(samples: int) -> dict:
+    wl = workload()
+    w = _spawn_worker("baseline", samples)
+    return {"value": wl["P"] / w["t_step_est_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"numpy FP64 oracle, 1 thread: coefficient build of one of the 3 components at full "
+                      f"{wl['N']}^3 (x3) + u/grad u at {samples} of the {wl['P']} particles "
+                      f"(x{wl['P'] // samples}); {w['t_coef_one_component_s']:.2f} s + "
+                      f"{w['t_gather_sample_s']:.2f} s measured",
+            "t_step_est_s": w["t_step_est_s"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    wl = workload()
+    samples = 2048
+    w = _spawn_worker("reference", samples, steps=args.steps, warmup=args.warmup)
+    per = w["per_step_est_s"]
+    t_step = statistics.mean(per)
+    value = wl["P"] / t_step
+    sample = (f"numpy FP64 oracle, 1 thread: coefficient build of one component at full {wl['N']}^3 timed once "
+              f"({w['t_coef_one_component_s']:.2f} s, x3 per step) + per step u/grad u at {samples} random "
+              f"particles of {wl['P']} (x{wl['P'] // samples})")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (same recipe and seeds)",
+           "config": config_block(wl, "f64 (oracle)", world),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="headline only (no other forms, no e2e)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--samples", type=int, default=4096, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_worker:
+        print(json.dumps(cpu_worker(args.cpu_worker, args.samples, args.steps, args.warmup)))
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * bspline.h -- C ABI of the GB300 (sm_103a) B-spline interpolation library
+ * for pseudo-spectral fields.
+ *
+ * The method (van Hinsberg, ten Thije Boonkkamp, Toschi, Clercx, "On the
+ * efficiency and accuracy of interpolation methods for spectral codes"):
+ *   1. prefilter every Fourier mode by c(kx) c(ky) c(kz), c(k) = 1/F_D[B_D](k)
+ *      (Section 7, Eqs. B_spline_multiplication, B_spline_multiplication_3d);
+ *   2. one inverse real 3D FFT gives the B-spline coefficients u_B
+ *      (Section 7, coefficient transform);
+ *   3. evaluate the order-n tensor-product B-spline and its first derivatives
+ *      at off-grid points (Sections 3-4, Eqs. interpolation, interpolation2,
+ *      Table 1; stencil nodes by Eq. alg-int-6).
+ *
+ * Conventions shared by every entry point
+ *   - Domain [0, L)^3, default L = 2 pi, N grid points per axis.
+ *   - Field u(x) = sum_k u_hat_k exp(i (2 pi / L) k . x): u_hat holds
+ *     Fourier-series coefficients (not N^3-scaled DFT output).
+ *   - u_hat layout: half spectrum [3][N][N][N/2+1] of interleaved complex
+ *     (re, im), index (component, kx, ky, kz), signed wavenumber k stored at
+ *     index k mod N, kz >= 0 only, kz fastest.  Real-to-complex semantics:
+ *     the imaginary part of self-conjugate modes (kz = 0 or N/2 planes) is
+ *     ignored, as by any inverse real FFT.
+ *   - Coefficient layout: real [3][N][N][N], z fastest, element type of the
+ *     plan's dtype (double, float or bfloat16).
+ *   - Positions x: double [P][3], any real values; wrapped periodically.
+ *   - Outputs: out_u [P][3] and out_grad [P][3][3] with
+ *     out_grad[p][i][j] = d u_i / d x_j in physical units; element type
+ *     double for BSPLINE_F64 plans, float otherwise.
+ *   - All pointers passed to the compute calls are device pointers unless the
+ *     name says host.  The caller owns every buffer it passes; the plan owns
+ *     its tables and workspace and frees them in bspline_destroy.
+ *   - Calls are asynchronous on the plan's stream (default: the legacy
+ *     default stream).  Device-side status (non-finite input count) is read
+ *     with bspline_status after synchronising that stream.
+ *   - Every function returns 0 (BSPLINE_OK) or a negative status code and
+ *     never aborts or throws; a failed call leaves the outputs unspecified.
+ */
+#ifndef BSPLINE_H
+#define BSPLINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bspline_plan_s* bspline_plan_t;
+
+/* Coefficient storage type.  F64: FP64 everywhere.  F32: FP32 transform,
+ * FP32 coefficients, FP32 weights and accumulation.  BF16: FP32 transform,
+ * coefficients rounded to bfloat16 on store, FP32 weights and accumulation.
+ * Position-to-cell index and local offset are computed in FP64 for all. */
+typedef enum { BSPLINE_F64 = 0, BSPLINE_F32 = 1, BSPLINE_BF16 = 2 } bspline_dtype;
+
+/* Prefilter choice (Section 7): INTERP is c(k) = 1/F_D[B_D](k), which makes
+ * the interpolant reproduce the grid values; L2 is the L2-optimal
+ * c(k) = F[B](kappa) / sum_i F[B](kappa + i)^2 of Eq. B_spline_coeff. */
+typedef enum { BSPLINE_PREFILTER_INTERP = 0, BSPLINE_PREFILTER_L2 = 1 } bspline_prefilter;
+
+enum {
+    BSPLINE_OK = 0,
+    BSPLINE_ERR_INVALID_ARG = -1,       /* null/misaligned pointer, P < 0, bad flag, bad plan */
+    BSPLINE_ERR_UNSUPPORTED_N = -2,     /* N not a supported transform length */
+    BSPLINE_ERR_UNSUPPORTED_ORDER = -3, /* order outside [2, 8] */
+    BSPLINE_ERR_CUDA = -4,              /* a CUDA runtime call failed */
+    BSPLINE_ERR_NONFINITE_INPUT = -5,   /* returned by bspline_status when positions were NaN/Inf */
+    BSPLINE_ERR_TIMEOUT = -6,           /* a bounded device-side wait gave up */
+    BSPLINE_ERR_NOT_IMPLEMENTED = -7,
+    BSPLINE_ERR_OUT_OF_MEMORY = -8      /* workspace allocation failed */
+};
+
+/* Flags of bspline_interp. */
+#define BSPLINE_INTERP_NO_GRAD 0x1      /* out_grad may be NULL; only u is evaluated */
+
+/* Create a plan for an N^3 periodic grid, B-spline order `order` (the
+ * paper's N: stencil width, degree order-1), coefficient type `dtype`.
+ * N: even power of two, 8 <= N <= 1024.  order: 2..8.  L = 2 pi.
+ * Allocates device tables on the current CUDA device.  On success *out
+ * receives the plan; on failure *out is set to NULL. */
+int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype);
+
+/* Domain length L > 0 (finite). */
+int bspline_plan_set_length(bspline_plan_t plan, double L);
+
+/* Prefilter choice (default BSPLINE_PREFILTER_INTERP). */
+int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind);
+
+/* Bind the plan to a cudaStream_t (passed as void*; NULL = legacy stream). */
+int bspline_plan_set_stream(bspline_plan_t plan, void* stream);
+
+/* Size in bytes of the coefficient buffer (3 N^3 elements of the dtype). */
+int bspline_coeffs_bytes(bspline_plan_t plan, size_t* bytes);
+
+/* Size in bytes of the u_hat buffer (3 N^2 (N/2+1) complex of the dtype's
+ * transform type: complex double for F64, complex float otherwise). */
+int bspline_uhat_bytes(bspline_plan_t plan, size_t* bytes);
+
+/* Steps 1-2: coeffs = inverse real FFT of c(kx)c(ky)c(kz) u_hat
+ * (Section 7, Eqs. B_spline_multiplication_3d and the coefficient transform).
+ * u_hat: device, layout above, complex double (F64 plan) or complex float
+ * (F32/BF16 plans), 16-byte aligned, not modified.  coeffs: device,
+ * bspline_coeffs_bytes() bytes, 16-byte aligned; must not alias u_hat. */
+int bspline_coeffs(bspline_plan_t plan, const void* u_hat, void* coeffs);
+
+/* Step 3: evaluate u and grad u at P positions (Sections 3-4, Table 1).
+ * coeffs: device, as written by bspline_coeffs.  x: device double [P][3].
+ * out_u: device [P][3]; out_grad: device [P][3][3] or NULL with
+ * BSPLINE_INTERP_NO_GRAD.  P = 0 is a no-op.  Positions that are NaN or Inf
+ * give NaN outputs and are counted in the plan's status word.  Uses plan
+ * workspace sized for P (grown on demand; growth synchronises the device). */
+int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
+                   void* out_u, void* out_grad, int flags);
+
+/* Adjoint of bspline_interp and bspline_coeffs: spreads cotangents g_u [P][3]
+ * and g_grad [P][3][3] (NULL = zero) onto g_coeffs (accumulated, [3][N][N][N]
+ * of the output type), optionally continues through the transposed transform
+ * and prefilter into g_u_hat (half spectrum, overwritten; NULL = skip) and
+ * writes position gradients g_x [P][3] (NULL = skip). */
+int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
+                           const void* g_u, const void* g_grad, void* g_coeffs, void* g_u_hat,
+                           double* g_x);
+
+/* Device workspace bspline_interp needs for P positions. */
+int bspline_workspace_bytes(bspline_plan_t plan, int64_t P, size_t* bytes);
+
+/* Synchronise the plan's stream and report the device status word of the
+ * last bspline_interp call: BSPLINE_OK, or BSPLINE_ERR_NONFINITE_INPUT with
+ * the count of non-finite positions in *nonfinite (may be NULL). */
+int bspline_status(bspline_plan_t plan, int64_t* nonfinite);
+
+/* Whole path with HOST buffers: copies u_hat_host and x_host to plan-owned
+ * device buffers, runs bspline_coeffs and bspline_interp, copies the results
+ * to u_host and grad_host (grad_host may be NULL), and synchronises the
+ * plan's stream.  Host buffers should be page-locked for full copy speed. */
+int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P,
+                     void* u_host, void* grad_host);
+
+/* Free the plan, its tables and workspace.  NULL is accepted. */
+int bspline_destroy(bspline_plan_t plan);
+
+/* Static string for a status code. */
+const char* bspline_status_string(int status);
+
+/* Library version string. */
+const char* bspline_version(void);
+
+/* Per-kernel device timing, for profiling.  When enabled, every kernel the
+ * plan launches is bracketed by CUDA events recorded on the plan's stream;
+ * bspline_stage_times synchronises the stream and adds the elapsed times
+ * (milliseconds) and launch counts of all calls since the last reset into
+ * ms[i] and launches[i], i < BSPLINE_NSTAGES (either pointer may be NULL),
+ * then clears the record.  Disabled by default; enabling or disabling clears
+ * the record.  The stage index identifies the kernel: */
+enum {
+    BSPLINE_STAGE_FFT_X = 0,    /* prefilter + c2c along kx */
+    BSPLINE_STAGE_FFT_Y = 1,    /* c2c along ky */
+    BSPLINE_STAGE_FFT_Z = 2,    /* c2r along kz, store coefficients */
+    BSPLINE_STAGE_BIN = 3,      /* locate + brick histogram */
+    BSPLINE_STAGE_SCAN = 4,     /* brick offsets */
+    BSPLINE_STAGE_SCATTER = 5,  /* counting-sort scatter */
+    BSPLINE_STAGE_GATHER = 6,   /* weights + stencil contraction */
+    BSPLINE_NSTAGES = 7
+};
+int bspline_plan_set_timing(bspline_plan_t plan, int enable);
+int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSPLINE_H */

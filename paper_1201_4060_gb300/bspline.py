@@ -1,0 +1,291 @@
+"""Python binding of libbspline.so (the C ABI in include/bspline.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Functions named like the ABI take raw integers/pointers; the Plan
+class accepts torch tensors (device memory and streams come from PyTorch) and
+passes their data pointers and the current stream to the ABI.  There is no
+fallback: if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+from . import _build
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_UNSUPPORTED_N = -2
+ERR_UNSUPPORTED_ORDER = -3
+ERR_CUDA = -4
+ERR_NONFINITE_INPUT = -5
+ERR_TIMEOUT = -6
+ERR_NOT_IMPLEMENTED = -7
+ERR_OUT_OF_MEMORY = -8
+
+F64, F32, BF16 = 0, 1, 2
+PREFILTER_INTERP, PREFILTER_L2 = 0, 1
+INTERP_NO_GRAD = 0x1
+
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
+
+_lib = None
+
+
+class BSplineError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+def _load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1201_4060_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "bspline_plan": (i32, [ctypes.POINTER(vp), i32, i32, i32]),
+        "bspline_plan_set_length": (i32, [vp, ctypes.c_double]),
+        "bspline_plan_set_prefilter": (i32, [vp, i32]),
+        "bspline_plan_set_stream": (i32, [vp, vp]),
+        "bspline_coeffs_bytes": (i32, [vp, ctypes.POINTER(sz)]),
+        "bspline_uhat_bytes": (i32, [vp, ctypes.POINTER(sz)]),
+        "bspline_coeffs": (i32, [vp, vp, vp]),
+        "bspline_interp": (i32, [vp, vp, vp, i64, vp, vp, i32]),
+        "bspline_spread_adjoint": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "bspline_workspace_bytes": (i32, [vp, i64, ctypes.POINTER(sz)]),
+        "bspline_status": (i32, [vp, ctypes.POINTER(i64)]),
+        "bspline_run_host": (i32, [vp, vp, vp, i64, vp, vp]),
+        "bspline_destroy": (i32, [vp]),
+        "bspline_status_string": (ctypes.c_char_p, [i32]),
+        "bspline_version": (ctypes.c_char_p, []),
+        "bspline_plan_set_timing": (i32, [vp, i32]),
+        "bspline_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib() -> ctypes.CDLL:
+    return _load()
+
+
+def status_string(code: int) -> str:
+    return _load().bspline_status_string(code).decode()
+
+
+def version() -> str:
+    return _load().bspline_version().decode()
+
+
+def _check(code: int, where: str) -> None:
+    if code != OK:
+        raise BSplineError(code, where)
+
+
+# ---- ABI-named thin wrappers (raw pointers / ints) --------------------------------
+
+def bspline_plan(N: int, order: int, dtype: int) -> tuple[int, int]:
+    h = ctypes.c_void_p()
+    rc = _load().bspline_plan(ctypes.byref(h), N, order, dtype)
+    return rc, (h.value or 0)
+
+
+def bspline_plan_set_length(plan: int, L: float) -> int:
+    return _load().bspline_plan_set_length(plan, L)
+
+
+def bspline_plan_set_prefilter(plan: int, kind: int) -> int:
+    return _load().bspline_plan_set_prefilter(plan, kind)
+
+
+def bspline_plan_set_stream(plan: int, stream: int) -> int:
+    return _load().bspline_plan_set_stream(plan, stream)
+
+
+def bspline_coeffs(plan: int, u_hat_ptr: int, coeffs_ptr: int) -> int:
+    return _load().bspline_coeffs(plan, u_hat_ptr, coeffs_ptr)
+
+
+def bspline_interp(plan: int, coeffs_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int, flags: int) -> int:
+    return _load().bspline_interp(plan, coeffs_ptr, x_ptr, P, u_ptr, grad_ptr, flags)
+
+
+def bspline_spread_adjoint(plan, coeffs_ptr, x_ptr, P, gu_ptr, ggrad_ptr, gcoef_ptr, guhat_ptr, gx_ptr) -> int:
+    return _load().bspline_spread_adjoint(plan, coeffs_ptr, x_ptr, P, gu_ptr, ggrad_ptr, gcoef_ptr, guhat_ptr, gx_ptr)
+
+
+def bspline_workspace_bytes(plan: int, P: int) -> tuple[int, int]:
+    b = ctypes.c_size_t()
+    rc = _load().bspline_workspace_bytes(plan, P, ctypes.byref(b))
+    return rc, b.value
+
+
+def bspline_coeffs_bytes(plan: int) -> tuple[int, int]:
+    b = ctypes.c_size_t()
+    rc = _load().bspline_coeffs_bytes(plan, ctypes.byref(b))
+    return rc, b.value
+
+
+def bspline_uhat_bytes(plan: int) -> tuple[int, int]:
+    b = ctypes.c_size_t()
+    rc = _load().bspline_uhat_bytes(plan, ctypes.byref(b))
+    return rc, b.value
+
+
+def bspline_status(plan: int) -> tuple[int, int]:
+    n = ctypes.c_int64()
+    rc = _load().bspline_status(plan, ctypes.byref(n))
+    return rc, n.value
+
+
+def bspline_run_host(plan: int, uhat_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int) -> int:
+    return _load().bspline_run_host(plan, uhat_ptr, x_ptr, P, u_ptr, grad_ptr)
+
+
+def bspline_destroy(plan: int) -> int:
+    return _load().bspline_destroy(plan)
+
+
+def bspline_status_string(code: int) -> str:
+    return status_string(code)
+
+
+NSTAGES = 7
+STAGES = ["fft_x", "fft_y", "fft_z", "bin", "scan", "scatter", "gather"]
+
+
+def bspline_plan_set_timing(plan: int, enable: int) -> int:
+    return _load().bspline_plan_set_timing(plan, enable)
+
+
+def bspline_stage_times(plan: int) -> tuple[int, list[float], list[int]]:
+    ms = (ctypes.c_double * NSTAGES)()
+    n = (ctypes.c_int64 * NSTAGES)()
+    rc = _load().bspline_stage_times(plan, ms, n)
+    return rc, list(ms), list(n)
+
+
+# ---- torch-facing plan -------------------------------------------------------------
+
+class Plan:
+    """A plan for an N^3 periodic grid, B-spline order `order`, coefficient type `dtype`.
+
+    u_hat: complex half spectrum [3, N, N, N//2+1] (complex128 for "f64", complex64 otherwise)
+    coefficients: [3, N, N, N] of float64 / float32 / bfloat16
+    positions: float64 [P, 3]; outputs u [P, 3], grad [P, 3, 3] (float64 for "f64", float32 otherwise)
+    """
+
+    def __init__(self, N: int, order: int, dtype: str = "f32", L: float = 2.0 * math.pi,
+                 prefilter: str = "interp"):
+        import torch  # noqa: F401  (device memory and streams)
+        self.N, self.order, self.dtype = int(N), int(order), dtype
+        rc, h = bspline_plan(self.N, self.order, DTYPES[dtype])
+        _check(rc, "bspline_plan")
+        self.handle = h
+        self.L = float(L)
+        if L != 2.0 * math.pi:
+            _check(bspline_plan_set_length(h, self.L), "bspline_plan_set_length")
+        if prefilter != "interp":
+            _check(bspline_plan_set_prefilter(h, PREFILTER_L2), "bspline_plan_set_prefilter")
+
+    def close(self) -> None:
+        if getattr(self, "handle", 0):
+            bspline_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # dtypes
+    @property
+    def uhat_dtype(self):
+        import torch
+        return torch.complex128 if self.dtype == "f64" else torch.complex64
+
+    @property
+    def coef_dtype(self):
+        import torch
+        return {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[self.dtype]
+
+    @property
+    def out_dtype(self):
+        import torch
+        return torch.float64 if self.dtype == "f64" else torch.float32
+
+    def _stream(self, stream=None) -> None:
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(bspline_plan_set_stream(self.handle, s.cuda_stream), "bspline_plan_set_stream")
+
+    def empty_coeffs(self):
+        import torch
+        return torch.empty((3, self.N, self.N, self.N), dtype=self.coef_dtype, device="cuda")
+
+    def coeffs(self, u_hat, out=None, stream=None):
+        import torch
+        N = self.N
+        if u_hat.shape != (3, N, N, N // 2 + 1) or u_hat.dtype != self.uhat_dtype or not u_hat.is_cuda \
+                or not u_hat.is_contiguous():
+            raise ValueError(f"u_hat must be contiguous CUDA {self.uhat_dtype} of shape {(3, N, N, N // 2 + 1)}")
+        if out is None:
+            out = self.empty_coeffs()
+        if out.shape != (3, N, N, N) or out.dtype != self.coef_dtype or not out.is_contiguous():
+            raise ValueError("bad coefficient buffer")
+        self._stream(stream)
+        _check(bspline_coeffs(self.handle, u_hat.data_ptr(), out.data_ptr()), "bspline_coeffs")
+        return out
+
+    def interp(self, coef, x, out_u=None, out_grad=None, grad: bool = True, stream=None):
+        import torch
+        if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
+        P = x.shape[0]
+        if out_u is None:
+            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=x.device)
+        if grad and out_grad is None:
+            out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=x.device)
+        self._stream(stream)
+        rc = bspline_interp(self.handle, coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
+                            out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
+        _check(rc, "bspline_interp")
+        return (out_u, out_grad) if grad else out_u
+
+    def status(self) -> int:
+        rc, n = bspline_status(self.handle)
+        if rc not in (OK, ERR_NONFINITE_INPUT):
+            raise BSplineError(rc, "bspline_status")
+        return n
+
+    def set_timing(self, enable: bool) -> None:
+        _check(bspline_plan_set_timing(self.handle, 1 if enable else 0), "bspline_plan_set_timing")
+
+    def stage_times(self) -> dict:
+        """{stage: (total ms, launches)} since the last call; synchronises the plan's stream."""
+        rc, ms, n = bspline_stage_times(self.handle)
+        _check(rc, "bspline_stage_times")
+        return {STAGES[i]: (ms[i], n[i]) for i in range(NSTAGES)}
+
+    def workspace_bytes(self, P: int) -> int:
+        rc, b = bspline_workspace_bytes(self.handle, P)
+        _check(rc, "bspline_workspace_bytes")
+        return b
+
+    def run_host(self, u_hat_host, x_host, u_host, grad_host=None, stream=None):
+        """Whole path on host (ideally pinned) tensors; copies happen inside the library call."""
+        self._stream(stream)
+        rc = bspline_run_host(self.handle, u_hat_host.data_ptr(), x_host.data_ptr(), x_host.shape[0],
+                              u_host.data_ptr(), grad_host.data_ptr() if grad_host is not None else 0)
+        _check(rc, "bspline_run_host")

@@ -1,0 +1,449 @@
+// C ABI of the library: plan life cycle, argument checks, host-side tables.
+//
+// Tables are computed on the host in FP64 when a plan is made:
+//   * node values B_(n)(d) of the centred B-spline by the Cox-de Boor
+//     recurrence of the cardinal B-spline M_n (B_(n)(y) = M_n(y + n/2));
+//   * prefilter c(k) = 1 / sum_d B_(n)(d) cos(2 pi k d / N) (Section 7,
+//     Eq. B_spline_multiplication: F_D[B_D] is real because B is even), or
+//     the L2-optimal c(k) = sinc(kappa)^n / sum_d B_(2n)(d) cos(2 pi kappa d)
+//     (Eq. B_spline_coeff; its alias sum of sinc^(2n) is the cosine series of
+//     the node values of B_(2n) by Poisson summation);
+//   * twiddles exp(+2 pi i m / N) with quadrant reduction of the angle.
+// The FP64 values are rounded to FP32 once for the FP32/BF16 plans.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace bs {
+
+int set_cuda_error(cudaError_t e) {
+    if (e == cudaSuccess) return BSPLINE_OK;
+    if (e == cudaErrorMemoryAllocation) return BSPLINE_ERR_OUT_OF_MEMORY;
+    return BSPLINE_ERR_CUDA;
+}
+
+int DeviceBuffer::grow(size_t need) {
+    if (need <= bytes && ptr) return BSPLINE_OK;
+    release();
+    if (need == 0) return BSPLINE_OK;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return set_cuda_error(e);
+    }
+    bytes = need;
+    return BSPLINE_OK;
+}
+
+static cudaEvent_t take_event(bspline_plan_s* p) {
+    if (!p->free_events.empty()) {
+        cudaEvent_t e = p->free_events.back();
+        p->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+StageTimer::StageTimer(bspline_plan_s* plan, int s) : p(plan), stage(s) {
+    if (!p->timing) return;
+    start = take_event(p);
+    if (start) cudaEventRecord(start, p->stream);
+}
+
+StageTimer::~StageTimer() {
+    if (!p->timing || !start) return;
+    cudaEvent_t stop = take_event(p);
+    if (!stop) {
+        p->free_events.push_back(start);
+        return;
+    }
+    cudaEventRecord(stop, p->stream);
+    p->pending.push_back(PendingTiming{stage, start, stop});
+}
+
+void DeviceBuffer::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+// Cardinal B-spline of order k (support [0, k)) by the Cox-de Boor recurrence.
+double cardinal(int k, double x) {
+    if (k == 1) return (x >= 0.0 && x < 1.0) ? 1.0 : 0.0;
+    return (x * cardinal(k - 1, x) + (k - x) * cardinal(k - 1, x - 1.0)) / (k - 1);
+}
+
+// Node values B_(n)(d), d = -h..h with h = n/2 + 1 (zero outside the support).
+std::vector<double> node_values(int n) {
+    const int h = n / 2 + 1;
+    std::vector<double> b(2 * h + 1);
+    for (int d = -h; d <= h; ++d) b[d + h] = cardinal(n, d + 0.5 * n);
+    return b;
+}
+
+// exp(2 pi i m / N) for N divisible by 4, angle reduced to the first octant.
+void twiddle(int m, int N, double* re, double* im) {
+    m = ((m % N) + N) % N;
+    const int q = (4 * m) / N;
+    const int r = m - q * (N / 4);
+    double c, s;
+    if (8 * r <= N) {
+        c = std::cos(2.0 * kPi * r / N);
+        s = std::sin(2.0 * kPi * r / N);
+    } else {
+        const int rr = N / 4 - r;
+        c = std::sin(2.0 * kPi * rr / N);
+        s = std::cos(2.0 * kPi * rr / N);
+    }
+    switch (q) {
+        case 0: *re = c; *im = s; break;
+        case 1: *re = -s; *im = c; break;
+        case 2: *re = -c; *im = -s; break;
+        default: *re = s; *im = -c; break;
+    }
+}
+
+int upload_prefilter(bspline_plan_s* p) {
+    const int N = p->N, n = p->order;
+    const std::vector<double> b = node_values(n);
+    const std::vector<double> b2 = node_values(2 * n);
+    const int h = n / 2 + 1, h2 = n + 1;
+    std::vector<double> c(N);
+    std::vector<float> cf(N);
+    for (int k = 0; k < N; ++k) {
+        const int ks = (k < N / 2) ? k : k - N;
+        double v;
+        if (p->prefilter == BSPLINE_PREFILTER_INTERP) {
+            // F_D[B_D](k) = sum_d B(d) cos(2 pi k d / N), phase k d reduced mod N exactly
+            double s = 0.0;
+            for (int d = -h; d <= h; ++d) {
+                if (b[d + h] == 0.0) continue;
+                double re, im;
+                twiddle((int)(((long long)k * d) % N), N, &re, &im);
+                s += b[d + h] * re;
+            }
+            v = 1.0 / s;
+        } else {
+            const double x = kPi * ks / N;
+            const double sinc = (ks == 0) ? 1.0 : std::sin(x) / x;
+            double s = 0.0;
+            for (int d = -h2; d <= h2; ++d) {
+                if (b2[d + h2] == 0.0) continue;
+                double re, im;
+                twiddle((int)(((long long)k * d) % N), N, &re, &im);
+                s += b2[d + h2] * re;
+            }
+            v = std::pow(sinc, n) / s;
+        }
+        c[k] = v;
+        cf[k] = (float)v;
+    }
+    cudaError_t e = cudaMemcpy(p->d_c64, c.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_c32, cf.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    return set_cuda_error(e);
+}
+
+int upload_twiddles(bspline_plan_s* p) {
+    const int N = p->N;
+    std::vector<double2> t(N);
+    std::vector<float2> tf(N);
+    for (int m = 0; m < N; ++m) {
+        double re, im;
+        twiddle(m, N, &re, &im);
+        t[m] = make_double2(re, im);
+        tf[m] = make_float2((float)re, (float)im);
+    }
+    cudaError_t e = cudaMemcpy(p->d_tw64, t.data(), sizeof(double2) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw32, tf.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+    return set_cuda_error(e);
+}
+
+bool valid_plan(bspline_plan_t p) { return p != nullptr && p->N > 0; }
+
+bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; cudaGetLastError(); return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) { ok = false; cudaGetLastError(); }
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (ok && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_bytes(int dtype) {
+    return dtype == BSPLINE_F64 ? 8 : (dtype == BSPLINE_F32 ? 4 : 2);
+}
+
+size_t out_bytes(int dtype) { return dtype == BSPLINE_F64 ? 8 : 4; }
+
+size_t uhat_bytes_of(const bspline_plan_s* p) {
+    return (p->dtype == BSPLINE_F64 ? 16 : 8) * 3 * (size_t)p->N * p->N * (p->N / 2 + 1);
+}
+
+size_t coef_bytes_of(const bspline_plan_s* p) { return elem_bytes(p->dtype) * 3 * (size_t)p->N * p->N * p->N; }
+
+void clear_timing(bspline_plan_s* p) {
+    for (auto& t : p->pending) {
+        p->free_events.push_back(t.start);
+        p->free_events.push_back(t.stop);
+    }
+    p->pending.clear();
+}
+
+void free_plan(bspline_plan_s* p) {
+    clear_timing(p);
+    for (cudaEvent_t e : p->free_events) cudaEventDestroy(e);
+    p->free_events.clear();
+    if (p->d_c64) cudaFree(p->d_c64);
+    if (p->d_c32) cudaFree(p->d_c32);
+    if (p->d_tw64) cudaFree(p->d_tw64);
+    if (p->d_tw32) cudaFree(p->d_tw32);
+    if (p->d_status) cudaFree(p->d_status);
+    p->work.release();
+    p->pws.release();
+    p->host_uhat.release();
+    p->host_coef.release();
+    p->host_x.release();
+    p->host_u.release();
+    p->host_grad.release();
+    p->N = 0;
+    delete p;
+}
+
+}  // namespace
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype) {
+    if (!out) return BSPLINE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (dtype != BSPLINE_F64 && dtype != BSPLINE_F32 && dtype != BSPLINE_BF16) return BSPLINE_ERR_INVALID_ARG;
+    if (N < 8 || N > 1024 || (N & (N - 1)) != 0) return BSPLINE_ERR_UNSUPPORTED_N;
+    if (order < 2 || order > 8) return BSPLINE_ERR_UNSUPPORTED_ORDER;
+    bspline_plan_s* p = new (std::nothrow) bspline_plan_s();
+    if (!p) return BSPLINE_ERR_OUT_OF_MEMORY;
+    p->N = N;
+    p->order = order;
+    p->dtype = dtype;
+    p->L = 2.0 * kPi;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_c64, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_c32, sizeof(float) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw64, sizeof(double2) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw32, sizeof(float2) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned long long) * 2);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return set_cuda_error(e);
+    }
+    int rc = upload_prefilter(p);
+    if (!rc) rc = upload_twiddles(p);
+    if (rc) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return BSPLINE_OK;
+}
+
+int bspline_plan_set_length(bspline_plan_t plan, double L) {
+    if (!valid_plan(plan) || !(L > 0.0) || !std::isfinite(L)) return BSPLINE_ERR_INVALID_ARG;
+    plan->L = L;
+    return BSPLINE_OK;
+}
+
+int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (kind != BSPLINE_PREFILTER_INTERP && kind != BSPLINE_PREFILTER_L2) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    plan->prefilter = kind;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    return upload_prefilter(plan);
+}
+
+int bspline_plan_set_stream(bspline_plan_t plan, void* stream) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    plan->stream = (cudaStream_t)stream;
+    return BSPLINE_OK;
+}
+
+int bspline_coeffs_bytes(bspline_plan_t plan, size_t* bytes) {
+    if (!valid_plan(plan) || !bytes) return BSPLINE_ERR_INVALID_ARG;
+    *bytes = coef_bytes_of(plan);
+    return BSPLINE_OK;
+}
+
+int bspline_uhat_bytes(bspline_plan_t plan, size_t* bytes) {
+    if (!valid_plan(plan) || !bytes) return BSPLINE_ERR_INVALID_ARG;
+    *bytes = uhat_bytes_of(plan);
+    return BSPLINE_OK;
+}
+
+int bspline_coeffs(bspline_plan_t plan, const void* u_hat, void* coeffs) {
+    if (!valid_plan(plan) || !u_hat || !coeffs) return BSPLINE_ERR_INVALID_ARG;
+    if (!aligned(u_hat, 16) || !aligned(coeffs, 16)) return BSPLINE_ERR_INVALID_ARG;
+    const char* a = (const char*)u_hat;
+    const char* b = (const char*)coeffs;
+    if (a < b + coef_bytes_of(plan) && b < a + uhat_bytes_of(plan)) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    return launch_coeffs(plan, u_hat, coeffs);
+}
+
+int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, void* out_u,
+                   void* out_grad, int flags) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (flags & ~BSPLINE_INTERP_NO_GRAD) return BSPLINE_ERR_INVALID_ARG;
+    if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
+    if (P == 0) return BSPLINE_OK;
+    if (!coeffs || !x || !out_u) return BSPLINE_ERR_INVALID_ARG;
+    if (!(flags & BSPLINE_INTERP_NO_GRAD) && !out_grad) return BSPLINE_ERR_INVALID_ARG;
+    const size_t ob = out_bytes(plan->dtype);
+    if (!aligned(coeffs, 16) || !aligned(x, 8) || !aligned(out_u, ob) || (out_grad && !aligned(out_grad, ob)))
+        return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    return launch_interp(plan, coeffs, x, P, out_u, out_grad, flags);
+}
+
+int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, const void* g_u,
+                           const void* g_grad, void* g_coeffs, void* g_u_hat, double* g_x) {
+    (void)coeffs; (void)x; (void)g_u; (void)g_grad; (void)g_coeffs; (void)g_u_hat; (void)g_x;
+    if (!valid_plan(plan) || P < 0) return BSPLINE_ERR_INVALID_ARG;
+    return BSPLINE_ERR_NOT_IMPLEMENTED;
+}
+
+int bspline_workspace_bytes(bspline_plan_t plan, int64_t P, size_t* bytes) {
+    if (!valid_plan(plan) || !bytes || P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
+    *bytes = interp_workspace_bytes(plan, P);
+    return BSPLINE_OK;
+}
+
+int bspline_status(bspline_plan_t plan, int64_t* nonfinite) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h, plan->d_status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (nonfinite) *nonfinite = (int64_t)h[0];
+    return h[0] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
+}
+
+int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P, void* u_host,
+                     void* grad_host) {
+    if (!valid_plan(plan) || !u_hat_host || !u_host || (P > 0 && !x_host)) return BSPLINE_ERR_INVALID_ARG;
+    if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    const size_t ob = out_bytes(plan->dtype);
+    int rc;
+    if ((rc = plan->host_uhat.grow(uhat_bytes_of(plan)))) return rc;
+    if ((rc = plan->host_coef.grow(coef_bytes_of(plan)))) return rc;
+    if ((rc = plan->host_x.grow(sizeof(double) * 3 * (size_t)(P ? P : 1)))) return rc;
+    if ((rc = plan->host_u.grow(ob * 3 * (size_t)(P ? P : 1)))) return rc;
+    if ((rc = plan->host_grad.grow(ob * 9 * (size_t)(P ? P : 1)))) return rc;
+    cudaStream_t st = plan->stream;
+    cudaError_t e = cudaMemcpyAsync(plan->host_uhat.ptr, u_hat_host, uhat_bytes_of(plan), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && P)
+        e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if ((rc = launch_coeffs(plan, plan->host_uhat.ptr, plan->host_coef.ptr))) return rc;
+    if (P) {
+        const int flags = grad_host ? 0 : BSPLINE_INTERP_NO_GRAD;
+        if ((rc = launch_interp(plan, plan->host_coef.ptr, (const double*)plan->host_x.ptr, P, plan->host_u.ptr,
+                                plan->host_grad.ptr, flags)))
+            return rc;
+        e = cudaMemcpyAsync(u_host, plan->host_u.ptr, ob * 3 * P, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && grad_host)
+            e = cudaMemcpyAsync(grad_host, plan->host_grad.ptr, ob * 9 * P, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return set_cuda_error(cudaStreamSynchronize(st));
+}
+
+int bspline_destroy(bspline_plan_t plan) {
+    if (!plan) return BSPLINE_OK;
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(plan->device);
+        cudaStreamSynchronize(plan->stream);
+        free_plan(plan);
+    }
+    return BSPLINE_OK;
+}
+
+const char* bspline_status_string(int status) {
+    switch (status) {
+        case BSPLINE_OK: return "ok";
+        case BSPLINE_ERR_INVALID_ARG: return "invalid argument";
+        case BSPLINE_ERR_UNSUPPORTED_N: return "unsupported grid size N";
+        case BSPLINE_ERR_UNSUPPORTED_ORDER: return "unsupported B-spline order";
+        case BSPLINE_ERR_CUDA: return "CUDA runtime error";
+        case BSPLINE_ERR_NONFINITE_INPUT: return "non-finite positions";
+        case BSPLINE_ERR_TIMEOUT: return "device wait timed out";
+        case BSPLINE_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case BSPLINE_ERR_OUT_OF_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+const char* bspline_version(void) { return "bspline-gb300 0.1.0"; }
+
+int bspline_plan_set_timing(bspline_plan_t plan, int enable) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    clear_timing(plan);
+    plan->timing = enable != 0;
+    return set_cuda_error(e);
+}
+
+int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    for (auto& t : plan->pending) {
+        float dt = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&dt, t.start, t.stop);
+        if (t.stage >= 0 && t.stage < BSPLINE_NSTAGES) {
+            if (ms) ms[t.stage] += dt;
+            if (launches) launches[t.stage] += 1;
+        }
+    }
+    clear_timing(plan);
+    return set_cuda_error(e);
+}
+
+}  // extern "C"

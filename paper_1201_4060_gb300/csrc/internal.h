@@ -1,0 +1,86 @@
+// Internal declarations of the B-spline interpolation library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "../../include/bspline.h"
+
+namespace bs {
+
+// Cells per brick edge: particles are binned by the brick that holds the first
+// node of their stencil, and one CTA stages one brick (plus the order-1 halo)
+// of coefficients in shared memory.
+constexpr int kBrick = 8;
+
+struct PendingTiming {
+    int stage;
+    cudaEvent_t start, stop;
+};
+
+struct DeviceBuffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    int grow(size_t need);      // cudaMalloc on first use / growth (synchronises)
+    void release();
+};
+
+}  // namespace bs
+
+struct bspline_plan_s {
+    int N = 0;
+    int order = 0;
+    int dtype = 0;
+    int prefilter = BSPLINE_PREFILTER_INTERP;
+    double L = 0.0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    // Prefilter c(k), k = 0..N-1 (index k <-> signed wavenumber k mod N), in
+    // FP64 and rounded to FP32; twiddles exp(+2 pi i m / N), m = 0..N-1.
+    double* d_c64 = nullptr;
+    float* d_c32 = nullptr;
+    double2* d_tw64 = nullptr;
+    float2* d_tw32 = nullptr;
+
+    // Transform workspace: complex [3][N][N][N/2+1].
+    bs::DeviceBuffer work;
+    // Particle workspace (binning, sort, sorted particle records).
+    bs::DeviceBuffer pws;
+    // Device status word: [0] = count of non-finite positions of the last interp.
+    unsigned long long* d_status = nullptr;
+    // Buffers of bspline_run_host.
+    bs::DeviceBuffer host_uhat, host_coef, host_x, host_u, host_grad;
+    // Per-kernel timing (bspline_plan_set_timing): event pairs recorded on the
+    // plan's stream around each launch, resolved by bspline_stage_times.
+    bool timing = false;
+    std::vector<bs::PendingTiming> pending;
+    std::vector<cudaEvent_t> free_events;
+};
+
+namespace bs {
+
+int set_cuda_error(cudaError_t e);
+
+// Bracket a kernel launch with timing events when the plan's timing is on.
+struct StageTimer {
+    bspline_plan_s* p;
+    int stage;
+    cudaEvent_t start = nullptr;
+    StageTimer(bspline_plan_s* plan, int s);
+    ~StageTimer();
+};
+
+// Transform: u_hat -> coefficients (prefilter fused into the first pass).
+int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs);
+
+// Particles: bin, sort and evaluate u and grad u.
+size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P);
+int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u,
+                  void* out_grad, int flags);
+
+}  // namespace bs

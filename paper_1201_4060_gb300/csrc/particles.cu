@@ -1,0 +1,202 @@
+// Particle side of the path: locate, bin/sort, and evaluate u and grad u.
+//
+// Locate (Eq. alg-int-6): s = x N / L in FP64; the stencil nodes are
+// floor(s - n/2) + j, j = 1..n; the local variable is t = (s - n/2) - floor(s - n/2).
+// The first node (the "anchor") picks a brick of kBrick^3 cells; particles are
+// counting-sorted by brick so that one CTA stages the brick's coefficients
+// (plus the n-1 halo) in shared memory once and evaluates all of its particles.
+//
+// Weights: per axis, the n node weights B(t + n/2 - j) and their derivatives
+// come from the Cox-de Boor recurrence of the cardinal B-spline
+// (M_k(x) = (x M_{k-1}(x) + (k - x) M_{k-1}(x - 1)) / (k - 1)), in registers.
+// They equal the columns of M x_bar and M^(1) x_bar of Section 4.
+//
+// Contraction (Table 1, reordered to contract the contiguous z axis first):
+// per component, Z0 = sum_z w_z a, Z1 = sum_z w'_z a (2 n^3), then
+// Y00 = sum_y w_y Z0, Y10 = sum_y w'_y Z0, Y01 = sum_y w_y Z1 (3 n^2), then
+// u = sum_x w_x Y00, du/dx = sum_x w'_x Y00, du/dy = sum_x w_x Y10,
+// du/dz = sum_x w_x Y01 (4 n), derivatives scaled by N / L.
+#include "particles.cuh"
+
+namespace bs {
+
+#define BS_ORDERS(M, CT, AT, TR) M(2, CT, AT, TR) M(3, CT, AT, TR) M(4, CT, AT, TR) M(5, CT, AT, TR) \
+    M(6, CT, AT, TR) M(7, CT, AT, TR) M(8, CT, AT, TR)
+BS_ORDERS(BS_GATHER_EXTERN, double, double, double)
+BS_ORDERS(BS_GATHER_EXTERN, float, float, float)
+BS_ORDERS(BS_GATHER_EXTERN, __nv_bfloat16, float, float)
+
+namespace {
+using namespace gather_impl;
+
+// ------------------------------------------------------------------ bin
+template <typename TR>
+__global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, double half,
+                           int nbx, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+        unsigned anc[3];
+        TR tt[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double s = x[3 * p + a] * scale;
+            const double sh = s - half;
+            if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
+                ok = false;
+                anc[a] = 0;
+                tt[a] = 0;
+                continue;
+            }
+            const double f = floor(sh);
+            tt[a] = (TR)(sh - f);
+            anc[a] = (unsigned)(((long long)f + 1) & (long long)(N - 1));
+        }
+        unsigned k = NB;
+        if (ok) {
+            k = ((anc[0] / kBrick) * nbx + anc[1] / kBrick) * nbx + anc[2] / kBrick;
+            w.cell[p] = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
+            w.tf[3 * p + 0] = tt[0];
+            w.tf[3 * p + 1] = tt[1];
+            w.tf[3 * p + 2] = tt[2];
+        } else {
+            atomicAdd(status, 1ULL);
+        }
+        w.key[p] = k;
+        w.rank[p] = atomicAdd(&w.count[k], 1u);
+    }
+}
+
+// ------------------------------------------------------------------ scan (single CTA)
+__global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
+                                                    unsigned n) {
+    __shared__ unsigned part[1024];
+    const unsigned t = threadIdx.x;
+    const unsigned chunk = (n + 1023) / 1024;
+    const unsigned b = min(n, t * chunk), e = min(n, b + chunk);
+    unsigned s = 0;
+    for (unsigned i = b; i < e; ++i) s += count[i];
+    part[t] = s;
+    __syncthreads();
+    for (unsigned d = 1; d < 1024; d <<= 1) {
+        unsigned v = (t >= d) ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned run = part[t] - s;         // exclusive
+    for (unsigned i = b; i < e; ++i) {
+        offset[i] = run;
+        run += count[i];
+    }
+    if (t == 1023) offset[n] = part[1023];
+}
+
+// ------------------------------------------------------------------ scatter
+template <typename TR, typename OT>
+__global__ void scatter_kernel(long long P, unsigned NB, Ws<TR> w, OT* __restrict__ out_u,
+                               OT* __restrict__ out_grad) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+        const unsigned k = w.key[p];
+        if (k >= NB) {
+            const OT nan = (OT)NAN;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) out_u[3 * p + i] = nan;
+            if (out_grad) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) out_grad[9 * p + i] = nan;
+            }
+            continue;
+        }
+        const unsigned d = w.offset[k] + w.rank[p];
+        w.s_cell[d] = w.cell[p];
+        w.s_t[3 * (size_t)d + 0] = w.tf[3 * p + 0];
+        w.s_t[3 * (size_t)d + 1] = w.tf[3 * p + 1];
+        w.s_t[3 * (size_t)d + 2] = w.tf[3 * p + 2];
+        w.s_idx[d] = (unsigned)p;
+    }
+}
+
+template <typename CT, typename AT, typename TR>
+int dispatch_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, void* out_u,
+                   void* out_grad, bool grad) {
+    switch (p->order) {
+        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+    }
+    return BSPLINE_ERR_UNSUPPORTED_ORDER;
+}
+
+inline unsigned grid_for(long long P, int threads) {
+    long long g = (P + threads - 1) / threads;
+    if (g > (1LL << 30)) g = 1LL << 30;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <typename CT, typename AT, typename TR>
+int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
+               int flags) {
+    const int nbx = p->N / kBrick;
+    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    Ws<TR> w;
+    const size_t need = carve<TR>(&w, nullptr, NB, P);
+    int rc = p->pws.grow(need);
+    if (rc) return rc;
+    carve<TR>(&w, p->pws.ptr, NB, P);
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
+    const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
+    {
+        StageTimer tm(p, BSPLINE_STAGE_BIN);
+        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx, NB,
+                                                         w, p->d_status);
+    }
+    {
+        StageTimer tm(p, BSPLINE_STAGE_SCAN);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, NB + 1);
+    }
+    {
+        StageTimer tm(p, BSPLINE_STAGE_SCATTER);
+        scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u,
+                                                                 grad ? (AT*)out_grad : nullptr);
+    }
+    {
+        StageTimer tm(p, BSPLINE_STAGE_GATHER);
+        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+    }
+    if (rc) return rc;
+    return set_cuda_error(cudaGetLastError());
+}
+
+}  // namespace
+
+size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P) {
+    const int nbx = p->N / kBrick;
+    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    if (p->dtype == BSPLINE_F64) {
+        Ws<double> w;
+        return carve<double>(&w, nullptr, NB, P);
+    }
+    Ws<float> w;
+    return carve<float>(&w, nullptr, NB, P);
+}
+
+int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
+                  int flags) {
+    switch (p->dtype) {
+        case BSPLINE_F64: return run_interp<double, double, double>(p, coeffs, x, P, out_u, out_grad, flags);
+        case BSPLINE_F32: return run_interp<float, float, float>(p, coeffs, x, P, out_u, out_grad, flags);
+        case BSPLINE_BF16: return run_interp<__nv_bfloat16, float, float>(p, coeffs, x, P, out_u, out_grad, flags);
+    }
+    return BSPLINE_ERR_INVALID_ARG;
+}
+
+}  // namespace bs

@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every symbol include/bspline.h declares.
+
+No compute calls: only argument checks that return before any CUDA call.
+"""
+import os
+import re
+
+import pytest
+
+from paper_1201_4060_gb300 import _build
+from paper_1201_4060_gb300 import bspline as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "bspline.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bspline_[a-z_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert "bspline_interp" in names and "bspline_coeffs" in names and len(names) >= 14
+    lib = B.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_version():
+    assert B.status_string(B.OK) == "ok"
+    assert "not implemented" in B.status_string(B.ERR_NOT_IMPLEMENTED)
+    assert B.status_string(12345) == "unknown status"
+    assert B.version().startswith("bspline-gb300")
+
+
+def test_plan_argument_checks_before_cuda():
+    assert B.lib().bspline_plan(None, 32, 4, B.F32) == B.ERR_INVALID_ARG
+    for N in (0, 4, 7, 12, 48, 2048):
+        rc, h = B.bspline_plan(N, 4, B.F32)
+        assert rc == B.ERR_UNSUPPORTED_N and h == 0
+    for order in (0, 1, 9, -3):
+        rc, h = B.bspline_plan(32, order, B.F32)
+        assert rc == B.ERR_UNSUPPORTED_ORDER and h == 0
+    rc, h = B.bspline_plan(32, 4, 7)
+    assert rc == B.ERR_INVALID_ARG and h == 0
+
+
+def test_null_plan_is_rejected_everywhere():
+    assert B.bspline_destroy(0) == B.OK
+    assert B.bspline_coeffs(0, 16, 32) == B.ERR_INVALID_ARG
+    assert B.bspline_interp(0, 16, 16, 10, 16, 16, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_plan_set_stream(0, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_plan_set_length(0, 1.0) == B.ERR_INVALID_ARG
+    assert B.bspline_plan_set_prefilter(0, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_workspace_bytes(0, 10)[0] == B.ERR_INVALID_ARG
+    assert B.bspline_coeffs_bytes(0)[0] == B.ERR_INVALID_ARG
+    assert B.bspline_uhat_bytes(0)[0] == B.ERR_INVALID_ARG
+    assert B.bspline_status(0)[0] == B.ERR_INVALID_ARG
+    assert B.bspline_run_host(0, 16, 16, 1, 16, 16) == B.ERR_INVALID_ARG
+    assert B.bspline_spread_adjoint(0, 0, 0, 0, 0, 0, 0, 0, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_plan_set_timing(0, 1) == B.ERR_INVALID_ARG
+    assert B.bspline_stage_times(0)[0] == B.ERR_INVALID_ARG

@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (normwise per output quantity: max_p |gpu - oracle| / max_p |oracle|):
+* F64 plans: 1e-12 (the target the method's FP64 path is held to);
+* F32 plans: TOL32 below, derived from the FP32 arithmetic of the transform
+  (~log2(N^3) rounding steps on values of the size of the coefficients) and
+  of the n^3-term stencil sums with FP32 weights;
+* BF16 plans: TOL16, dominated by the 2^-9 relative rounding of each stored
+  coefficient (reported, not a precision claim).
+The FP32 form is also held to the statistical bar of the method: its error
+against the FP64 oracle stays below the interpolation's own truncation error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bspline_oracle as O
+from paper_1201_4060_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L = 2.0 * math.pi
+TOL64 = 1e-12
+TOL32 = {"u": 2e-5, "grad": 5e-5}
+TOL16 = {"u": 2e-2, "grad": 5e-2}
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1201_4060_gb300 import _build
+    _build.build()
+    from paper_1201_4060_gb300 import bspline
+    assert torch.cuda.is_available()
+    return bspline
+
+
+def normwise(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def gpu_path(B, half, x, N, order, dtype, prefilter="interp", grad=True):
+    plan = B.Plan(N, order, dtype, prefilter=prefilter)
+    uh = torch.from_numpy(np.ascontiguousarray(half)).to(plan.uhat_dtype).cuda()
+    coef = plan.coeffs(uh)
+    xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    res = plan.interp(coef, xt, grad=grad)
+    nonfinite = plan.status()
+    torch.cuda.synchronize()
+    c = coef.float().cpu().numpy() if dtype == "bf16" else coef.cpu().numpy()
+    if grad:
+        u, g = res
+        return c, u.cpu().numpy(), g.cpu().numpy(), nonfinite
+    return c, res.cpu().numpy(), None, nonfinite
+
+
+def rounded_input(half, dtype):
+    return half if dtype == "f64" else half.astype(np.complex64).astype(np.complex128)
+
+
+# ----------------------------------------------------------------------- coefficients
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+@pytest.mark.parametrize("order", [2, 3, 4, 6, 8])
+def test_coeffs_f64(B, N, order):
+    half = synth.random_half_spectrum(N, seed=N + order, hermitian=True)
+    x = synth.uniform_particles(64, seed=1)
+    c, _, _, _ = gpu_path(B, half, x, N, order, "f64")
+    ref = O.coefficients(half, order)
+    assert normwise(c, ref) < TOL64
+
+
+@pytest.mark.parametrize("N", [8, 32, 128])
+def test_coeffs_f64_non_hermitian_input_follows_c2r_semantics(B, N):
+    half = synth.random_half_spectrum(N, seed=3, hermitian=False)
+    c, _, _, _ = gpu_path(B, half, synth.uniform_particles(8, 2), N, 4, "f64")
+    assert normwise(c, O.coefficients(half, 4)) < TOL64
+
+
+@pytest.mark.parametrize("order", [3, 4, 6])
+def test_coeffs_l2_prefilter_f64(B, order):
+    N = 32
+    half = synth.kolmogorov_field(N, seed=7).dense()
+    c, _, _, _ = gpu_path(B, half, synth.uniform_particles(8, 2), N, order, "f64", prefilter="l2")
+    assert normwise(c, O.coefficients(half, order, kind="l2")) < TOL64
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("N", [32, 256])
+def test_coeffs_reduced_precision(B, dtype, N):
+    half = synth.kolmogorov_field(N, seed=11).dense()
+    c, _, _, _ = gpu_path(B, half.astype(np.complex64), synth.uniform_particles(8, 2), N, 6, dtype)
+    err = normwise(c, O.coefficients(rounded_input(half, dtype), 6))
+    assert err < (2e-6 if dtype == "f32" else 4e-3), err
+
+
+# ----------------------------------------------------------------------- interpolation
+
+def test_parity_32cubed_cubic_f64(B):
+    """Plain method, FP64: 32^3 Kolmogorov field, order 4, 10^4 uniform particles."""
+    wl = synth.WORKLOADS["parity32"]
+    N, order = wl["N"], wl["order"]
+    half = synth.kolmogorov_field(N, seed=wl["field_seed"]).dense()
+    x = synth.uniform_particles(wl["P"], seed=wl["particle_seed"])
+    _, u, g, nf = gpu_path(B, half, x, N, order, "f64")
+    ru, rg = O.interpolate(half, x, order)
+    assert nf == 0
+    for c in range(3):
+        assert normwise(u[:, c], ru[:, c]) < TOL64
+        for d in range(3):
+            assert normwise(g[:, c, d], rg[:, c, d]) < TOL64
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("N", [8, 16, 64])
+def test_interp_f64_orders_and_sizes(B, order, N):
+    half = synth.kolmogorov_field(N, seed=order).dense()
+    rng = np.random.default_rng(order * 100 + N)
+    x = rng.uniform(-L, 2 * L, (3001, 3))                   # outside [0, L) too, ragged count
+    _, u, g, nf = gpu_path(B, half, x, N, order, "f64")
+    ru, rg = O.interpolate(half, x, order)
+    assert nf == 0
+    assert normwise(u, ru) < TOL64
+    assert normwise(g, rg) < TOL64
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_interp_reduced_precision(B, dtype, order):
+    N = 64
+    half = synth.kolmogorov_field(N, seed=21).dense().astype(np.complex64)
+    x = synth.clustered_particles(20000, seed=5)
+    _, u, g, nf = gpu_path(B, half, x, N, order, dtype)
+    ru, rg = O.interpolate(rounded_input(half.astype(np.complex128), dtype), x, order)
+    tol = TOL32 if dtype == "f32" else TOL16
+    assert nf == 0
+    assert normwise(u, ru) < tol["u"], normwise(u, ru)
+    assert normwise(g, rg) < tol["grad"], normwise(g, rg)
+
+
+def test_no_grad_flag_matches(B):
+    N, order = 32, 6
+    half = synth.kolmogorov_field(N, seed=3).dense()
+    x = synth.uniform_particles(5000, seed=9)
+    _, u1, _, _ = gpu_path(B, half, x, N, order, "f64", grad=False)
+    ru, _ = O.interpolate(half, x, order)
+    assert normwise(u1, ru) < TOL64
+
+
+# ----------------------------------------------------------------------- edge cases
+
+def test_edge_cases_f64(B):
+    N, order = 16, 4
+    half = synth.kolmogorov_field(N, seed=4).dense()
+    h = L / N
+    pts = [
+        [0.0, 0.0, 0.0],                     # on a node, t = 0
+        [h, 2 * h, 3 * h],                   # on nodes
+        [L, L, L],                           # the far corner wraps to 0
+        [-1e-13, 1e-13, L - 1e-13],          # just across the periodic seam
+        [-7.5 * L, 3.25 * L, 1e3],           # far outside, still many fractional bits
+        [0.5 * h, 0.5 * h, 0.5 * h],
+    ]
+    # many particles in a single cell and in a single brick, plus a ragged count
+    rng = np.random.default_rng(0)
+    pts += (np.array([3.3, 4.4, 5.5]) * h + rng.uniform(0, h, (777, 3))).tolist()
+    x = np.array(pts)
+    _, u, g, nf = gpu_path(B, half, x, N, order, "f64")
+    ru, rg = O.interpolate(half, x, order)
+    assert nf == 0
+    assert normwise(u, ru) < TOL64
+    assert normwise(g, rg) < TOL64
+
+
+def test_nonfinite_positions_give_nan_and_status(B):
+    N, order = 16, 4
+    half = synth.kolmogorov_field(N, seed=4).dense()
+    x = synth.uniform_particles(100, seed=3)
+    x[5, 0] = np.nan
+    x[17, 2] = np.inf
+    x[42, 1] = -np.inf
+    x[60, 1] = 1e300                        # finite but beyond any fractional resolution
+    _, u, g, nf = gpu_path(B, half, x, N, order, "f64")
+    bad = [5, 17, 42, 60]
+    assert nf == len(bad)
+    assert np.all(np.isnan(u[bad])) and np.all(np.isnan(g[bad]))
+    good = np.setdiff1d(np.arange(100), bad)
+    ru, rg = O.interpolate(half, x[good], order)
+    assert normwise(u[good], ru) < TOL64
+    assert normwise(g[good], rg) < TOL64
+
+
+def test_zero_and_one_particle(B):
+    N, order = 16, 6
+    half = synth.kolmogorov_field(N, seed=5).dense()
+    plan = B.Plan(N, order, "f64")
+    coef = plan.coeffs(torch.from_numpy(half).cuda())
+    x0 = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    u0, g0 = plan.interp(coef, x0)
+    assert u0.shape == (0, 3) and g0.shape == (0, 3, 3)
+    x1 = np.array([[1.0, 2.0, 3.0]])
+    u1, g1 = plan.interp(coef, torch.from_numpy(x1).cuda())
+    ru, rg = O.interpolate(half, x1, order)
+    assert normwise(u1.cpu().numpy(), ru) < TOL64
+    assert normwise(g1.cpu().numpy(), rg) < TOL64
+
+
+def test_abi_rejects_bad_arguments_on_gpu(B):
+    plan = B.Plan(16, 4, "f32")
+    h = plan.handle
+    assert B.bspline_interp(h, 0, 0, 10, 0, 0, 0) == B.ERR_INVALID_ARG
+    buf = torch.empty(1 << 16, dtype=torch.float64, device="cuda")
+    p = buf.data_ptr()
+    assert B.bspline_interp(h, p, p + 4, 10, p, p, 0) == B.ERR_INVALID_ARG       # misaligned x
+    assert B.bspline_interp(h, p, p, -1, p, p, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_interp(h, p, p, 10, p, 0, 0) == B.ERR_INVALID_ARG           # grad NULL without flag
+    assert B.bspline_interp(h, p, p, 10, p, p, 0x80) == B.ERR_INVALID_ARG        # unknown flag
+    assert B.bspline_coeffs(h, p, p) == B.ERR_INVALID_ARG                        # aliasing
+    assert B.bspline_spread_adjoint(h, p, p, 10, p, p, p, 0, 0) == B.ERR_NOT_IMPLEMENTED
+    assert B.bspline_plan_set_length(h, -1.0) == B.ERR_INVALID_ARG
+
+
+def test_run_host_matches_device_path(B):
+    N, order = 32, 4
+    half = synth.kolmogorov_field(N, seed=8).dense().astype(np.complex64)
+    x = synth.uniform_particles(4096, seed=8)
+    _, u, g, _ = gpu_path(B, half, x, N, order, "f32")
+    plan = B.Plan(N, order, "f32")
+    uh = torch.from_numpy(half).pin_memory()
+    xh = torch.from_numpy(x).pin_memory()
+    uo = torch.empty((4096, 3), dtype=torch.float32).pin_memory()
+    go = torch.empty((4096, 3, 3), dtype=torch.float32).pin_memory()
+    plan.run_host(uh, xh, uo, go)
+    assert np.array_equal(uo.numpy(), u) and np.array_equal(go.numpy(), g)
+
+
+def test_custom_domain_length(B):
+    N, order, Lc = 16, 4, 3.0
+    half = synth.kolmogorov_field(N, seed=12).dense()
+    x = np.random.default_rng(1).uniform(0, Lc, (500, 3))
+    plan = B.Plan(N, order, "f64", L=Lc)
+    coef = plan.coeffs(torch.from_numpy(half).cuda())
+    u, g = plan.interp(coef, torch.from_numpy(x).cuda())
+    ru, rg = O.evaluate(O.coefficients(half, order), x, order, L=Lc)
+    assert normwise(u.cpu().numpy(), ru) < TOL64
+    assert normwise(g.cpu().numpy(), rg) < TOL64
