@@ -321,7 +321,9 @@ def direct_sum_modes(N: int, idx: np.ndarray, val: np.ndarray, x: np.ndarray,
                              np.asarray(x, dtype=np.float64), L)
 
 
-def _direct_sum_modes(N, idx, val, x, L, chunk_modes: int = 1 << 18):
+def _direct_sum_modes(N, idx, val, x, L, chunk_elems: int = 1 << 22):
+    """Re sum_k m_k a_k exp(i K.x) and its gradient Re sum_k m_k a_k i K_j exp(i K.x), written with
+    cos/sin of the phase; modes are taken in chunks of at most chunk_elems (particle, mode) pairs."""
     kx = _signed(idx[:, 0], N).astype(np.float64)
     ky = _signed(idx[:, 1], N).astype(np.float64)
     kz = idx[:, 2].astype(np.float64)
@@ -331,15 +333,19 @@ def _direct_sum_modes(N, idx, val, x, L, chunk_modes: int = 1 << 18):
     u = np.zeros((P, 3))
     g = np.zeros((P, 3, 3))
     K = np.stack([kx, ky, kz], axis=1) * w                # [M, 3] physical wavenumbers
+    chunk_modes = max(1, chunk_elems // max(P, 1))
     for m0 in range(0, idx.shape[0], chunk_modes):
         Kc = K[m0:m0 + chunk_modes]
-        ph = np.exp(1j * (x @ Kc.T))                        # [P, Mc]
+        phase = x @ Kc.T                                     # [P, Mc]
+        cs, sn = np.cos(phase), np.sin(phase)
+        del phase
         for c in range(3):
             a = val[c, m0:m0 + chunk_modes] * mult[m0:m0 + chunk_modes]
-            z = ph * a[None, :]
-            u[:, c] += z.real.sum(axis=1)
+            re = cs @ a.real - sn @ a.imag                   # Re(a e^{i phase}) summed over modes
+            u[:, c] += re
             for j in range(3):
-                g[:, c, j] += (1j * z * Kc[None, :, j]).real.sum(axis=1)
+                # Re(i K_j a e^{i phase}) = -K_j Im(a e^{i phase})
+                g[:, c, j] -= cs @ (Kc[:, j] * a.imag) + sn @ (Kc[:, j] * a.real)
     return u, g
 
 
