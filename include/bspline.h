@@ -68,7 +68,8 @@ enum {
     BSPLINE_ERR_NONFINITE_INPUT = -5,   /* returned by bspline_status when positions were NaN/Inf */
     BSPLINE_ERR_TIMEOUT = -6,           /* a bounded device-side wait gave up */
     BSPLINE_ERR_NOT_IMPLEMENTED = -7,
-    BSPLINE_ERR_OUT_OF_MEMORY = -8      /* workspace allocation failed */
+    BSPLINE_ERR_OUT_OF_MEMORY = -8,     /* workspace allocation failed */
+    BSPLINE_ERR_TOO_LARGE = -9          /* beyond the fixed scratch of bspline_interp_noalloc */
 };
 
 /* Flags of bspline_interp. */
@@ -165,6 +166,34 @@ enum {
 };
 int bspline_plan_set_timing(bspline_plan_t plan, int enable);
 int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);
+
+/* Allocation-free evaluation of u and grad u (no counterpart in the paper: it
+ * serves callers, not the method).  Some callers cannot allocate device
+ * memory: code running inside a CUDA graph capture that another framework
+ * owns (allocation cannot be captured), code that must never stall the GPU
+ * (cudaMalloc and cudaFree may synchronise the device), and processes whose
+ * device memory belongs to another allocator with a fixed budget.  This entry
+ * point needs no plan and calls no allocator: it does what bspline_interp
+ * does on a plan with the same N, order, dtype and L, with all scratch in one
+ * fixed 16 MiB device array inside the library (present on every GPU that
+ * loads the library until the process exits).
+ * Arguments as bspline_interp, plus: N, order, dtype, L (domain length; the
+ * coefficients come from bspline_coeffs of such a plan) and stream (a
+ * cudaStream_t as void*, NULL = legacy stream).
+ * Limits: N <= BSPLINE_NOALLOC_MAX_N and P <= BSPLINE_NOALLOC_MAX_PARTICLES,
+ * else BSPLINE_ERR_TOO_LARGE is returned before any device work.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array, whose contents persist between
+ * calls; each call clears the parts that must start at zero.  Calls that
+ * overlap on the GPU (concurrent streams or host threads) race on the array,
+ * so serialise them.  Non-finite positions give NaN outputs; their count is
+ * not reported (there is no plan to hold a status word). */
+#define BSPLINE_NOALLOC_MAX_N 256
+#define BSPLINE_NOALLOC_MAX_PARTICLES 131072
+int bspline_interp_noalloc(const void* coeffs, int N, int order, bspline_dtype dtype, double L,
+                           const double* x, int64_t P, void* out_u, void* out_grad, int flags,
+                           void* stream);
 
 #ifdef __cplusplus
 }

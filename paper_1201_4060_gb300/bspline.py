@@ -23,6 +23,9 @@ ERR_NONFINITE_INPUT = -5
 ERR_TIMEOUT = -6
 ERR_NOT_IMPLEMENTED = -7
 ERR_OUT_OF_MEMORY = -8
+ERR_TOO_LARGE = -9
+NOALLOC_MAX_N = 256
+NOALLOC_MAX_PARTICLES = 131072
 
 F64, F32, BF16 = 0, 1, 2
 PREFILTER_INTERP, PREFILTER_L2 = 0, 1
@@ -66,6 +69,7 @@ def _load() -> ctypes.CDLL:
         "bspline_version": (ctypes.c_char_p, []),
         "bspline_plan_set_timing": (i32, [vp, i32]),
         "bspline_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
+        "bspline_interp_noalloc": (i32, [vp, i32, i32, i32, ctypes.c_double, vp, i64, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -173,6 +177,12 @@ def bspline_stage_times(plan: int) -> tuple[int, list[float], list[int]]:
     n = (ctypes.c_int64 * NSTAGES)()
     rc = _load().bspline_stage_times(plan, ms, n)
     return rc, list(ms), list(n)
+
+
+def bspline_interp_noalloc(coeffs_ptr: int, N: int, order: int, dtype: int, L: float, x_ptr: int, P: int,
+                           u_ptr: int, grad_ptr: int, flags: int, stream: int) -> int:
+    """Allocation-free evaluation (fixed scratch inside the library; see include/bspline.h)."""
+    return _load().bspline_interp_noalloc(coeffs_ptr, N, order, dtype, L, x_ptr, P, u_ptr, grad_ptr, flags, stream)
 
 
 # ---- torch-facing plan -------------------------------------------------------------

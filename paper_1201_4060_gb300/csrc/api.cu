@@ -413,6 +413,7 @@ const char* bspline_status_string(int status) {
         case BSPLINE_ERR_TIMEOUT: return "device wait timed out";
         case BSPLINE_ERR_NOT_IMPLEMENTED: return "not implemented";
         case BSPLINE_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case BSPLINE_ERR_TOO_LARGE: return "size beyond the fixed scratch of bspline_interp_noalloc";
     }
     return "unknown status";
 }

@@ -82,5 +82,8 @@ int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs);
 size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P);
 int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u,
                   void* out_grad, int flags);
+// The same sequence on a caller-supplied workspace (interp_workspace_bytes bytes) and status word.
+int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs,
+                     const double* x, int64_t P, void* out_u, void* out_grad, int flags);
 
 }  // namespace bs

@@ -176,7 +176,43 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     return set_cuda_error(cudaGetLastError());
 }
 
+// Same launch sequence as run_interp, with the workspace and the status word
+// supplied by the caller instead of the plan.
+template <typename CT, typename AT, typename TR>
+int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs, const double* x,
+                  int64_t P, void* out_u, void* out_grad, int flags) {
+    const int nbx = p->N / kBrick;
+    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    Ws<TR> w;
+    carve<TR>(&w, ws, NB, P);
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
+    const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
+    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx, NB, w,
+                                                     status);
+    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, NB + 1);
+    scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
+    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+    if (rc) return rc;
+    return set_cuda_error(cudaGetLastError());
+}
+
 }  // namespace
+
+int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs, const double* x,
+                     int64_t P, void* out_u, void* out_grad, int flags) {
+    switch (p->dtype) {
+        case BSPLINE_F64:
+            return run_interp_ws<double, double, double>(p, ws, status, coeffs, x, P, out_u, out_grad, flags);
+        case BSPLINE_F32:
+            return run_interp_ws<float, float, float>(p, ws, status, coeffs, x, P, out_u, out_grad, flags);
+        case BSPLINE_BF16:
+            return run_interp_ws<__nv_bfloat16, float, float>(p, ws, status, coeffs, x, P, out_u, out_grad, flags);
+    }
+    return BSPLINE_ERR_INVALID_ARG;
+}
 
 size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P) {
     const int nbx = p->N / kBrick;
