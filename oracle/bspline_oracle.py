@@ -438,14 +438,15 @@ def l2_error_field(N: int, idx: np.ndarray, val: np.ndarray, n: int, L: float = 
     val = np.asarray(val, dtype=np.complex128)
     k = np.stack([_signed(idx[:, 0], N), _signed(idx[:, 1], N), idx[:, 2]], axis=1).astype(np.float64)
     kappa = k / N
+    # per-axis factors depend only on the signed wavenumber: tabulate them for -N/2..N/2
+    ktab = np.arange(-(N // 2), N // 2 + 1, dtype=np.float64)
     with np.errstate(divide="ignore", invalid="ignore"):
-        F0, D, E0, E1 = _alias_sums(kappa, n, kind)          # [M, 3] each
-    # kappa_a = 0: the mode is constant along a, reproduced exactly (c(0) sinc(i)^n = delta_i0)
-    zero = kappa == 0
-    F0 = np.where(zero, 1.0, F0)
-    D = np.where(zero, 0.0, D)
-    E0 = np.where(zero, 0.0, E0)
-    E1 = np.where(zero, 0.0, E1)
+        tabs = _alias_sums(ktab / N, n, kind)
+    # kappa = 0: the mode is constant along that axis, reproduced exactly (c(0) sinc(i)^n = delta_i0)
+    z0 = ktab == 0
+    tabs = [np.where(z0, v0, t) for t, v0 in zip(tabs, (1.0, 0.0, 0.0, 0.0))]
+    pos = (k + N // 2).astype(np.int64)
+    F0, D, E0, E1 = (t[pos] for t in tabs)                    # [M, 3] each
     mult = np.where((idx[:, 2] == 0) | (2 * idx[:, 2] == N), 1.0, 2.0)
     amp2 = np.abs(val) ** 2 * mult[None, :]                   # [3, M]
     # prod F0 - 1 = (1+Dx)(1+Dy)(1+Dz) - 1, expanded
