@@ -137,15 +137,17 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
     tb = 8 if dtype == "f64" else 4
     spec = 3 * N * N * H * cplx
     coef = 3 * N ** 3 * elem
-    nb = (N // 8) ** 3
+    brick = 8 if dtype == "f64" else 16
+    nb = max(1, N // brick) ** 3
+    rec = 16 if tb == 4 else 32                  # packed record: first node + t per axis
     return {
         "fft_x": 2 * spec,                       # read u_hat, write the x-transformed spectrum
         "fft_y": 2 * spec,                       # in place
         "fft_z": spec + coef,                    # read spectrum, write coefficients
-        "bin": P * (24 + 12 + 4 + 3 * tb),       # positions in; key, rank, cell, t out
+        "bin": P * (24 + 8 + rec),               # positions in; key, rank, record out
         "scan": 2 * 4 * (nb + 1),
-        "scatter": P * (12 + 3 * tb) + P * (8 + 3 * tb),   # key, rank, cell, t in; sorted cell, t, index out
-        "gather": coef + P * (8 + 3 * tb) + P * 12 * outb,  # coefficients once, sorted records, u and grad out
+        "scatter": P * (8 + rec) + P * (rec + 4),          # key, rank, record in; sorted record, index out
+        "gather": coef + P * (rec + 4) + P * 12 * outb,    # coefficients once, sorted records, u and grad out
     }[stage]
 
 

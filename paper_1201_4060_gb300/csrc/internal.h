@@ -14,8 +14,11 @@ namespace bs {
 
 // Cells per brick edge: particles are binned by the brick that holds the first
 // node of their stencil, and one CTA stages one brick (plus the order-1 halo)
-// of coefficients in shared memory.
-constexpr int kBrick = 8;
+// of coefficients in shared memory.  16^3 bricks for FP32/BF16 (enough
+// particles per brick to assemble bank-conflict-free warps, and a 21^3 x 3
+// FP32 tile at order 6 still fits two CTAs per SM); 8^3 for FP64.
+constexpr int brick_edge(int dtype) { return dtype == BSPLINE_F64 ? 8 : 16; }
+inline int bricks_per_axis(int N, int dtype) { return N >= brick_edge(dtype) ? N / brick_edge(dtype) : 1; }
 
 struct PendingTiming {
     int stage;

@@ -2,7 +2,7 @@
 //
 // Locate (Eq. alg-int-6): s = x N / L in FP64; the stencil nodes are
 // floor(s - n/2) + j, j = 1..n; the local variable is t = (s - n/2) - floor(s - n/2).
-// The first node (the "anchor") picks a brick of kBrick^3 cells; particles are
+// The first node (the "anchor") picks a brick of 16^3 (FP64: 8^3) cells; particles are
 // counting-sorted by brick so that one CTA stages the brick's coefficients
 // (plus the n-1 halo) in shared memory once and evaluates all of its particles.
 //
@@ -30,9 +30,31 @@ namespace {
 using namespace gather_impl;
 
 // ------------------------------------------------------------------ bin
+// For 0 <= sh < 2^52: floor(sh) and the fraction sh - floor(sh) rounded to
+// float, read off the bits of the double with integer operations (GB300's
+// FP64 pipe is narrow; only the multiply and the shift by n/2 stay in FP64).
+// Returns false outside that range.
+__device__ __forceinline__ bool split_nonneg(double sh, long long* fl, float* t) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(sh);
+    if (b >> 63) return false;                                 // negative
+    const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
+    if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
+    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
+    if (e < 0) {                                               // [0, 1): floor 0, fraction sh
+        *fl = 0;
+        // below 2^-60 (or subnormal) the fraction is 0 to FP32 accuracy of the weights
+        *t = (e < -60) ? 0.f : __ull2float_rn(m) * __int_as_float((127 + e - 52) << 23);
+        return true;
+    }
+    const int sa = 52 - e;                                     // fraction bits, 1..52
+    *fl = (long long)(m >> sa);
+    *t = __ull2float_rn(m & ((1ULL << sa) - 1)) * __int_as_float((127 - sa) << 23);
+    return true;
+}
+
 template <typename TR>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, double half,
-                           int nbx, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
+                           int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
         unsigned anc[3];
@@ -42,6 +64,15 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
         for (int a = 0; a < 3; ++a) {
             const double s = x[3 * p + a] * scale;
             const double sh = s - half;
+            if constexpr (sizeof(TR) == 4) {
+                long long fl;
+                float tf;
+                if (split_nonneg(sh, &fl, &tf)) {
+                    tt[a] = tf;
+                    anc[a] = (unsigned)((fl + 1) & (long long)(N - 1));
+                    continue;
+                }
+            }
             if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
                 ok = false;
                 anc[a] = 0;
@@ -54,11 +85,13 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
         }
         unsigned k = NB;
         if (ok) {
-            k = ((anc[0] / kBrick) * nbx + anc[1] / kBrick) * nbx + anc[2] / kBrick;
-            w.cell[p] = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
-            w.tf[3 * p + 0] = tt[0];
-            w.tf[3 * p + 1] = tt[1];
-            w.tf[3 * p + 2] = tt[2];
+            k = ((anc[0] >> bshift) * nbx + (anc[1] >> bshift)) * nbx + (anc[2] >> bshift);
+            Rec<TR> r;
+            r.cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
+            r.t[0] = tt[0];
+            r.t[1] = tt[1];
+            r.t[2] = tt[2];
+            w.rec[p] = r;
         } else {
             atomicAdd(status, 1ULL);
         }
@@ -110,10 +143,7 @@ __global__ void scatter_kernel(long long P, unsigned NB, Ws<TR> w, OT* __restric
             continue;
         }
         const unsigned d = w.offset[k] + w.rank[p];
-        w.s_cell[d] = w.cell[p];
-        w.s_t[3 * (size_t)d + 0] = w.tf[3 * p + 0];
-        w.s_t[3 * (size_t)d + 1] = w.tf[3 * p + 1];
-        w.s_t[3 * (size_t)d + 2] = w.tf[3 * p + 2];
+        w.s_rec[d] = w.rec[p];
         w.s_idx[d] = (unsigned)p;
     }
 }
@@ -142,7 +172,8 @@ inline unsigned grid_for(long long P, int threads) {
 template <typename CT, typename AT, typename TR>
 int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
                int flags) {
-    const int nbx = p->N / kBrick;
+    const int nbx = bricks_per_axis(p->N, p->dtype);
+    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
     const unsigned NB = (unsigned)nbx * nbx * nbx;
     Ws<TR> w;
     const size_t need = carve<TR>(&w, nullptr, NB, P);
@@ -156,8 +187,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx, NB,
-                                                         w, p->d_status);
+        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx,
+                                                         bshift, NB, w, p->d_status);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -181,7 +212,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
 template <typename CT, typename AT, typename TR>
 int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs, const double* x,
                   int64_t P, void* out_u, void* out_grad, int flags) {
-    const int nbx = p->N / kBrick;
+    const int nbx = bricks_per_axis(p->N, p->dtype);
+    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
     const unsigned NB = (unsigned)nbx * nbx * nbx;
     Ws<TR> w;
     carve<TR>(&w, ws, NB, P);
@@ -190,8 +222,8 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
-    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx, NB, w,
-                                                     status);
+    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx,
+                                                     bshift, NB, w, status);
     scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, NB + 1);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
@@ -215,7 +247,8 @@ int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, co
 }
 
 size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P) {
-    const int nbx = p->N / kBrick;
+    const int nbx = bricks_per_axis(p->N, p->dtype);
+    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
     const unsigned NB = (unsigned)nbx * nbx * nbx;
     if (p->dtype == BSPLINE_F64) {
         Ws<double> w;

@@ -10,16 +10,22 @@ namespace gather_impl {
 
 constexpr int kAnchorBits = 10;          // N <= 1024
 
+// One particle's located record: packed first stencil node
+// (ax << 20 | ay << 10 | az) and the local variable t per axis.  16 bytes
+// for FP32 t, 32 bytes for FP64 t, so that it moves in one vector access.
+template <typename TR> struct __align__(16) Rec {
+    unsigned cell;
+    TR t[3];
+};
+
 template <typename TR> struct Ws {
     unsigned* count;    // [NB + 1]  particles per brick; slot NB = invalid positions
     unsigned* offset;   // [NB + 2]  exclusive prefix sum of count
     unsigned* key;      // [P]
     unsigned* rank;     // [P]
-    unsigned* cell;     // [P]       packed anchor node (ax << 20 | ay << 10 | az)
-    TR* tf;             // [P][3]    local variable t per axis
-    unsigned* s_cell;   // [P]       sorted copies
-    TR* s_t;            // [P][3]
-    unsigned* s_idx;    // [P]       original particle index
+    Rec<TR>* rec;       // [P]       located records in input order
+    Rec<TR>* s_rec;     // [P]       sorted by brick
+    unsigned* s_idx;    // [P]       original particle index of each sorted record
 };
 
 inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -35,10 +41,8 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 2));
     w->key = (unsigned*)take(sizeof(unsigned) * P);
     w->rank = (unsigned*)take(sizeof(unsigned) * P);
-    w->cell = (unsigned*)take(sizeof(unsigned) * P);
-    w->tf = (TR*)take(sizeof(TR) * 3 * P);
-    w->s_cell = (unsigned*)take(sizeof(unsigned) * P);
-    w->s_t = (TR*)take(sizeof(TR) * 3 * P);
+    w->rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
+    w->s_rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
     w->s_idx = (unsigned*)take(sizeof(unsigned) * P);
     return off;
 }
@@ -75,86 +79,208 @@ __device__ __forceinline__ void bspline_weights(A t, A (&w)[n], A (&dw)[n]) {
     }
 }
 
-template <typename C> __device__ __forceinline__ float ld_coef(const C* p);
-template <> __device__ __forceinline__ float ld_coef<float>(const float* p) { return *p; }
-template <> __device__ __forceinline__ float ld_coef<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+// ------------------------------------------------------------------ gather
+// Coefficient tile of one brick: (BRICK + ORD - 1)^3 nodes per component,
+// [c][x][y][z] with z fastest, periodic wrap of the grid indices on staging.
+// FP32 and BF16 coefficients are staged as FP32 (BF16 widened on load).
+template <typename CT> struct TileT { using T = float; };
+template <> struct TileT<double> { using T = double; };
 
-template <typename C, typename A> __device__ __forceinline__ A load_a(const C* p) {
-    if constexpr (sizeof(A) == 8) return *p;
-    else return ld_coef<C>(p);
+template <typename CT> __device__ __forceinline__ typename TileT<CT>::T widen(CT v) { return v; }
+template <> __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <int ORD, typename CT> constexpr int tile_edge() { return brick_edge(sizeof(CT) == 8 ? BSPLINE_F64 : BSPLINE_F32) + ORD - 1; }
+
+template <int ORD, typename CT>
+constexpr size_t tile_bytes() {
+    return sizeof(typename TileT<CT>::T) * 3 * (size_t)tile_edge<ORD, CT>() * tile_edge<ORD, CT>() * tile_edge<ORD, CT>();
 }
 
-// ------------------------------------------------------------------ gather
-template <int ORD> constexpr int tile_edge() { return kBrick + ORD - 1; }
+constexpr int kGatherThreads = 256;
+constexpr int kChunk = 1024;          // particles bucketed together (FP32 path)
 
-template <int ORD, typename CT, typename AT, typename TR, bool GRAD>
-__global__ void __launch_bounds__(128)
-gather_kernel(const CT* __restrict__ coef, int N, int nbx, Ws<TR> w, AT* __restrict__ out_u,
-              AT* __restrict__ out_grad, AT dscale) {
-    constexpr int E = tile_edge<ORD>();
+template <int ORD, typename CT>
+__device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
+                                           int y0, int z0) {
+    constexpr int E = tile_edge<ORD, CT>();
     constexpr int E3 = E * E * E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CT* tile = reinterpret_cast<CT*>(smem_raw);
-    const unsigned brick = blockIdx.x;
-    const unsigned beg = w.offset[brick], end = w.offset[brick + 1];
-    if (beg == end) return;
-    const int bx = brick / (nbx * nbx), by = (brick / nbx) % nbx, bz = brick % nbx;
-    const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
     const int msk = N - 1;
     for (int e = threadIdx.x; e < 3 * E3; e += blockDim.x) {
         const int c = e / E3, r = e - c * E3;
         const int ix = r / (E * E), iy = (r / E) % E, iz = r % E;
         const size_t g = (((size_t)c * N + ((x0 + ix) & msk)) * N + ((y0 + iy) & msk)) * N + ((z0 + iz) & msk);
-        tile[e] = coef[g];
+        tile[e] = widen<CT>(coef[g]);
     }
-    __syncthreads();
-    for (unsigned i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        const unsigned cp = w.s_cell[i];
-        const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
-        const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
-        const int oz = (int)(cp & 1023u) - z0;
-        AT wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
-        bspline_weights<ORD, AT>((AT)w.s_t[3 * (size_t)i + 0], wx, dwx);
-        bspline_weights<ORD, AT>((AT)w.s_t[3 * (size_t)i + 1], wy, dwy);
-        bspline_weights<ORD, AT>((AT)w.s_t[3 * (size_t)i + 2], wz, dwz);
-        const unsigned idx = w.s_idx[i];
+}
+
+// u and grad u of one particle from the staged tile (Table 1 contraction,
+// z axis first).  base points at the particle's first stencil node.
+template <int ORD, typename A, bool GRAD, int E>
+__device__ __forceinline__ void eval_particle(const A* __restrict__ base, A tx, A ty, A tz, A dscale,
+                                              A* __restrict__ out_u, A* __restrict__ out_grad) {
+    constexpr int E3 = E * E * E;
+    A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+    bspline_weights<ORD, A>(tx, wx, dwx);
+    bspline_weights<ORD, A>(ty, wy, dwy);
+    bspline_weights<ORD, A>(tz, wz, dwz);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const CT* tc = tile + c * E3 + (ox * E + oy) * E + oz;
-            AT u = 0, gx = 0, gy = 0, gz = 0;
+    for (int c = 0; c < 3; ++c) {
+        const A* tc = base + c * E3;
+        A u = 0, gx = 0, gy = 0, gz = 0;
 #pragma unroll
-            for (int jx = 0; jx < ORD; ++jx) {
-                AT y00 = 0, y10 = 0, y01 = 0;
+        for (int jx = 0; jx < ORD; ++jx) {
+            A y00 = 0, y10 = 0, y01 = 0;
 #pragma unroll
-                for (int jy = 0; jy < ORD; ++jy) {
-                    const CT* line = tc + (jx * E + jy) * E;
-                    AT z0v = 0, z1v = 0;
+            for (int jy = 0; jy < ORD; ++jy) {
+                const A* line = tc + (jx * E + jy) * E;
+                A z0v = 0, z1v = 0;
 #pragma unroll
-                    for (int jz = 0; jz < ORD; ++jz) {
-                        const AT a = load_a<CT, AT>(line + jz);
-                        z0v = fma(wz[jz], a, z0v);
-                        if (GRAD) z1v = fma(dwz[jz], a, z1v);
-                    }
-                    y00 = fma(wy[jy], z0v, y00);
-                    if (GRAD) {
-                        y10 = fma(dwy[jy], z0v, y10);
-                        y01 = fma(wy[jy], z1v, y01);
-                    }
+                for (int jz = 0; jz < ORD; ++jz) {
+                    const A a = line[jz];
+                    z0v = fma(wz[jz], a, z0v);
+                    if (GRAD) z1v = fma(dwz[jz], a, z1v);
                 }
-                u = fma(wx[jx], y00, u);
+                y00 = fma(wy[jy], z0v, y00);
                 if (GRAD) {
-                    gx = fma(dwx[jx], y00, gx);
-                    gy = fma(wx[jx], y10, gy);
-                    gz = fma(wx[jx], y01, gz);
+                    y10 = fma(dwy[jy], z0v, y10);
+                    y01 = fma(wy[jy], z1v, y01);
                 }
             }
-            out_u[3 * (size_t)idx + c] = u;
+            u = fma(wx[jx], y00, u);
             if (GRAD) {
-                out_grad[9 * (size_t)idx + 3 * c + 0] = gx * dscale;
-                out_grad[9 * (size_t)idx + 3 * c + 1] = gy * dscale;
-                out_grad[9 * (size_t)idx + 3 * c + 2] = gz * dscale;
+                gx = fma(dwx[jx], y00, gx);
+                gy = fma(wx[jx], y10, gy);
+                gz = fma(wx[jx], y01, gz);
             }
         }
+        out_u[c] = u;
+        if (GRAD) {
+            out_grad[3 * c + 0] = gx * dscale;
+            out_grad[3 * c + 1] = gy * dscale;
+            out_grad[3 * c + 2] = gz * dscale;
+        }
+    }
+}
+
+// FP64: one thread per particle (the FP64 pipe, not shared memory, bounds it).
+template <int ORD, typename TR, bool GRAD>
+__global__ void __launch_bounds__(128)
+gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __restrict__ out_u,
+           double* __restrict__ out_grad, double dscale) {
+    constexpr int B = brick_edge(BSPLINE_F64);
+    constexpr int E = tile_edge<ORD, double>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* tile = reinterpret_cast<double*>(smem_raw);
+    const unsigned brick = blockIdx.x;
+    const unsigned beg = w.offset[brick], end = w.offset[brick + 1];
+    if (beg == end) return;
+    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
+    stage_tile<ORD, double>(tile, coef, N, x0, y0, z0);
+    __syncthreads();
+    for (unsigned i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        const Rec<TR> rc = w.s_rec[i];
+        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+        const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+        const int oz = (int)(rc.cell & 1023u) - z0;
+        const unsigned idx = w.s_idx[i];
+        double u[3], g[9];
+        eval_particle<ORD, double, GRAD, E>(tile + (ox * E + oy) * E + oz, (double)rc.t[0], (double)rc.t[1],
+                                             (double)rc.t[2], dscale, u, g);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out_u[3 * (size_t)idx + c] = u[c];
+        if (GRAD) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) out_grad[9 * (size_t)idx + k] = g[k];
+        }
+    }
+}
+
+// FP32 accumulation (FP32 or BF16 coefficients).  Shared-memory bandwidth
+// bounds this kernel: each particle reads 3 ORD^3 tile values, and a warp
+// load costs one cycle per distinct address in the busiest of the 32 banks.
+// Particles of a brick are therefore assembled into warp "jobs" in which no
+// two particles' stencil origins fall into the same bank: within a chunk,
+// particles are bucketed by the bank of their origin (residue mod 32) and
+// job j takes the j-th particle of every bucket.  Every load of a job is then
+// conflict-free; the number of jobs is the largest bucket.
+template <int ORD, typename CT, typename TR, bool GRAD>
+__global__ void __launch_bounds__(kGatherThreads)
+gather_f32(const CT* __restrict__ coef, int N, int nbx, Ws<TR> w, float* __restrict__ out_u,
+           float* __restrict__ out_grad, float dscale) {
+    constexpr int B = brick_edge(BSPLINE_F32);
+    constexpr int E = tile_edge<ORD, CT>();
+    constexpr int NW = kGatherThreads / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* tile = reinterpret_cast<float*>(smem_raw);
+    __shared__ unsigned s_bucket[32];
+    __shared__ unsigned short s_rank[kChunk];
+    __shared__ unsigned short s_order[kChunk];
+    const unsigned brick = blockIdx.x;
+    const unsigned beg = w.offset[brick], end = w.offset[brick + 1];
+    if (beg == end) return;
+    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
+    stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (unsigned c0 = beg; c0 < end; c0 += kChunk) {
+        const int n = (int)min((unsigned)kChunk, end - c0);
+        if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
+        __syncthreads();                                  // also orders the tile staging before first use
+        for (int i = threadIdx.x; i < n; i += kGatherThreads) {
+            const unsigned cp = w.s_rec[c0 + i].cell;
+            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
+            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
+            const int oz = (int)(cp & 1023u) - z0;
+            const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
+            s_rank[i] = (unsigned short)atomicAdd(&s_bucket[r], 1u);
+        }
+        __syncthreads();
+        // job-sorted position: all particles of smaller rank, then the same rank in smaller buckets
+        for (int i = threadIdx.x; i < n; i += kGatherThreads) {
+            const unsigned cp = w.s_rec[c0 + i].cell;
+            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
+            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
+            const int oz = (int)(cp & 1023u) - z0;
+            const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
+            const unsigned k = s_rank[i];
+            unsigned pos = 0;
+#pragma unroll 8
+            for (unsigned q = 0; q < 32; ++q) {
+                const unsigned bq = s_bucket[q];
+                pos += min(bq, k) + ((q < r && bq > k) ? 1u : 0u);
+            }
+            s_order[pos] = (unsigned short)i;
+        }
+        __syncthreads();
+        const unsigned my_bucket = s_bucket[lane];
+        unsigned njobs = my_bucket;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) njobs = max(njobs, __shfl_xor_sync(0xffffffffu, njobs, d));
+        for (unsigned j = warp; j < njobs; j += NW) {
+            unsigned lo = min(my_bucket, j), hi = min(my_bucket, j + 1);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                lo += __shfl_xor_sync(0xffffffffu, lo, d);
+                hi += __shfl_xor_sync(0xffffffffu, hi, d);
+            }
+            if (lo + lane < hi) {
+                const unsigned i = c0 + s_order[lo + lane];
+                const Rec<TR> rc = w.s_rec[i];
+                const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+                const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+                const int oz = (int)(rc.cell & 1023u) - z0;
+                const unsigned idx = w.s_idx[i];
+                float u[3], g[9];
+                eval_particle<ORD, float, GRAD, E>(tile + (ox * E + oy) * E + oz, (float)rc.t[0], (float)rc.t[1],
+                                                    (float)rc.t[2], dscale, u, g);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out_u[3 * (size_t)idx + c] = u[c];
+                if (GRAD) {
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) out_grad[9 * (size_t)idx + k] = g[k];
+                }
+            }
+        }
+        __syncthreads();                                  // s_rank / s_order reused by the next chunk
     }
 }
 
@@ -169,20 +295,19 @@ template <typename K> int set_smem(K kernel, size_t bytes) {
 template <int ORD, typename CT, typename AT, typename TR>
 int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, void* out_u, void* out_grad,
                bool grad) {
-    constexpr int E = tile_edge<ORD>();
-    const size_t sm = sizeof(CT) * 3 * (size_t)E * E * E;
+    const size_t sm = tile_bytes<ORD, CT>();
     const AT dscale = (AT)((double)p->N / p->L);
     int rc;
-    if (grad) {
-        auto k = gather_kernel<ORD, CT, AT, TR, true>;
+    if constexpr (sizeof(AT) == 8) {
+        auto k = grad ? gather_f64<ORD, TR, true> : gather_f64<ORD, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, nbx, w, (AT*)out_u, (AT*)out_grad,
-                                      dscale);
+        k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const double*>(coeffs), p->N, nbx, w, (double*)out_u,
+                                      grad ? (double*)out_grad : nullptr, dscale);
     } else {
-        auto k = gather_kernel<ORD, CT, AT, TR, false>;
+        auto k = grad ? gather_f32<ORD, CT, TR, true> : gather_f32<ORD, CT, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, nbx, w, (AT*)out_u, nullptr,
-                                      dscale);
+        k<<<NB, kGatherThreads, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, nbx, w, (float*)out_u,
+                                                 grad ? (float*)out_grad : nullptr, dscale);
     }
     return BSPLINE_OK;
 }
