@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particles/s for u+grad-u (quintic B-spline, 512^3), FP32 vs FP64 form, % HBM peak"
 UNIT = "particles/s"
 WORKLOAD_NAME = "throughput512"
-STAGES = ["fft_x", "fft_y", "fft_z", "bin", "scan", "scatter", "gather"]
+STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather"]
 
 
 def peaks() -> dict:
@@ -48,9 +48,14 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
+_OVERRIDE = {}
+
+
 def workload():
+    """The benchmark workload; --N/--P shrink it for profiling captures only (not bench values)."""
     from paper_1201_4060_gb300 import synth
     wl = dict(synth.WORKLOADS[WORKLOAD_NAME])
+    wl.update(_OVERRIDE)
     return wl
 
 
@@ -142,8 +147,7 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
     rec = 16 if tb == 4 else 32                  # packed record: first node + t per axis
     return {
         "fft_x": 2 * spec,                       # read u_hat, write the x-transformed spectrum
-        "fft_y": 2 * spec,                       # in place
-        "fft_z": spec + coef,                    # read spectrum, write coefficients
+        "fft_yz": spec + coef,                   # read that spectrum, write coefficients (ring stays in L2)
         "bin": P * (24 + 8 + rec),               # positions in; key, rank, record out
         "scan": 2 * 4 * (nb + 1),
         "scatter": P * (8 + rec) + P * (rec + 4),          # key, rank, record in; sorted record, index out
@@ -153,7 +157,7 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
 
 def kernel_source_sha(stage: str) -> str:
     files = {"gather": ["particles.cuh"], "bin": ["particles.cu"], "scan": ["particles.cu"],
-             "scatter": ["particles.cu"], "fft_x": ["fft.cu"], "fft_y": ["fft.cu"], "fft_z": ["fft.cu"]}[stage]
+             "scatter": ["particles.cu"], "fft_x": ["fft.cu"], "fft_yz": ["fft.cu"]}[stage]
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_1201_4060_gb300", "csrc", f), "rb") as fh:
@@ -350,7 +354,7 @@ def run_ours(args):
         ms_64, st_64, _ = run_form(B, wl, F, x, "f64", 2, 1, device)
         g64 = st_64["gather"][0] / max(st_64["gather"][1], 1)
         forms["f64"] = {"particles_per_s": P / (ms_64 / 1e3), "ms_per_step": ms_64, "gather_ms": g64,
-                        "fft_ms": sum(st_64[s][0] / max(st_64[s][1], 1) for s in ("fft_x", "fft_y", "fft_z"))}
+                        "fft_ms": sum(st_64[s][0] / max(st_64[s][1], 1) for s in ("fft_x", "fft_yz"))}
         out["forms"] = forms
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -479,7 +483,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--samples", type=int, default=4096, help=argparse.SUPPRESS)
+    ap.add_argument("--N", type=int, default=None, help="grid size override (profiling captures only)")
+    ap.add_argument("--P", type=int, default=None, help="particle count override (profiling captures only)")
     args = ap.parse_args()
+    if args.N:
+        _OVERRIDE["N"] = args.N
+    if args.P:
+        _OVERRIDE["P"] = args.P
     if args.cpu_worker:
         print(json.dumps(cpu_worker(args.cpu_worker, args.samples, args.steps, args.warmup)))
         return

@@ -126,9 +126,11 @@ int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double
 /* Device workspace bspline_interp needs for P positions. */
 int bspline_workspace_bytes(bspline_plan_t plan, int64_t P, size_t* bytes);
 
-/* Synchronise the plan's stream and report the device status word of the
- * last bspline_interp call: BSPLINE_OK, or BSPLINE_ERR_NONFINITE_INPUT with
- * the count of non-finite positions in *nonfinite (may be NULL). */
+/* Synchronise the plan's stream and report the device status words:
+ * BSPLINE_ERR_TIMEOUT if a bounded wait of the last bspline_coeffs ran out
+ * (its coefficients are then unspecified), else BSPLINE_ERR_NONFINITE_INPUT
+ * if the last bspline_interp met non-finite positions, else BSPLINE_OK.
+ * *nonfinite (may be NULL) receives that count of non-finite positions. */
 int bspline_status(bspline_plan_t plan, int64_t* nonfinite);
 
 /* Whole path with HOST buffers: copies u_hat_host and x_host to plan-owned
@@ -156,16 +158,23 @@ const char* bspline_version(void);
  * the record.  The stage index identifies the kernel: */
 enum {
     BSPLINE_STAGE_FFT_X = 0,    /* prefilter + c2c along kx */
-    BSPLINE_STAGE_FFT_Y = 1,    /* c2c along ky */
-    BSPLINE_STAGE_FFT_Z = 2,    /* c2r along kz, store coefficients */
-    BSPLINE_STAGE_BIN = 3,      /* locate + brick histogram */
-    BSPLINE_STAGE_SCAN = 4,     /* brick offsets */
-    BSPLINE_STAGE_SCATTER = 5,  /* counting-sort scatter */
-    BSPLINE_STAGE_GATHER = 6,   /* weights + stencil contraction */
-    BSPLINE_NSTAGES = 7
+    BSPLINE_STAGE_FFT_YZ = 1,   /* c2c along ky and c2r along kz, store coefficients */
+    BSPLINE_STAGE_BIN = 2,      /* locate + brick histogram */
+    BSPLINE_STAGE_SCAN = 3,     /* brick offsets */
+    BSPLINE_STAGE_SCATTER = 4,  /* counting-sort scatter */
+    BSPLINE_STAGE_GATHER = 5,   /* weights + stencil contraction */
+    BSPLINE_NSTAGES = 6
 };
 int bspline_plan_set_timing(bspline_plan_t plan, int enable);
 int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);
+
+/* Test hooks.  BSPLINE_TEST_DROP_TRANSFORM_SIGNALS makes the ky-transform
+ * items of bspline_coeffs skip their completion signals, so the waits that
+ * depend on them run out after about a second: the kernel then stops, leaves
+ * the coefficients unspecified, and bspline_status reports
+ * BSPLINE_ERR_TIMEOUT.  It exists to test that error path; 0 clears. */
+#define BSPLINE_TEST_DROP_TRANSFORM_SIGNALS 0x1
+int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks);
 
 /* Allocation-free evaluation of u and grad u (no counterpart in the paper: it
  * serves callers, not the method).  Some callers cannot allocate device

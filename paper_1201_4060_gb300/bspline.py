@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "bspline_status_string": (ctypes.c_char_p, [i32]),
         "bspline_version": (ctypes.c_char_p, []),
         "bspline_plan_set_timing": (i32, [vp, i32]),
+        "bspline_plan_set_test_hooks": (i32, [vp, i32]),
         "bspline_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
         "bspline_interp_noalloc": (i32, [vp, i32, i32, i32, ctypes.c_double, vp, i64, vp, vp, i32, vp]),
     }
@@ -164,8 +165,13 @@ def bspline_status_string(code: int) -> str:
     return status_string(code)
 
 
-NSTAGES = 7
-STAGES = ["fft_x", "fft_y", "fft_z", "bin", "scan", "scatter", "gather"]
+NSTAGES = 6
+STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather"]
+TEST_DROP_TRANSFORM_SIGNALS = 0x1
+
+
+def bspline_plan_set_test_hooks(plan: int, hooks: int) -> int:
+    return _load().bspline_plan_set_test_hooks(plan, hooks)
 
 
 def bspline_plan_set_timing(plan: int, enable: int) -> int:
@@ -274,10 +280,14 @@ class Plan:
         return (out_u, out_grad) if grad else out_u
 
     def status(self) -> int:
+        """Count of non-finite positions of the last interp; raises if the last transform timed out."""
         rc, n = bspline_status(self.handle)
         if rc not in (OK, ERR_NONFINITE_INPUT):
             raise BSplineError(rc, "bspline_status")
         return n
+
+    def set_test_hooks(self, hooks: int) -> None:
+        _check(bspline_plan_set_test_hooks(self.handle, hooks), "bspline_plan_set_test_hooks")
 
     def set_timing(self, enable: bool) -> None:
         _check(bspline_plan_set_timing(self.handle, 1 if enable else 0), "bspline_plan_set_timing")

@@ -251,6 +251,7 @@ int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype) {
     p->dtype = dtype;
     p->L = 2.0 * kPi;
     cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_c64, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_c32, sizeof(float) * N);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw64, sizeof(double2) * N);
@@ -356,7 +357,14 @@ int bspline_status(bspline_plan_t plan, int64_t* nonfinite) {
     if (e == cudaSuccess) e = cudaMemcpy(h, plan->d_status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(e);
     if (nonfinite) *nonfinite = (int64_t)h[0];
+    if (h[1]) return BSPLINE_ERR_TIMEOUT;
     return h[0] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
+}
+
+int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {
+    if (!valid_plan(plan) || (hooks & ~BSPLINE_TEST_DROP_TRANSFORM_SIGNALS)) return BSPLINE_ERR_INVALID_ARG;
+    plan->test_hooks = hooks;
+    return BSPLINE_OK;
 }
 
 int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P, void* u_host,

@@ -5,18 +5,20 @@
 // negligible next to the transform (Section 8), so it is fused into the first
 // pass's load.
 //
-// Three passes, each one HBM read + write of the array:
-//   X: per (component, ky, kz-tile): Stockham c2c along kx, prefilter on load;
-//   Y: per (component, x, kz-tile):  Stockham c2c along ky, in place;
-//   Z: per (component, x, y) row:    c2r along kz via a half-length complex
-//      transform (even/odd outputs packed as real/imaginary parts), output
-//      rounded to the coefficient type on store.
+// Two kernels, each one HBM read + write of the array:
+//   X:  per (component, 16 batch columns): Stockham c2c along kx, prefilter on load;
+//   YZ: per (component, x) plane: Stockham c2c along ky into an L2-resident
+//       ring of planes, then c2r along kz via a half-length complex transform
+//       (even/odd outputs packed as real/imaginary parts), output rounded to
+//       the coefficient type on store.
 // Each CTA holds a tile of lines in shared memory in a [position][line+1]
 // layout (line index fastest, one complex of padding per row), so that global
 // loads and stores are coalesced along contiguous lines and every butterfly
 // read/write is bank-conflict free.  Radix-8/4/2 Stockham stages, fully
 // unrolled per transform length; twiddles exp(+2 pi i m / N) from a table
 // computed on the host in FP64.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace bs {
@@ -172,36 +174,6 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
     }
 }
 
-// ---------------------------------------------------------------- pass Y
-// Lines along ky (stride H); batch along kz (contiguous), ragged last tile.
-template <typename R, int N, int NL>
-__global__ void __launch_bounds__(threads_for<N, NL>())
-fft_y(typename Cx<R>::T* __restrict__ data, const typename Cx<R>::T* __restrict__ tw, int H) {
-    using V = typename Cx<R>::T;
-    constexpr int T = threads_for<N, NL>();
-    constexpr int QS = NL + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* tws = reinterpret_cast<V*>(smem_raw);
-    V* s = tws + N;
-    const int t = threadIdx.x;
-    const int tpz = (H + NL - 1) / NL;
-    const int kz0 = (int)(blockIdx.x % tpz) * NL;
-    const long long line = blockIdx.x / tpz;                    // component * N + x
-    V* base = data + line * N * H + kz0;
-    for (int m = t; m < N; m += T) tws[m] = tw[m];
-    for (int e = t; e < N * NL; e += T) {
-        const int q = e / NL, b = e % NL;
-        s[q * QS + b] = (kz0 + b < H) ? base[(long long)q * H + b] : mk<V>(0, 0);
-    }
-    __syncthreads();
-    fft_smem<V, N, NL, T, QS>(s, tws, 1);
-    for (int e = t; e < N * NL; e += T) {
-        const int q = e / NL, b = e % NL;
-        if (kz0 + b < H) base[(long long)q * H + b] = s[q * QS + b];
-    }
-}
-
-// ---------------------------------------------------------------- pass Z
 template <typename OutT, typename V> __device__ __forceinline__ void store_pair(OutT* p, V z);
 template <> __device__ __forceinline__ void store_pair<double, double2>(double* p, double2 z) {
     *reinterpret_cast<double2*>(p) = z;
@@ -213,54 +185,151 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(z.x, z.y);
 }
 
-// c2r of rows of H = N/2 + 1 complex along kz.  With M = N/2 and
-// X[M + k] = conj(X[M - k]) (X[M] itself for k = 0), E[k] = X[k] + X[M + k]
-// and O[k] = (X[k] - X[M + k]) exp(2 pi i k / N) have the even and odd
-// outputs as their length-M inverse transforms; one complex transform of
-// Z = E + i O gives z[m] = x[2m] + i x[2m + 1].  Only the real parts of X[0]
-// and X[M] enter (real-to-complex semantics).
-template <typename R, typename OutT, int N, int NR>
-__global__ void __launch_bounds__(threads_for<N / 2, NR>())
-fft_z_c2r(const typename Cx<R>::T* __restrict__ in, OutT* __restrict__ out,
-          const typename Cx<R>::T* __restrict__ tw, int H) {
+
+// c2r along kz (Z items below): with M = N/2 and X[M + k] = conj(X[M - k])
+// (X[M] itself for k = 0), E[k] = X[k] + X[M + k] and
+// O[k] = (X[k] - X[M + k]) exp(2 pi i k / N) have the even and odd outputs as
+// their length-M inverse transforms; one complex transform of Z = E + i O
+// gives z[m] = x[2m] + i x[2m + 1].  Only the real parts of X[0] and X[M]
+// enter (real-to-complex semantics).
+
+// ---------------------------------------------------------------- passes Y + Z fused
+// One persistent kernel does the ky transform and the kz c2r of every
+// (component, x) plane, handing each plane from one to the other through a
+// ring of kRing plane buffers small enough to stay in L2 (kRing x N x H
+// complex, 16.8 MB at N = 512 FP32), so the intermediate spectrum never makes
+// a round trip through HBM.  Work items are taken in order from a global
+// counter: per plane, ceil(H / NL) "Y" items (NL kz columns, all ky) then
+// N / NR "Z" items (NR rows y, all kz).  A Z item waits until all Y items of
+// its plane have been stored; a Y item waits until the Z items that last used
+// its ring slot have read it.  Every dependency points to an earlier item,
+// taken by a CTA that is already running, so the waits end; each wait is
+// still bounded (about a second) and, if it runs out, sets the error word and
+// the kernel returns.
+constexpr int kRing = 16;
+constexpr long long kWaitLimit = 1LL << 22;
+
+// Counters of one launch (zeroed before it): [0] = work-item counter, then per
+// plane the number of finished Y items, then per plane the finished Z items.
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 waits until *flag >= target (bounded); returns false for the whole CTA on error.
+__device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, unsigned* error, unsigned* s_ok) {
+    if (threadIdx.x == 0) {
+        unsigned ok = 1;
+        long long it = 0;
+        while (ld_acquire(flag) < target) {
+            if (ld_acquire(error) != 0u) { ok = 0; break; }
+            if (++it > kWaitLimit) {
+                atomicExch(error, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(200);
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0u;
+}
+
+template <typename V> __device__ __forceinline__ V ld_l2(const V* p) { return __ldcg(p); }
+
+template <typename R, typename OutT, int N, int NL>
+__global__ void __launch_bounds__(threads_for<N, NL>())
+fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
+             const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int drop_signals) {
     using V = typename Cx<R>::T;
+    constexpr int T = threads_for<N, NL>();
+    constexpr int H = N / 2 + 1;
     constexpr int M = N / 2;
-    constexpr int T = threads_for<M, NR>();
-    constexpr int QS = NR + 1;
+    constexpr int NR = (2 * NL < N) ? 2 * NL : N;       // Z rows per item: same thread count as a Y item
+    constexpr int QY = NL + 1, QZ = NR + 1;
+    constexpr int TPZ = (H + NL - 1) / NL;              // Y items per plane
+    constexpr int ZPP = N / NR;                         // Z items per plane
+    constexpr int IPP = TPZ + ZPP;
+    constexpr long long PLANES = 3LL * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* s = tws + N;
+    __shared__ unsigned s_item, s_ok;
+    unsigned* next = ctr;
+    unsigned* done_y = ctr + 1;
+    unsigned* done_z = ctr + 1 + PLANES;
     const int t = threadIdx.x;
-    const long long r0 = (long long)blockIdx.x * NR;
     for (int m = t; m < N; m += T) tws[m] = tw[m];
-    __syncthreads();
-    for (int e = t; e < NR * M; e += T) {
-        const int b = e / M, k = e % M;
-        const V* row = in + (r0 + b) * H;
-        V z;
-        if (k == 0) {
-            const R x0 = row[0].x, xm = row[M].x;
-            z = mk<V>(x0 + xm, x0 - xm);
+    for (;;) {
+        if (t == 0) s_item = (ld_acquire(error) != 0u) ? 0xffffffffu : atomicAdd(next, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        __syncthreads();
+        if (item >= (unsigned)(PLANES * IPP)) return;
+        const long long pl = item / IPP;
+        const int r = (int)(item % IPP);
+        V* slot = ring + (pl % kRing) * (long long)N * H;
+        if (r < TPZ) {
+            // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
+            if (pl >= kRing && !cta_wait(&done_z[pl - kRing], (unsigned)ZPP, error, &s_ok)) return;
+            const int kz0 = r * NL;
+            const V* src = w + pl * N * H + kz0;
+            for (int e = t; e < N * NL; e += T) {
+                const int q = e / NL, b = e % NL;
+                s[q * QY + b] = (kz0 + b < H) ? src[(long long)q * H + b] : mk<V>(0, 0);
+            }
+            __syncthreads();
+            fft_smem<V, N, NL, T, QY>(s, tws, 1);
+            for (int e = t; e < N * NL; e += T) {
+                const int q = e / NL, b = e % NL;
+                if (kz0 + b < H) slot[(long long)q * H + kz0 + b] = s[q * QY + b];
+            }
+            __syncthreads();
+            if (t == 0 && !drop_signals) {
+                __threadfence();
+                atomicAdd(&done_y[pl], 1u);
+            }
         } else {
-            const V a = row[k];
-            const V c = row[M - k];
-            const V bb = mk<V>(c.x, -c.y);
-            const V E = cadd(a, bb);
-            const V O = cmul(csub(a, bb), tws[k]);
-            z = mk<V>(E.x - O.y, E.y + O.x);
+            // ---- Z item: rows y0..y0+NR-1 of the plane, c2r along kz (see fft_z_c2r)
+            if (!cta_wait(&done_y[pl], (unsigned)TPZ, error, &s_ok)) return;
+            const int y0 = (r - TPZ) * NR;
+            for (int e = t; e < NR * M; e += T) {
+                const int b = e / M, k = e % M;
+                const V* row = slot + (long long)(y0 + b) * H;
+                V z;
+                if (k == 0) {
+                    const R x0 = ld_l2(row).x, xm = ld_l2(row + M).x;
+                    z = mk<V>(x0 + xm, x0 - xm);
+                } else {
+                    const V a = ld_l2(row + k);
+                    const V c = ld_l2(row + M - k);
+                    const V bb = mk<V>(c.x, -c.y);
+                    const V E = cadd(a, bb);
+                    const V O = cmul(csub(a, bb), tws[k]);
+                    z = mk<V>(E.x - O.y, E.y + O.x);
+                }
+                s[k * QZ + b] = z;
+            }
+            __syncthreads();                            // the slot's rows are read: release it
+            if (t == 0) {
+                __threadfence();
+                atomicAdd(&done_z[pl], 1u);
+            }
+            fft_smem<V, M, NR, T, QZ>(s, tws, 2);
+            OutT* dst = out + (pl * N + y0) * (long long)N;
+            for (int e = t; e < NR * M; e += T) {
+                const int b = e / M, m = e % M;
+                store_pair<OutT, V>(dst + (long long)b * N + 2 * m, s[m * QZ + b]);
+            }
+            __syncthreads();                            // s is reused by the next item
         }
-        s[k * QS + b] = z;
-    }
-    __syncthreads();
-    fft_smem<V, M, NR, T, QS>(s, tws, 2);
-    for (int e = t; e < NR * M; e += T) {
-        const int b = e / M, m = e % M;
-        store_pair<OutT, V>(out + (r0 + b) * N + 2 * m, s[m * QS + b]);
     }
 }
 
 template <typename R> constexpr int lines_x() { return sizeof(R) == 4 ? 16 : 8; }
-constexpr int kRowsZ = 16;
 
 template <typename K> int set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) {
@@ -296,22 +365,33 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         k<<<(unsigned)(3 * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw, H);
     }
     {
-        auto k = fft_y<R, N, NLX>;
-        const size_t sm = sizeof(V) * (N + (size_t)N * (NLX + 1));
+        auto k = fft_yz_fused<R, OutT, N, NLX>;
+        constexpr int NR = (2 * NLX < N) ? 2 * NLX : N;
+        constexpr int T = threads_for<N, NLX>();
+        const size_t tile = std::max((size_t)N * (NLX + 1), (size_t)(N / 2) * (NR + 1));
+        const size_t sm = sizeof(V) * (N + tile);
         if ((rc = set_smem(k, sm))) return rc;
-        const long long blocks = 3LL * N * ((H + NLX - 1) / NLX);
-        StageTimer tm(p, BSPLINE_STAGE_FFT_Y);
-        k<<<(unsigned)blocks, threads_for<N, NLX>(), sm, st>>>(w, tw, H);
-    }
-    {
-        auto k = fft_z_c2r<R, OutT, N, kRowsZ>;
-        const size_t sm = sizeof(V) * (N + (size_t)(N / 2) * (kRowsZ + 1));
-        if ((rc = set_smem(k, sm))) return rc;
-        const long long rows = 3LL * N * N;
-        StageTimer tm(p, BSPLINE_STAGE_FFT_Z);
-        k<<<(unsigned)(rows / kRowsZ), threads_for<N / 2, kRowsZ>(), sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), tw, H);
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, sm);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        const long long items = 3LL * N * ((H + NLX - 1) / NLX + N / NR);
+        const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
+        V* ring = w + 3LL * N * N * H;
+        unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRing * N * H);
+        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 6LL * N), st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        StageTimer tm(p, BSPLINE_STAGE_FFT_YZ);
+        k<<<(unsigned)grid, T, sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), ring, tw, ctr,
+                                         reinterpret_cast<unsigned*>(p->d_status + 1),
+                                         (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0);
     }
     return set_cuda_error(cudaGetLastError());
+}
+
+// Workspace of the transform: the x-transformed spectrum, the plane ring and the counters.
+template <typename V> size_t transform_workspace(int N) {
+    const size_t H = N / 2 + 1;
+    return sizeof(V) * (3ull * N * N * H + (size_t)kRing * N * H) + sizeof(unsigned) * (1 + 6ull * N);
 }
 
 template <int N> int run_n(bspline_plan_s* p, const void* u_hat, void* coeffs) {
@@ -326,10 +406,11 @@ template <int N> int run_n(bspline_plan_s* p, const void* u_hat, void* coeffs) {
 }  // namespace
 
 int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs) {
-    const size_t csz = p->dtype == BSPLINE_F64 ? sizeof(double2) : sizeof(float2);
-    const size_t need = csz * 3 * (size_t)p->N * p->N * (p->N / 2 + 1);
+    const size_t need = p->dtype == BSPLINE_F64 ? transform_workspace<double2>(p->N) : transform_workspace<float2>(p->N);
     int rc = p->work.grow(need);
     if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(unsigned long long), p->stream);
+    if (e != cudaSuccess) return set_cuda_error(e);
     switch (p->N) {
         case 8: return run_n<8>(p, u_hat, coeffs);
         case 16: return run_n<16>(p, u_hat, coeffs);

@@ -54,8 +54,11 @@ struct bspline_plan_s {
     bs::DeviceBuffer work;
     // Particle workspace (binning, sort, sorted particle records).
     bs::DeviceBuffer pws;
-    // Device status word: [0] = count of non-finite positions of the last interp.
+    // Device status words: [0] = count of non-finite positions of the last
+    // interp; [1] = nonzero if a bounded wait of the last transform ran out.
     unsigned long long* d_status = nullptr;
+    int sms = 1;            // streaming multiprocessors of the plan's device
+    int test_hooks = 0;     // BSPLINE_TEST_* flags
     // Buffers of bspline_run_host.
     bs::DeviceBuffer host_uhat, host_coef, host_x, host_u, host_grad;
     // Per-kernel timing (bspline_plan_set_timing): event pairs recorded on the

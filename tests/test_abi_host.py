@@ -66,3 +66,4 @@ def test_null_plan_is_rejected_everywhere():
     assert B.bspline_spread_adjoint(0, 0, 0, 0, 0, 0, 0, 0, 0) == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_timing(0, 1) == B.ERR_INVALID_ARG
     assert B.bspline_stage_times(0)[0] == B.ERR_INVALID_ARG
+    assert B.bspline_plan_set_test_hooks(0, 1) == B.ERR_INVALID_ARG

@@ -223,6 +223,26 @@ def test_abi_rejects_bad_arguments_on_gpu(B):
     assert B.bspline_plan_set_length(h, -1.0) == B.ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_transform_wait_timeout_is_reported_and_context_survives(B, dtype):
+    """A bounded wait of the transform runs out (its producer signals are dropped by a test hook):
+    bspline_status reports TIMEOUT, and the next transform on the same plan is correct."""
+    N, order = 64, 4
+    half = synth.kolmogorov_field(N, seed=13).dense()
+    plan = B.Plan(N, order, dtype)
+    uh = torch.from_numpy(half).to(plan.uhat_dtype).cuda()
+    plan.set_test_hooks(B.TEST_DROP_TRANSFORM_SIGNALS)
+    plan.coeffs(uh)
+    rc, _ = B.bspline_status(plan.handle)
+    assert rc == B.ERR_TIMEOUT
+    plan.set_test_hooks(0)
+    coef = plan.coeffs(uh)
+    rc, _ = B.bspline_status(plan.handle)
+    assert rc == B.OK
+    ref = O.coefficients(rounded_input(half, dtype), order)
+    assert normwise(coef.double().cpu().numpy(), ref) < (TOL64 if dtype == "f64" else 2e-6)
+
+
 def test_run_host_matches_device_path(B):
     N, order = 32, 4
     half = synth.kolmogorov_field(N, seed=8).dense().astype(np.complex64)
