@@ -101,28 +101,47 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
 }
 
 // ------------------------------------------------------------------ scan (single CTA)
+// Exclusive prefix sums over the NB + 1 bins (NB bricks, then the invalid
+// bin): offset[] of the counts, and chunk[] (bricks only) of the number of
+// gather work items per brick, ceil(count / kChunk).
 __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
-                                                    unsigned n) {
-    __shared__ unsigned part[1024];
+                                                    unsigned* __restrict__ chunk, unsigned NB) {
+    __shared__ unsigned part[1024], partc[1024];
+    const unsigned n = NB + 1;
     const unsigned t = threadIdx.x;
-    const unsigned chunk = (n + 1023) / 1024;
-    const unsigned b = min(n, t * chunk), e = min(n, b + chunk);
-    unsigned s = 0;
-    for (unsigned i = b; i < e; ++i) s += count[i];
+    const unsigned per = (n + 1023) / 1024;
+    const unsigned b = min(n, t * per), e = min(n, b + per);
+    unsigned s = 0, sc = 0;
+    for (unsigned i = b; i < e; ++i) {
+        const unsigned ci = count[i];
+        s += ci;
+        if (i < NB) sc += (ci + kChunk - 1) / kChunk;
+    }
     part[t] = s;
+    partc[t] = sc;
     __syncthreads();
     for (unsigned d = 1; d < 1024; d <<= 1) {
-        unsigned v = (t >= d) ? part[t - d] : 0;
+        const unsigned v = (t >= d) ? part[t - d] : 0;
+        const unsigned vc = (t >= d) ? partc[t - d] : 0;
         __syncthreads();
         part[t] += v;
+        partc[t] += vc;
         __syncthreads();
     }
-    unsigned run = part[t] - s;         // exclusive
+    unsigned run = part[t] - s, runc = partc[t] - sc;      // exclusive
     for (unsigned i = b; i < e; ++i) {
+        const unsigned ci = count[i];
         offset[i] = run;
-        run += count[i];
+        run += ci;
+        if (i < NB) {
+            chunk[i] = runc;
+            runc += (ci + kChunk - 1) / kChunk;
+        }
     }
-    if (t == 1023) offset[n] = part[1023];
+    if (t == 1023) {
+        offset[n] = part[1023];
+        chunk[NB] = partc[1023];
+    }
 }
 
 // ------------------------------------------------------------------ scatter
@@ -192,7 +211,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, NB + 1);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
@@ -224,7 +243,7 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx,
                                                      bshift, NB, w, status);
-    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, NB + 1);
+    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
     if (rc) return rc;

@@ -18,9 +18,15 @@ template <typename TR> struct __align__(16) Rec {
     TR t[3];
 };
 
+// Particles per gather work item: a brick with more particles is split into
+// several items, each staging the brick's tile, so no CTA serialises a clump.
+constexpr unsigned kChunk = 1024;
+
 template <typename TR> struct Ws {
     unsigned* count;    // [NB + 1]  particles per brick; slot NB = invalid positions
     unsigned* offset;   // [NB + 2]  exclusive prefix sum of count
+    unsigned* chunk;    // [NB + 1]  exclusive prefix sum of ceil(count / kChunk): first work item of a brick
+    long long P;        // particles
     unsigned* key;      // [P]
     unsigned* rank;     // [P]
     Rec<TR>* rec;       // [P]       located records in input order
@@ -37,8 +43,10 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
         off += align_up(bytes);
         return ptr;
     };
+    w->P = P;
     w->count = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 2));
+    w->chunk = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->key = (unsigned*)take(sizeof(unsigned) * P);
     w->rank = (unsigned*)take(sizeof(unsigned) * P);
     w->rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
@@ -96,20 +104,53 @@ constexpr size_t tile_bytes() {
     return sizeof(typename TileT<CT>::T) * 3 * (size_t)tile_edge<ORD, CT>() * tile_edge<ORD, CT>() * tile_edge<ORD, CT>();
 }
 
-constexpr int kGatherThreads = 256;
-constexpr int kChunk = 1024;          // particles bucketed together (FP32 path)
+constexpr int kGatherThreads = 384;
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy the brick's tile into shared memory, one z-row of E nodes per warp
+// step: lane = z offset (lanes >= E idle), so each step reads E consecutive
+// coefficients and writes E consecutive tile entries.  Rows are walked in
+// (c, ix, iy) order with incremental global addresses; indices wrap
+// periodically.  Same-type coefficients go through cp.async (no register
+// round trip); BF16 is widened to FP32 through registers.  The caller
+// synchronises the CTA after cp_async_wait_all.
 template <int ORD, typename CT>
 __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                            int y0, int z0) {
+    using TT = typename TileT<CT>::T;
     constexpr int E = tile_edge<ORD, CT>();
-    constexpr int E3 = E * E * E;
+    static_assert(E <= 32, "one z-row per warp step");
     const int msk = N - 1;
-    for (int e = threadIdx.x; e < 3 * E3; e += blockDim.x) {
-        const int c = e / E3, r = e - c * E3;
-        const int ix = r / (E * E), iy = (r / E) % E, iz = r % E;
-        const size_t g = (((size_t)c * N + ((x0 + ix) & msk)) * N + ((y0 + iy) & msk)) * N + ((z0 + iz) & msk);
-        tile[e] = widen<CT>(coef[g]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane >= E) return;
+    const int gz = (z0 + lane) & msk;
+    // planes (c, ix): E * 3 of them, each E rows along y; warps take planes round-robin
+    for (int pl = warp; pl < 3 * E; pl += nw) {
+        const int c = pl / E, ix = pl - c * E;
+        const CT* src = coef + ((size_t)c * N + ((x0 + ix) & msk)) * (size_t)N * N + gz;
+        TT* dst = tile + (size_t)pl * E * E + lane;
+        int gy = y0;
+#pragma unroll 7
+        for (int iy = 0; iy < E; ++iy, ++gy) {
+            const CT* s = src + (size_t)(gy & msk) * N;
+            if constexpr (sizeof(CT) == sizeof(TT)) {
+                if constexpr (sizeof(CT) == 4) cp_async4(dst + iy * E, s);
+                else cp_async8(dst + iy * E, s);
+            } else {
+                dst[iy * E] = widen<CT>(*s);
+            }
+        }
     }
 }
 
@@ -176,6 +217,7 @@ gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __
     if (beg == end) return;
     const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
     stage_tile<ORD, double>(tile, coef, N, x0, y0, z0);
+    cp_async_wait_all();
     __syncthreads();
     for (unsigned i = beg + threadIdx.x; i < end; i += blockDim.x) {
         const Rec<TR> rc = w.s_rec[i];
@@ -203,9 +245,12 @@ gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __
 // particles are bucketed by the bank of their origin (residue mod 32) and
 // job j takes the j-th particle of every bucket.  Every load of a job is then
 // conflict-free; the number of jobs is the largest bucket.
+// One CTA per work item: item i is chunk i - chunk[b] of the brick b with
+// chunk[b] <= i < chunk[b + 1] (at most kChunk particles); the grid is an
+// upper bound on the number of items and surplus CTAs return at once.
 template <int ORD, typename CT, typename TR, bool GRAD>
 __global__ void __launch_bounds__(kGatherThreads)
-gather_f32(const CT* __restrict__ coef, int N, int nbx, Ws<TR> w, float* __restrict__ out_u,
+gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, float* __restrict__ out_u,
            float* __restrict__ out_grad, float dscale) {
     constexpr int B = brick_edge(BSPLINE_F32);
     constexpr int E = tile_edge<ORD, CT>();
@@ -215,15 +260,24 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, Ws<TR> w, float* __restr
     __shared__ unsigned s_bucket[32];
     __shared__ unsigned short s_rank[kChunk];
     __shared__ unsigned short s_order[kChunk];
-    const unsigned brick = blockIdx.x;
-    const unsigned beg = w.offset[brick], end = w.offset[brick + 1];
-    if (beg == end) return;
+    const unsigned item = blockIdx.x;
+    if (item >= w.chunk[NB]) return;
+    unsigned lo_b = 0, hi_b = NB;                         // largest b with chunk[b] <= item
+    while (hi_b - lo_b > 1) {
+        const unsigned mid = (lo_b + hi_b) >> 1;
+        if (w.chunk[mid] <= item) lo_b = mid;
+        else hi_b = mid;
+    }
+    const unsigned brick = lo_b;
+    const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * kChunk;
+    const unsigned end = w.offset[brick + 1];
     const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
     stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (unsigned c0 = beg; c0 < end; c0 += kChunk) {
-        const int n = (int)min((unsigned)kChunk, end - c0);
+    {
+        const int n = (int)min(kChunk, end - c0);
         if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
+        cp_async_wait_all();
         __syncthreads();                                  // also orders the tile staging before first use
         for (int i = threadIdx.x; i < n; i += kGatherThreads) {
             const unsigned cp = w.s_rec[c0 + i].cell;
@@ -280,7 +334,6 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, Ws<TR> w, float* __restr
                 }
             }
         }
-        __syncthreads();                                  // s_rank / s_order reused by the next chunk
     }
 }
 
@@ -306,8 +359,10 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int
     } else {
         auto k = grad ? gather_f32<ORD, CT, TR, true> : gather_f32<ORD, CT, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<NB, kGatherThreads, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, nbx, w, (float*)out_u,
-                                                 grad ? (float*)out_grad : nullptr, dscale);
+        // work items: at most one partial chunk per brick plus P / kChunk full ones
+        const long long items = (long long)NB + (w.P + kChunk - 1) / kChunk;
+        k<<<(unsigned)items, kGatherThreads, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, nbx, NB, w,
+                                                              (float*)out_u, grad ? (float*)out_grad : nullptr, dscale);
     }
     return BSPLINE_OK;
 }
