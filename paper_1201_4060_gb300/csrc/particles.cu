@@ -30,30 +30,56 @@ namespace {
 using namespace gather_impl;
 
 // ------------------------------------------------------------------ bin
-// For 0 <= sh < 2^52: floor(sh) and the fraction sh - floor(sh) rounded to
-// float, read off the bits of the double with integer operations (GB300's
-// FP64 pipe is narrow; only the multiply and the shift by n/2 stay in FP64).
-// Returns false outside that range.
-__device__ __forceinline__ bool split_nonneg(double sh, long long* fl, float* t) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(sh);
+// For 0 <= s < 2^52: base = floor(s - n/2) and t = (s - n/2) - base rounded to
+// float, computed exactly from the bits of s with integer operations (GB300's
+// FP64 pipe is narrow: only s = x N / L stays in FP64).  s = fl + fr 2^-sa
+// with integer fl and an sa-bit fraction fr; for odd n the half is folded
+// into the fraction.  Returns false outside that range.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
+
+__device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, float* t) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
     if (b >> 63) return false;                                 // negative
     const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
     if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
     const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
-    if (e < 0) {                                               // [0, 1): floor 0, fraction sh
-        *fl = 0;
-        // below 2^-60 (or subnormal) the fraction is 0 to FP32 accuracy of the weights
-        *t = (e < -60) ? 0.f : __ull2float_rn(m) * __int_as_float((127 + e - 52) << 23);
+    const long long hfl = n >> 1;                              // floor(n / 2)
+    if (e < 0) {                                               // s in [0, 1)
+        // below 2^-60 (or subnormal) s is 0 to the FP32 accuracy of the weights
+        const float sf = (e < -60) ? 0.f : __ull2float_rn(m) * pow2f(e - 52);
+        if (!(n & 1)) {
+            *base = -hfl;
+            *t = sf;
+        } else if (e == -1) {                                  // s in [0.5, 1): s - 1/2 = (m - 2^52) 2^-53
+            *base = -hfl;
+            *t = __ull2float_rn(m - (1ULL << 52)) * pow2f(-53);
+        } else {                                               // s in [0, 0.5)
+            *base = -hfl - 1;
+            *t = sf + 0.5f;
+        }
         return true;
     }
     const int sa = 52 - e;                                     // fraction bits, 1..52
-    *fl = (long long)(m >> sa);
-    *t = __ull2float_rn(m & ((1ULL << sa) - 1)) * __int_as_float((127 - sa) << 23);
+    const long long fl = (long long)(m >> sa);
+    const unsigned long long fr = m & ((1ULL << sa) - 1);
+    if (!(n & 1)) {
+        *base = fl - hfl;
+        *t = __ull2float_rn(fr) * pow2f(-sa);
+    } else {
+        const unsigned long long hb = 1ULL << (sa - 1);        // one half in the fraction's units
+        if (fr >= hb) {
+            *base = fl - hfl;
+            *t = __ull2float_rn(fr - hb) * pow2f(-sa);
+        } else {
+            *base = fl - hfl - 1;
+            *t = __ull2float_rn(fr + hb) * pow2f(-sa);
+        }
+    }
     return true;
 }
 
 template <typename TR>
-__global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, double half,
+__global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                            int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
@@ -63,16 +89,16 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double s = x[3 * p + a] * scale;
-            const double sh = s - half;
             if constexpr (sizeof(TR) == 4) {
-                long long fl;
+                long long base;
                 float tf;
-                if (split_nonneg(sh, &fl, &tf)) {
+                if (locate_nonneg(s, order, &base, &tf)) {
                     tt[a] = tf;
-                    anc[a] = (unsigned)((fl + 1) & (long long)(N - 1));
+                    anc[a] = (unsigned)((base + 1) & (long long)(N - 1));
                     continue;
                 }
             }
+            const double sh = s - 0.5 * order;
             if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
                 ok = false;
                 anc[a] = 0;
@@ -206,7 +232,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx,
+        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
                                                          bshift, NB, w, p->d_status);
     }
     {
@@ -241,7 +267,7 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
-    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, 0.5 * p->order, nbx,
+    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
                                                      bshift, NB, w, status);
     scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
