@@ -3,17 +3,21 @@
 // Section 7: the coefficients follow from F_D[u_B](k) = c(kx) c(ky) c(kz) F_D[u](k)
 // (Eq. B_spline_multiplication_3d) and one inverse transform; the multiply is
 // negligible next to the transform (Section 8), so it is fused into the first
-// pass's load.
+// pass.
 //
 // Two kernels, each one HBM read + write of the array:
-//   X:  per (component, 16 batch columns): Stockham c2c along kx, prefilter on load;
-//   YZ: per (component, x) plane: Stockham c2c along ky into an L2-resident
-//       ring of planes, then c2r along kz via a half-length complex transform
-//       (even/odd outputs packed as real/imaginary parts), output rounded to
-//       the coefficient type on store.
-// Each CTA holds a tile of lines in shared memory in a [position][line+1]
-// layout (line index fastest, one complex of padding per row), so that global
-// loads and stores are coalesced along contiguous lines and every butterfly
+//   X:  per (component, NL batch columns): Stockham c2c along kx, prefilter
+//       applied to the staged tile; output spectrum with rows padded to a
+//       multiple of 8 complex (64 bytes);
+//   YZ: per (component, x) plane: Stockham c2c along ky into a ring of plane
+//       buffers small enough to stay in L2, then c2r along kz via a
+//       half-length complex transform (even/odd outputs packed as real and
+//       imaginary parts), rounded to the coefficient type on store.
+// Tiles move between global and shared memory with cp.async, so the data in
+// flight occupies shared memory rather than registers and several CTAs per SM
+// keep loads outstanding while others compute.  In shared memory a tile is
+// [position][line + 1] (line index fastest, one complex of padding per row):
+// global accesses are coalesced along contiguous lines and every butterfly
 // read/write is bank-conflict free.  Radix-8/4/2 Stockham stages, fully
 // unrolled per transform length; twiddles exp(+2 pi i m / N) from a table
 // computed on the host in FP64.
@@ -127,50 +131,88 @@ template <int L, int NL> constexpr int threads_for() {
     return (L * NL / 16) < 32 ? 32 : (L * NL / 16);
 }
 
+// Lines per tile: 8 complex float (64-byte row segments), 4 complex double.
+template <typename R> constexpr int tile_lines() { return sizeof(R) == 4 ? 8 : 4; }
+// Row pitch (complex elements) of the x-transformed spectrum and of the ring:
+// H = N/2 + 1 rounded up to a multiple of 8, so every row starts 64-byte aligned.
+constexpr int row_pitch(int N) { return ((N / 2 + 1) + 7) & ~7; }
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+// 16 bytes, cached in L2 only: for data another CTA of the same launch wrote.
+__device__ __forceinline__ void cp_async16_l2(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy a tile of NL-element row segments (row stride `pitch` elements) into
+// s[q * QS + b]; elements with b >= valid are zero.
+template <typename V, int ROWS, int NL, int T, int QS>
+__device__ __forceinline__ void load_tile(V* s, const V* __restrict__ src, long long pitch, int valid) {
+#pragma unroll
+    for (int e = threadIdx.x; e < ROWS * NL; e += T) {
+        const int q = e / NL, b = e % NL;
+        if (b < valid) {
+            if constexpr (sizeof(V) == 8) cp_async8(&s[q * QS + b], src + q * pitch + b);
+            else cp_async16(&s[q * QS + b], src + q * pitch + b);
+        } else {
+            s[q * QS + b] = mk<V>(0, 0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- pass X
-// Lines along kx (stride N*H complex); batch index b = ky*H + kz contiguous.
+// Lines along kx (input stride N*H complex); batch index b = ky*H + kz is
+// contiguous in the input.  Output: [3][N(x)][N(ky)][HP] with kz fastest.
 template <typename R, int N, int NL>
 __global__ void __launch_bounds__(threads_for<N, NL>())
 fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __restrict__ out,
-                const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw, int H) {
+                const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int QS = NL + 1;
+    constexpr int H = N / 2 + 1, HP = row_pitch(N);
+    constexpr long long NH = (long long)N * H;
+    constexpr long long TILES = (NH + NL - 1) / NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* s = tws + N;
     R* cyz = reinterpret_cast<R*>(s + N * QS);
     const int t = threadIdx.x;
-    const long long NH = (long long)N * H;
-    const long long tiles = (NH + NL - 1) / NL;
-    const int comp = (int)(blockIdx.x / tiles);
-    const long long b0 = (blockIdx.x % tiles) * NL;
+    const int comp = (int)(blockIdx.x / TILES);
+    const long long b0 = (blockIdx.x % TILES) * NL;
+    const int valid = (int)std::min<long long>(NL, NH - b0);
+    load_tile<V, N, NL, T, QS>(s, in + (long long)comp * N * NH + b0, NH, valid);
     for (int m = t; m < N; m += T) tws[m] = tw[m];
-    if (t < NL) {
-        const long long bb = b0 + t;
-        R f = 0;
-        if (bb < NH) f = c[(int)(bb / H)] * c[(int)(bb % H)];
-        cyz[t] = f;
-    }
+    if (t < NL) cyz[t] = (t < valid) ? c[(int)((b0 + t) / H)] * c[(int)((b0 + t) % H)] : R(0);
+    cp_async_wait_all();
     __syncthreads();
-    const V* src = in + (long long)comp * N * NH + b0;
-    for (int e = t; e < N * NL; e += T) {
+    for (int e = t; e < N * NL; e += T) {                 // prefilter c(kx) c(ky) c(kz)
         const int q = e / NL, b = e % NL;
-        V a = mk<V>(0, 0);
-        if (b0 + b < NH) {
-            a = src[(long long)q * NH + b];
-            const R f = c[q] * cyz[b];
-            a.x *= f;
-            a.y *= f;
-        }
-        s[q * QS + b] = a;
+        const R f = __ldg(&c[q]) * cyz[b];
+        V& a = s[q * QS + b];
+        a = mk<V>(a.x * f, a.y * f);
     }
     __syncthreads();
     fft_smem<V, N, NL, T, QS>(s, tws, 1);
-    V* dst = out + (long long)comp * N * NH + b0;
+    V* dst = out + (long long)comp * N * N * HP;
     for (int e = t; e < N * NL; e += T) {
         const int q = e / NL, b = e % NL;
-        if (b0 + b < NH) dst[(long long)q * NH + b] = s[q * QS + b];
+        if (b < valid) {
+            const long long bb = b0 + b;
+            const int ky = (int)(bb / H), kz = (int)(bb % H);
+            dst[((long long)q * N + ky) * HP + kz] = s[q * QS + b];
+        }
     }
 }
 
@@ -185,19 +227,11 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(z.x, z.y);
 }
 
-
-// c2r along kz (Z items below): with M = N/2 and X[M + k] = conj(X[M - k])
-// (X[M] itself for k = 0), E[k] = X[k] + X[M + k] and
-// O[k] = (X[k] - X[M + k]) exp(2 pi i k / N) have the even and odd outputs as
-// their length-M inverse transforms; one complex transform of Z = E + i O
-// gives z[m] = x[2m] + i x[2m + 1].  Only the real parts of X[0] and X[M]
-// enter (real-to-complex semantics).
-
 // ---------------------------------------------------------------- passes Y + Z fused
 // One persistent kernel does the ky transform and the kz c2r of every
 // (component, x) plane, handing each plane from one to the other through a
-// ring of kRing plane buffers small enough to stay in L2 (kRing x N x H
-// complex, 16.8 MB at N = 512 FP32), so the intermediate spectrum never makes
+// ring of kRing plane buffers small enough to stay in L2 (kRing x N x HP
+// complex, 17.3 MB at N = 512 FP32), so the intermediate spectrum never makes
 // a round trip through HBM.  Work items are taken in order from a global
 // counter: per plane, ceil(H / NL) "Y" items (NL kz columns, all ky) then
 // N / NR "Z" items (NR rows y, all kz).  A Z item waits until all Y items of
@@ -206,6 +240,12 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // taken by a CTA that is already running, so the waits end; each wait is
 // still bounded (about a second) and, if it runs out, sets the error word and
 // the kernel returns.
+//
+// c2r along kz: with M = N/2 and X[M + k] = conj(X[M - k]) (X[M] itself for
+// k = 0), E[k] = X[k] + X[M + k] and O[k] = (X[k] - X[M + k]) exp(2 pi i k / N)
+// have the even and odd outputs as their length-M inverse transforms; one
+// complex transform of Z = E + i O gives z[m] = x[2m] + i x[2m + 1].  Only the
+// real parts of X[0] and X[M] enter (real-to-complex semantics).
 constexpr int kRing = 16;
 constexpr long long kWaitLimit = 1LL << 22;
 
@@ -238,25 +278,36 @@ __device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, 
     return *s_ok != 0u;
 }
 
-template <typename V> __device__ __forceinline__ V ld_l2(const V* p) { return __ldcg(p); }
+template <int N, int NL> constexpr int z_rows() { return (2 * NL < N) ? 2 * NL : N; }
+
+template <typename R, int N, int NL>
+constexpr size_t yz_smem_elems() {
+    constexpr int HP = row_pitch(N), NR = z_rows<N, NL>();
+    constexpr size_t y = (size_t)N * (NL + 1);
+    constexpr size_t z = (size_t)NR * HP + (size_t)(N / 2) * (NR + 1);
+    return N + (y > z ? y : z);
+}
 
 template <typename R, typename OutT, int N, int NL>
-__global__ void __launch_bounds__(threads_for<N, NL>())
+__global__ void __launch_bounds__(threads_for<N, NL>(), 3)
 fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
              const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int drop_signals) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
-    constexpr int H = N / 2 + 1;
+    constexpr int H = N / 2 + 1, HP = row_pitch(N);
     constexpr int M = N / 2;
-    constexpr int NR = (2 * NL < N) ? 2 * NL : N;       // Z rows per item: same thread count as a Y item
+    constexpr int NR = z_rows<N, NL>();                 // Z rows per item: same thread count as a Y item
     constexpr int QY = NL + 1, QZ = NR + 1;
     constexpr int TPZ = (H + NL - 1) / NL;              // Y items per plane
     constexpr int ZPP = N / NR;                         // Z items per plane
     constexpr int IPP = TPZ + ZPP;
     constexpr long long PLANES = 3LL * N;
+    constexpr int CHUNKS = HP * (int)sizeof(V) / 16;    // 16-byte pieces of one ring row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tws = reinterpret_cast<V*>(smem_raw);
-    V* s = tws + N;
+    V* buf = tws + N;                                   // Y: [N][QY] tile
+    V* raw = buf;                                       // Z: NR ring rows, pitch HP
+    V* trans = buf + NR * HP;                           // Z: [M][QZ] transform buffer
     __shared__ unsigned s_item, s_ok;
     unsigned* next = ctr;
     unsigned* done_y = ctr + 1;
@@ -271,21 +322,22 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
         if (item >= (unsigned)(PLANES * IPP)) return;
         const long long pl = item / IPP;
         const int r = (int)(item % IPP);
-        V* slot = ring + (pl % kRing) * (long long)N * H;
+        V* slot = ring + (pl % kRing) * (long long)N * HP;
         if (r < TPZ) {
             // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
-            if (pl >= kRing && !cta_wait(&done_z[pl - kRing], (unsigned)ZPP, error, &s_ok)) return;
             const int kz0 = r * NL;
-            const V* src = w + pl * N * H + kz0;
-            for (int e = t; e < N * NL; e += T) {
-                const int q = e / NL, b = e % NL;
-                s[q * QY + b] = (kz0 + b < H) ? src[(long long)q * H + b] : mk<V>(0, 0);
+            const int valid = std::min(NL, H - kz0);
+            load_tile<V, N, NL, T, QY>(buf, w + pl * N * HP + kz0, HP, valid);
+            if (pl >= kRing && !cta_wait(&done_z[pl - kRing], (unsigned)ZPP, error, &s_ok)) {
+                cp_async_wait_all();                    // no copy of this CTA left in flight
+                return;
             }
+            cp_async_wait_all();
             __syncthreads();
-            fft_smem<V, N, NL, T, QY>(s, tws, 1);
+            fft_smem<V, N, NL, T, QY>(buf, tws, 1);
             for (int e = t; e < N * NL; e += T) {
                 const int q = e / NL, b = e % NL;
-                if (kz0 + b < H) slot[(long long)q * H + kz0 + b] = s[q * QY + b];
+                if (b < valid) slot[(long long)q * HP + kz0 + b] = buf[q * QY + b];
             }
             __syncthreads();
             if (t == 0 && !drop_signals) {
@@ -293,43 +345,44 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
                 atomicAdd(&done_y[pl], 1u);
             }
         } else {
-            // ---- Z item: rows y0..y0+NR-1 of the plane, c2r along kz (see fft_z_c2r)
+            // ---- Z item: rows y0..y0+NR-1 of the plane, c2r along kz
             if (!cta_wait(&done_y[pl], (unsigned)TPZ, error, &s_ok)) return;
             const int y0 = (r - TPZ) * NR;
-            for (int e = t; e < NR * M; e += T) {
-                const int b = e / M, k = e % M;
-                const V* row = slot + (long long)(y0 + b) * H;
-                V z;
-                if (k == 0) {
-                    const R x0 = ld_l2(row).x, xm = ld_l2(row + M).x;
-                    z = mk<V>(x0 + xm, x0 - xm);
-                } else {
-                    const V a = ld_l2(row + k);
-                    const V c = ld_l2(row + M - k);
-                    const V bb = mk<V>(c.x, -c.y);
-                    const V E = cadd(a, bb);
-                    const V O = cmul(csub(a, bb), tws[k]);
-                    z = mk<V>(E.x - O.y, E.y + O.x);
-                }
-                s[k * QZ + b] = z;
-            }
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(slot + (long long)y0 * HP);
+            unsigned char* dstb = reinterpret_cast<unsigned char*>(raw);
+            for (int j = t; j < NR * CHUNKS; j += T) cp_async16_l2(dstb + 16 * j, src + 16 * j);
+            cp_async_wait_all();
             __syncthreads();                            // the slot's rows are read: release it
             if (t == 0) {
                 __threadfence();
                 atomicAdd(&done_z[pl], 1u);
             }
-            fft_smem<V, M, NR, T, QZ>(s, tws, 2);
+            for (int e = t; e < NR * M; e += T) {
+                const int b = e / M, k = e % M;
+                const V* row = raw + b * HP;
+                const V a = row[k], c = row[M - k];     // k = 0: X[0] and X[M]
+                V z;
+                if (k == 0) {
+                    z = mk<V>(a.x + c.x, a.x - c.x);
+                } else {
+                    const V bb = mk<V>(c.x, -c.y);
+                    const V E = cadd(a, bb);
+                    const V O = cmul(csub(a, bb), tws[k]);
+                    z = mk<V>(E.x - O.y, E.y + O.x);
+                }
+                trans[k * QZ + b] = z;
+            }
+            __syncthreads();
+            fft_smem<V, M, NR, T, QZ>(trans, tws, 2);
             OutT* dst = out + (pl * N + y0) * (long long)N;
             for (int e = t; e < NR * M; e += T) {
                 const int b = e / M, m = e % M;
-                store_pair<OutT, V>(dst + (long long)b * N + 2 * m, s[m * QZ + b]);
+                store_pair<OutT, V>(dst + (long long)b * N + 2 * m, trans[m * QZ + b]);
             }
-            __syncthreads();                            // s is reused by the next item
+            __syncthreads();                            // smem is reused by the next item
         }
     }
 }
-
-template <typename R> constexpr int lines_x() { return sizeof(R) == 4 ? 16 : 8; }
 
 template <typename K> int set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) {
@@ -339,11 +392,18 @@ template <typename K> int set_smem(K kernel, size_t bytes) {
     return BSPLINE_OK;
 }
 
+// Workspace of the transform: the x-transformed spectrum, the plane ring and the counters.
+template <typename V> size_t transform_workspace(int N) {
+    const size_t HP = row_pitch(N);
+    return sizeof(V) * (3ull * N * N * HP + (size_t)kRing * N * HP) + sizeof(unsigned) * (1 + 6ull * N);
+}
+
 template <typename R, typename OutT, int N>
 int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
     using V = typename Cx<R>::T;
-    constexpr int NLX = lines_x<R>();
-    const int H = N / 2 + 1;
+    constexpr int NL = tile_lines<R>();
+    constexpr int T = threads_for<N, NL>();
+    constexpr int H = N / 2 + 1, HP = row_pitch(N);
     const R* c = nullptr;
     const V* tw = nullptr;
     if constexpr (sizeof(R) == 8) {
@@ -357,27 +417,25 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
     cudaStream_t st = p->stream;
     int rc;
     {
-        auto k = fft_x_prefilter<R, N, NLX>;
-        const size_t sm = sizeof(V) * (N + (size_t)N * (NLX + 1)) + sizeof(R) * NLX;
+        auto k = fft_x_prefilter<R, N, NL>;
+        const size_t sm = sizeof(V) * (N + (size_t)N * (NL + 1)) + sizeof(R) * NL;
         if ((rc = set_smem(k, sm))) return rc;
-        const long long tiles = ((long long)N * H + NLX - 1) / NLX;
+        const long long tiles = ((long long)N * H + NL - 1) / NL;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);
-        k<<<(unsigned)(3 * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw, H);
+        k<<<(unsigned)(3 * tiles), T, sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw);
     }
     {
-        auto k = fft_yz_fused<R, OutT, N, NLX>;
-        constexpr int NR = (2 * NLX < N) ? 2 * NLX : N;
-        constexpr int T = threads_for<N, NLX>();
-        const size_t tile = std::max((size_t)N * (NLX + 1), (size_t)(N / 2) * (NR + 1));
-        const size_t sm = sizeof(V) * (N + tile);
+        auto k = fft_yz_fused<R, OutT, N, NL>;
+        constexpr int NR = z_rows<N, NL>();
+        const size_t sm = sizeof(V) * yz_smem_elems<R, N, NL>();
         if ((rc = set_smem(k, sm))) return rc;
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, sm);
         if (e != cudaSuccess) return set_cuda_error(e);
-        const long long items = 3LL * N * ((H + NLX - 1) / NLX + N / NR);
+        const long long items = 3LL * N * ((H + NL - 1) / NL + N / NR);
         const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
-        V* ring = w + 3LL * N * N * H;
-        unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRing * N * H);
+        V* ring = w + 3LL * N * N * HP;
+        unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRing * N * HP);
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 6LL * N), st);
         if (e != cudaSuccess) return set_cuda_error(e);
         StageTimer tm(p, BSPLINE_STAGE_FFT_YZ);
@@ -386,12 +444,6 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
                                          (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0);
     }
     return set_cuda_error(cudaGetLastError());
-}
-
-// Workspace of the transform: the x-transformed spectrum, the plane ring and the counters.
-template <typename V> size_t transform_workspace(int N) {
-    const size_t H = N / 2 + 1;
-    return sizeof(V) * (3ull * N * N * H + (size_t)kRing * N * H) + sizeof(unsigned) * (1 + 6ull * N);
 }
 
 template <int N> int run_n(bspline_plan_s* p, const void* u_hat, void* coeffs) {
