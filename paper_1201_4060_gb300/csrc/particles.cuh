@@ -203,6 +203,87 @@ __device__ __forceinline__ void eval_particle(const A* __restrict__ base, A tx, 
     }
 }
 
+// FP32 version of eval_particle with packed two-way FMAs (fma.rn.f32x2):
+// adjacent y-lines jy, jy + 1 are contracted along z together (their loads
+// form the pair, the z weight is duplicated), and their y-sums are kept as
+// (even, odd) pairs that are added at the end of each x-plane.  Same
+// arithmetic per term as eval_particle; the sums are grouped by parity of jy.
+template <int ORD, bool GRAD, int E>
+__device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base, float tx, float ty, float tz,
+                                                 float dscale, float* __restrict__ out_u,
+                                                 float* __restrict__ out_grad) {
+    constexpr int E3 = E * E * E;
+    constexpr int NP = ORD / 2;                       // pairs of y-lines
+    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+    bspline_weights<ORD, float>(tx, wx, dwx);
+    bspline_weights<ORD, float>(ty, wy, dwy);
+    bspline_weights<ORD, float>(tz, wz, dwz);
+    float2 wz2[ORD], dwz2[ORD], wyp[NP > 0 ? NP : 1], dwyp[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int j = 0; j < ORD; ++j) {
+        wz2[j] = make_float2(wz[j], wz[j]);
+        dwz2[j] = make_float2(dwz[j], dwz[j]);
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        wyp[p] = make_float2(wy[2 * p], wy[2 * p + 1]);
+        dwyp[p] = make_float2(dwy[2 * p], dwy[2 * p + 1]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float* tc = base + c * E3;
+        float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int jx = 0; jx < ORD; ++jx) {
+            float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float* l0 = tc + (jx * E + 2 * p) * E;
+                const float* l1 = l0 + E;
+                float2 z0 = make_float2(0.f, 0.f), z1 = z0;
+#pragma unroll
+                for (int jz = 0; jz < ORD; ++jz) {
+                    const float2 a = make_float2(l0[jz], l1[jz]);
+                    z0 = __ffma2_rn(wz2[jz], a, z0);
+                    if (GRAD) z1 = __ffma2_rn(dwz2[jz], a, z1);
+                }
+                y00 = __ffma2_rn(wyp[p], z0, y00);
+                if (GRAD) {
+                    y10 = __ffma2_rn(dwyp[p], z0, y10);
+                    y01 = __ffma2_rn(wyp[p], z1, y01);
+                }
+            }
+            if constexpr (ORD % 2 == 1) {               // the unpaired last line
+                const float* l = tc + (jx * E + ORD - 1) * E;
+                float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+                for (int jz = 0; jz < ORD; ++jz) {
+                    z0 = fmaf(wz[jz], l[jz], z0);
+                    if (GRAD) z1 = fmaf(dwz[jz], l[jz], z1);
+                }
+                y00.x = fmaf(wy[ORD - 1], z0, y00.x);
+                if (GRAD) {
+                    y10.x = fmaf(dwy[ORD - 1], z0, y10.x);
+                    y01.x = fmaf(wy[ORD - 1], z1, y01.x);
+                }
+            }
+            const float s00 = y00.x + y00.y;
+            u = fmaf(wx[jx], s00, u);
+            if (GRAD) {
+                gx = fmaf(dwx[jx], s00, gx);
+                gy = fmaf(wx[jx], y10.x + y10.y, gy);
+                gz = fmaf(wx[jx], y01.x + y01.y, gz);
+            }
+        }
+        out_u[c] = u;
+        if (GRAD) {
+            out_grad[3 * c + 0] = gx * dscale;
+            out_grad[3 * c + 1] = gy * dscale;
+            out_grad[3 * c + 2] = gz * dscale;
+        }
+    }
+}
+
 // FP64: one thread per particle (the FP64 pipe, not shared memory, bounds it).
 template <int ORD, typename TR, bool GRAD>
 __global__ void __launch_bounds__(128)
@@ -324,8 +405,8 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
                 const int oz = (int)(rc.cell & 1023u) - z0;
                 const unsigned idx = w.s_idx[i];
                 float u[3], g[9];
-                eval_particle<ORD, float, GRAD, E>(tile + (ox * E + oy) * E + oz, (float)rc.t[0], (float)rc.t[1],
-                                                    (float)rc.t[2], dscale, u, g);
+                eval_particle_x2<ORD, GRAD, E>(tile + (ox * E + oy) * E + oz, (float)rc.t[0], (float)rc.t[1],
+                                                (float)rc.t[2], dscale, u, g);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) out_u[3 * (size_t)idx + c] = u[c];
                 if (GRAD) {
