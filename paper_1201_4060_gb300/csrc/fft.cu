@@ -247,7 +247,38 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // complex transform of Z = E + i O gives z[m] = x[2m] + i x[2m + 1].  Only the
 // real parts of X[0] and X[M] enter (real-to-complex semantics).
 constexpr int kRing = 16;
+// Items are dequeued in super-steps: step s holds the Y items of plane s and
+// then the Z items of plane s - kLag, so a plane's consumers come kLag planes
+// after its producers (kLag < kRing keeps every dependency pointing back).
+constexpr int kLag = 8;
+static_assert(kLag < kRing, "ring slots must outlive the lag");
 constexpr long long kWaitLimit = 1LL << 22;
+
+// Item index -> (plane, index within the plane: < TPZ for Y items, else TPZ + Z index).
+template <int TPZ, int ZPP>
+__device__ __forceinline__ void item_to_plane(long long item, long long planes, long long* pl, int* r) {
+    constexpr int IPP = TPZ + ZPP;
+    const long long head = (long long)kLag * TPZ;                  // steps 0..kLag-1: Y items only
+    const long long body = head + (planes - kLag) * IPP;           // steps kLag..planes-1: Y then Z
+    if (item < head) {
+        *pl = item / TPZ;
+        *r = (int)(item % TPZ);
+    } else if (item < body) {
+        const long long j = item - head, s = kLag + j / IPP;
+        const int q = (int)(j % IPP);
+        if (q < TPZ) {
+            *pl = s;
+            *r = q;
+        } else {
+            *pl = s - kLag;
+            *r = q;
+        }
+    } else {                                                       // steps planes..planes+kLag-1: Z only
+        const long long j = item - body;
+        *pl = planes + j / ZPP - kLag;
+        *r = TPZ + (int)(j % ZPP);
+    }
+}
 
 // Counters of one launch (zeroed before it): [0] = work-item counter, then per
 // plane the number of finished Y items, then per plane the finished Z items.
@@ -320,8 +351,9 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
         const unsigned item = s_item;
         __syncthreads();
         if (item >= (unsigned)(PLANES * IPP)) return;
-        const long long pl = item / IPP;
-        const int r = (int)(item % IPP);
+        long long pl;
+        int r;
+        item_to_plane<TPZ, ZPP>(item, PLANES, &pl, &r);
         V* slot = ring + (pl % kRing) * (long long)N * HP;
         if (r < TPZ) {
             // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot

@@ -318,14 +318,14 @@ gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __
     }
 }
 
-// FP32 accumulation (FP32 or BF16 coefficients).  Shared-memory bandwidth
-// bounds this kernel: each particle reads 3 ORD^3 tile values, and a warp
-// load costs one cycle per distinct address in the busiest of the 32 banks.
-// Particles of a brick are therefore assembled into warp "jobs" in which no
-// two particles' stencil origins fall into the same bank: within a chunk,
-// particles are bucketed by the bank of their origin (residue mod 32) and
-// job j takes the j-th particle of every bucket.  Every load of a job is then
-// conflict-free; the number of jobs is the largest bucket.
+// FP32 accumulation (FP32 or BF16 coefficients).  Each particle reads
+// 3 ORD^3 tile values from shared memory, and a warp load costs one cycle per
+// distinct address in the busiest of the 32 banks; random stencil origins
+// would make most loads 3-4 way conflicted.  Within a chunk, particles are
+// therefore bucketed by the bank of their stencil origin (residue mod 32),
+// ranked within their bucket, and ordered rank-major, bank-minor: a warp
+// that takes 32 consecutive particles of that order sees each bank at most
+// once per rank it spans.
 // One CTA per work item: item i is chunk i - chunk[b] of the brick b with
 // chunk[b] <= i < chunk[b + 1] (at most kChunk particles); the grid is an
 // upper bound on the number of items and surplus CTAs return at once.
@@ -386,19 +386,14 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
             s_order[pos] = (unsigned short)i;
         }
         __syncthreads();
-        const unsigned my_bucket = s_bucket[lane];
-        unsigned njobs = my_bucket;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) njobs = max(njobs, __shfl_xor_sync(0xffffffffu, njobs, d));
+        // Warp j takes positions 32 j .. 32 j + 31 of that order: full warps, and
+        // a warp spanning k ranks has at most k-way conflicts (each rank holds
+        // distinct banks), which only happens in the sparse tail of the ranks.
+        const unsigned njobs = ((unsigned)n + 31u) / 32u;
         for (unsigned j = warp; j < njobs; j += NW) {
-            unsigned lo = min(my_bucket, j), hi = min(my_bucket, j + 1);
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                lo += __shfl_xor_sync(0xffffffffu, lo, d);
-                hi += __shfl_xor_sync(0xffffffffu, hi, d);
-            }
-            if (lo + lane < hi) {
-                const unsigned i = c0 + s_order[lo + lane];
+            const unsigned pos = 32u * j + (unsigned)lane;
+            if (pos < (unsigned)n) {
+                const unsigned i = c0 + s_order[pos];
                 const Rec<TR> rc = w.s_rec[i];
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
