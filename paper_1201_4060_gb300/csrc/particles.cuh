@@ -386,13 +386,34 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
             s_order[pos] = (unsigned short)i;
         }
         __syncthreads();
-        // Warp j takes positions 32 j .. 32 j + 31 of that order: full warps, and
-        // a warp spanning k ranks has at most k-way conflicts (each rank holds
-        // distinct banks), which only happens in the sparse tail of the ranks.
-        const unsigned njobs = ((unsigned)n + 31u) / 32u;
+        // Warp jobs over that order.  Rank j holds #{banks with more than j
+        // particles} particles, non-increasing in j.  While a rank holds at
+        // least 16 particles it is one job (every load conflict-free); the
+        // sparse tail ranks are packed 32 to a job: a job spanning k ranks
+        // costs k-way conflicts, as k separate jobs would, in one instruction
+        // stream instead of k.
+        const unsigned my_bucket = s_bucket[lane];
+        unsigned above = 0;                               // buckets ordered before this lane's
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const unsigned bq = __shfl_sync(0xffffffffu, my_bucket, q);
+            above += (bq > my_bucket || (bq == my_bucket && q < lane)) ? 1u : 0u;
+        }
+        const unsigned src16 = __ffs(__ballot_sync(0xffffffffu, above == 15u)) - 1;
+        const unsigned j16 = __shfl_sync(0xffffffffu, my_bucket, src16);   // ranks j < j16 hold >= 16
+        const unsigned pos16 = __reduce_add_sync(0xffffffffu, min(my_bucket, j16));
+        const unsigned njobs = j16 + ((unsigned)n - pos16 + 31u) / 32u;
         for (unsigned j = warp; j < njobs; j += NW) {
-            const unsigned pos = 32u * j + (unsigned)lane;
-            if (pos < (unsigned)n) {
+            unsigned lo, hi;
+            if (j < j16) {
+                lo = __reduce_add_sync(0xffffffffu, min(my_bucket, j));
+                hi = __reduce_add_sync(0xffffffffu, min(my_bucket, j + 1));
+            } else {
+                lo = pos16 + 32u * (j - j16);
+                hi = min((unsigned)n, lo + 32u);
+            }
+            const unsigned pos = lo + (unsigned)lane;
+            if (pos < hi) {
                 const unsigned i = c0 + s_order[pos];
                 const Rec<TR> rc = w.s_rec[i];
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
