@@ -15,10 +15,12 @@
 //       imaginary parts), rounded to the coefficient type on store.
 // Tiles move between global and shared memory with cp.async, so the data in
 // flight occupies shared memory rather than registers and several CTAs per SM
-// keep loads outstanding while others compute.  In shared memory a tile is
-// [position][line + 1] (line index fastest, one complex of padding per row):
-// global accesses are coalesced along contiguous lines and every butterfly
-// read/write is bank-conflict free.  Radix-8/4/2 Stockham stages, fully
+// keep loads outstanding while others compute.  In shared memory a kx/ky tile
+// is [position][line] with 64-byte rows (line index fastest): a half-warp's
+// 64-bit accesses cover two whole rows, so butterfly reads are bank-conflict
+// free (only the first stage's scattered writes pair up); the kz transform
+// uses [position][line + 1], conflict-free for its transposed fill.
+// Global accesses are coalesced along contiguous lines.  Radix-8/4/2 Stockham stages, fully
 // unrolled per transform length; twiddles exp(+2 pi i m / N) from a table
 // computed on the host in FP64.
 #include <algorithm>
@@ -180,7 +182,7 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
                 const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
-    constexpr int QS = NL + 1;
+    constexpr int QS = NL;
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
     constexpr long long NH = (long long)N * H;
     constexpr long long TILES = (NH + NL - 1) / NL;
@@ -230,9 +232,8 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // ---------------------------------------------------------------- passes Y + Z fused
 // One persistent kernel does the ky transform and the kz c2r of every
 // (component, x) plane, handing each plane from one to the other through a
-// ring of kRing plane buffers small enough to stay in L2 (kRing x N x HP
-// complex, 17.3 MB at N = 512 FP32), so the intermediate spectrum never makes
-// a round trip through HBM.  Work items are taken in order from a global
+// ring of plane buffers small enough to stay in L2 (at most kRingMax x N x HP
+// complex), so the intermediate spectrum never makes a round trip through HBM.  Work items are taken in order from a global
 // counter: per plane, ceil(H / NL) "Y" items (NL kz columns, all ky) then
 // N / NR "Z" items (NR rows y, all kz).  A Z item waits until all Y items of
 // its plane have been stored; a Y item waits until the Z items that last used
@@ -246,36 +247,37 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // have the even and odd outputs as their length-M inverse transforms; one
 // complex transform of Z = E + i O gives z[m] = x[2m] + i x[2m + 1].  Only the
 // real parts of X[0] and X[M] enter (real-to-complex semantics).
-constexpr int kRing = 16;
 // Items are dequeued in super-steps: step s holds the Y items of plane s and
-// then the Z items of plane s - kLag, so a plane's consumers come kLag planes
-// after its producers (kLag < kRing keeps every dependency pointing back).
-constexpr int kLag = 8;
-static_assert(kLag < kRing, "ring slots must outlive the lag");
+// then the Z items of plane s - lag, so a plane's consumers come lag planes
+// after its producers.  The host picks lag from the number of planes the
+// resident CTAs work on at once (plus a margin) and ring = 2 lag slots, so a
+// Y item rarely waits for its slot either; lag < ring keeps every dependency
+// pointing back.
+constexpr int kRingMax = 32;
 constexpr long long kWaitLimit = 1LL << 22;
 
 // Item index -> (plane, index within the plane: < TPZ for Y items, else TPZ + Z index).
 template <int TPZ, int ZPP>
-__device__ __forceinline__ void item_to_plane(long long item, long long planes, long long* pl, int* r) {
+__device__ __forceinline__ void item_to_plane(long long item, long long planes, int lag, long long* pl, int* r) {
     constexpr int IPP = TPZ + ZPP;
-    const long long head = (long long)kLag * TPZ;                  // steps 0..kLag-1: Y items only
-    const long long body = head + (planes - kLag) * IPP;           // steps kLag..planes-1: Y then Z
+    const long long head = (long long)lag * TPZ;                   // steps 0..lag-1: Y items only
+    const long long body = head + (planes - lag) * IPP;            // steps lag..planes-1: Y then Z
     if (item < head) {
         *pl = item / TPZ;
         *r = (int)(item % TPZ);
     } else if (item < body) {
-        const long long j = item - head, s = kLag + j / IPP;
+        const long long j = item - head, s = lag + j / IPP;
         const int q = (int)(j % IPP);
         if (q < TPZ) {
             *pl = s;
             *r = q;
         } else {
-            *pl = s - kLag;
+            *pl = s - lag;
             *r = q;
         }
-    } else {                                                       // steps planes..planes+kLag-1: Z only
+    } else {                                                       // steps planes..planes+lag-1: Z only
         const long long j = item - body;
-        *pl = planes + j / ZPP - kLag;
+        *pl = planes + j / ZPP - lag;
         *r = TPZ + (int)(j % ZPP);
     }
 }
@@ -314,21 +316,27 @@ template <int N, int NL> constexpr int z_rows() { return (2 * NL < N) ? 2 * NL :
 template <typename R, int N, int NL>
 constexpr size_t yz_smem_elems() {
     constexpr int HP = row_pitch(N), NR = z_rows<N, NL>();
-    constexpr size_t y = (size_t)N * (NL + 1);
+    constexpr size_t y = (size_t)N * NL;
     constexpr size_t z = (size_t)NR * HP + (size_t)(N / 2) * (NR + 1);
     return N + (y > z ? y : z);
 }
 
+// CTAs per SM the fused kernel is compiled for: about 24 warps per SM.
+template <int N, int NL> constexpr int yz_min_blocks() {
+    return (768 / threads_for<N, NL>()) < 1 ? 1 : (768 / threads_for<N, NL>());
+}
+
 template <typename R, typename OutT, int N, int NL>
-__global__ void __launch_bounds__(threads_for<N, NL>(), 3)
+__global__ void __launch_bounds__(threads_for<N, NL>(), yz_min_blocks<N, NL>())
 fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
-             const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int drop_signals) {
+             const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int lag, int ring_slots,
+             int drop_signals) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
     constexpr int M = N / 2;
     constexpr int NR = z_rows<N, NL>();                 // Z rows per item: same thread count as a Y item
-    constexpr int QY = NL + 1, QZ = NR + 1;
+    constexpr int QY = NL, QZ = NR + 1;
     constexpr int TPZ = (H + NL - 1) / NL;              // Y items per plane
     constexpr int ZPP = N / NR;                         // Z items per plane
     constexpr int IPP = TPZ + ZPP;
@@ -353,20 +361,18 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
         if (item >= (unsigned)(PLANES * IPP)) return;
         long long pl;
         int r;
-        item_to_plane<TPZ, ZPP>(item, PLANES, &pl, &r);
-        V* slot = ring + (pl % kRing) * (long long)N * HP;
+        item_to_plane<TPZ, ZPP>(item, PLANES, lag, &pl, &r);
+        V* slot = ring + (pl % ring_slots) * (long long)N * HP;
         if (r < TPZ) {
             // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
             const int kz0 = r * NL;
             const int valid = std::min(NL, H - kz0);
             load_tile<V, N, NL, T, QY>(buf, w + pl * N * HP + kz0, HP, valid);
-            if (pl >= kRing && !cta_wait(&done_z[pl - kRing], (unsigned)ZPP, error, &s_ok)) {
-                cp_async_wait_all();                    // no copy of this CTA left in flight
-                return;
-            }
             cp_async_wait_all();
             __syncthreads();
             fft_smem<V, N, NL, T, QY>(buf, tws, 1);
+            // the slot is free once the Z items of the plane that used it before have read it
+            if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
             for (int e = t; e < N * NL; e += T) {
                 const int q = e / NL, b = e % NL;
                 if (b < valid) slot[(long long)q * HP + kz0 + b] = buf[q * QY + b];
@@ -427,7 +433,7 @@ template <typename K> int set_smem(K kernel, size_t bytes) {
 // Workspace of the transform: the x-transformed spectrum, the plane ring and the counters.
 template <typename V> size_t transform_workspace(int N) {
     const size_t HP = row_pitch(N);
-    return sizeof(V) * (3ull * N * N * HP + (size_t)kRing * N * HP) + sizeof(unsigned) * (1 + 6ull * N);
+    return sizeof(V) * (3ull * N * N * HP + (size_t)kRingMax * N * HP) + sizeof(unsigned) * (1 + 6ull * N);
 }
 
 template <typename R, typename OutT, int N>
@@ -450,7 +456,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
     int rc;
     {
         auto k = fft_x_prefilter<R, N, NL>;
-        const size_t sm = sizeof(V) * (N + (size_t)N * (NL + 1)) + sizeof(R) * NL;
+        const size_t sm = sizeof(V) * (N + (size_t)N * NL) + sizeof(R) * NL;
         if ((rc = set_smem(k, sm))) return rc;
         const long long tiles = ((long long)N * H + NL - 1) / NL;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);
@@ -464,15 +470,19 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, sm);
         if (e != cudaSuccess) return set_cuda_error(e);
-        const long long items = 3LL * N * ((H + NL - 1) / NL + N / NR);
+        const int ipp = (H + NL - 1) / NL + N / NR;
+        const long long items = 3LL * N * ipp;
         const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
+        // planes in progress at once ~ grid / items-per-plane; consumers trail by that plus a margin
+        const int lag = (int)std::min<long long>(kRingMax / 2, (grid + ipp - 1) / ipp + 2);
+        const int ring_slots = 2 * lag;
         V* ring = w + 3LL * N * N * HP;
-        unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRing * N * HP);
+        unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRingMax * N * HP);
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 6LL * N), st);
         if (e != cudaSuccess) return set_cuda_error(e);
         StageTimer tm(p, BSPLINE_STAGE_FFT_YZ);
         k<<<(unsigned)grid, T, sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), ring, tw, ctr,
-                                         reinterpret_cast<unsigned*>(p->d_status + 1),
+                                         reinterpret_cast<unsigned*>(p->d_status + 1), lag, ring_slots,
                                          (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0);
     }
     return set_cuda_error(cudaGetLastError());
