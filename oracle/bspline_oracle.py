@@ -476,3 +476,150 @@ def l2_error_field(N: int, idx: np.ndarray, val: np.ndarray, n: int, L: float = 
 def table1_fma_count(n: int) -> int:
     """Cost of u and all first derivatives of a 3-component field per point (Table 1)."""
     return 6 * n ** 3 + 15 * n ** 2 + 12 * n
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the path (differentiation with respect to u_hat and positions).
+# The paper has no adjoint; these are the transposes of the linear maps above
+# (Sections 3-4 and 7), written out, plus second-derivative weights for the
+# position gradient (the derivative of Eq. interpolation2 in x).
+# ---------------------------------------------------------------------------
+
+def weights2(t: np.ndarray, n: int) -> np.ndarray:
+    """Second-derivative weights W''[p, j] = sum_i (M D D)[j, i] t_p^i (monomial form)."""
+    t = np.asarray(t, dtype=np.float64)
+    M = bspline_matrix(n)
+    D = derivative_matrix(n)
+    xbar = t[..., None] ** np.arange(n, dtype=np.float64)
+    return xbar @ (M @ D @ D).T
+
+
+def _valid_positions(x: np.ndarray) -> np.ndarray:
+    return np.all(np.isfinite(x), axis=1)
+
+
+def hessian(coef: np.ndarray, x: np.ndarray, n: int, L: float = 2.0 * math.pi,
+            chunk: int = 4096) -> np.ndarray:
+    """H[p][c][d][e] = d^2 u_c / dx_d dx_e of the B-spline interpolant at x (physical units).
+
+    Each entry is the stencil contraction of Eq. interpolation with, per axis,
+    W, W' or W'' by how often that axis is differentiated, scaled by (N / L)^2.
+    """
+    coef = np.asarray(coef, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    N = coef.shape[1]
+    P = x.shape[0]
+    H = np.empty((P, 3, 3, 3))
+    scale2 = (float(N) / float(L)) ** 2
+    for p0 in range(0, P, chunk):
+        xs = x[p0:p0 + chunk]
+        nodes, t = locate(xs, N, n, L)
+        W = weights(t, n)
+        sets = (W[0], W[1], weights2(t, n))            # derivative order 0, 1, 2 -> [p, 3, n]
+        ix = nodes[:, 0, :, None, None]
+        iy = nodes[:, 1, None, :, None]
+        iz = nodes[:, 2, None, None, :]
+        for c in range(3):
+            B = coef[c][ix, iy, iz]
+            for d in range(3):
+                for e in range(3):
+                    k = [0, 0, 0]
+                    k[d] += 1
+                    k[e] += 1
+                    H[p0:p0 + chunk, c, d, e] = scale2 * np.einsum(
+                        "pabc,pa,pb,pc->p", B, sets[k[0]][:, 0], sets[k[1]][:, 1], sets[k[2]][:, 2])
+    return H
+
+
+def spread(x: np.ndarray, g_u: np.ndarray, g_grad: np.ndarray | None, N: int, n: int,
+           L: float = 2.0 * math.pi, chunk: int = 4096) -> np.ndarray:
+    """Adjoint of evaluate() in the coefficients: g_coef [3][N][N][N].
+
+    g_coef[c][node] = sum_p g_u[p, c] W_x W_y W_z + (N / L) sum_p sum_e g_grad[p, c, e] (W with W' on axis e),
+    summed over every particle whose stencil covers the node.  Particles with
+    non-finite positions contribute nothing.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    g_u = np.asarray(g_u, dtype=np.float64)
+    g_grad = None if g_grad is None else np.asarray(g_grad, dtype=np.float64)
+    out = np.zeros((3, N, N, N))
+    scale = float(N) / float(L)
+    ok = _valid_positions(x)
+    for p0 in range(0, x.shape[0], chunk):
+        sel = np.nonzero(ok[p0:p0 + chunk])[0] + p0
+        if sel.size == 0:
+            continue
+        nodes, t = locate(x[sel], N, n, L)
+        W, W1 = weights(t, n)
+        ix = np.broadcast_to(nodes[:, 0, :, None, None], (sel.size, n, n, n))
+        iy = np.broadcast_to(nodes[:, 1, None, :, None], (sel.size, n, n, n))
+        iz = np.broadcast_to(nodes[:, 2, None, None, :], (sel.size, n, n, n))
+        for c in range(3):
+            T = g_u[sel, c, None, None, None] * np.einsum("pa,pb,pc->pabc", W[:, 0], W[:, 1], W[:, 2])
+            if g_grad is not None:
+                T = T + scale * (
+                    g_grad[sel, c, 0, None, None, None] * np.einsum("pa,pb,pc->pabc", W1[:, 0], W[:, 1], W[:, 2])
+                    + g_grad[sel, c, 1, None, None, None] * np.einsum("pa,pb,pc->pabc", W[:, 0], W1[:, 1], W[:, 2])
+                    + g_grad[sel, c, 2, None, None, None] * np.einsum("pa,pb,pc->pabc", W[:, 0], W[:, 1], W1[:, 2]))
+            np.add.at(out[c], (ix, iy, iz), T)
+    return out
+
+
+def position_gradient(coef: np.ndarray, x: np.ndarray, g_u: np.ndarray, g_grad: np.ndarray | None,
+                      n: int, L: float = 2.0 * math.pi) -> np.ndarray:
+    """g_x[p][d] = sum_c g_u[p, c] du_c/dx_d + sum_{c, e} g_grad[p, c, e] d^2 u_c / dx_e dx_d.
+
+    NaN for non-finite positions.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    g_u = np.asarray(g_u, dtype=np.float64)
+    out = np.full((x.shape[0], 3), np.nan)
+    ok = _valid_positions(x)
+    if not ok.any():
+        return out
+    xs = x[ok]
+    _, grad = evaluate(coef, xs, n, L)
+    gx = np.einsum("pc,pcd->pd", g_u[ok], grad)
+    if g_grad is not None:
+        H = hessian(coef, xs, n, L)
+        gx = gx + np.einsum("pce,pced->pd", np.asarray(g_grad, dtype=np.float64)[ok], H)
+    out[ok] = gx
+    return out
+
+
+def real_transform_multiplicity(N: int) -> np.ndarray:
+    """m(kz) on the half spectrum: 1 for kz = 0 and kz = N/2, 2 otherwise (how often an
+    inverse real transform counts the stored mode)."""
+    m = np.full(N // 2 + 1, 2.0)
+    m[0] = 1.0
+    if N % 2 == 0:
+        m[N // 2] = 1.0
+    return m
+
+
+def adjoint_transform(g_coef: np.ndarray, n: int, kind: str = "interp") -> np.ndarray:
+    """Adjoint of coefficients(): g_u_hat [3][N][N][N//2+1] from g_coef [3][N][N][N].
+
+    coefficients() is u_hat -> inverse real transform of c(kx) c(ky) c(kz) u_hat.
+    For a real loss with gradient g_coef, the gradient with respect to the
+    half spectrum (real and imaginary parts, as d/dRe + i d/dIm) is
+    c(kx) c(ky) c(kz) m(kz) sum_x g_coef(x) exp(-2 pi i k.x / N): the
+    unnormalised forward real transform, counted m(kz) times.
+    """
+    g_coef = np.asarray(g_coef, dtype=np.float64)
+    N = g_coef.shape[1]
+    c = prefilter(N, n) if kind == "interp" else prefilter_l2(N, n)
+    G = np.fft.rfftn(g_coef, axes=(1, 2, 3), norm="backward")
+    nh = N // 2 + 1
+    f = c[:, None, None] * c[None, :, None] * (c[:nh] * real_transform_multiplicity(N))[None, None, :]
+    return G * f[None]
+
+
+def interpolate_adjoint(u_hat: np.ndarray, x: np.ndarray, g_u: np.ndarray, g_grad: np.ndarray | None,
+                        n: int, L: float = 2.0 * math.pi, kind: str = "interp"):
+    """Gradients of sum g_u . u + sum g_grad . grad u through the whole path:
+    (g_u_hat, g_x, g_coef)."""
+    N = np.asarray(u_hat).shape[1]
+    g_coef = spread(x, g_u, g_grad, N, n, L)
+    g_x = position_gradient(coefficients(u_hat, n, kind), x, g_u, g_grad, n, L)
+    return adjoint_transform(g_coef, n, kind), g_x, g_coef
