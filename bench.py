@@ -157,7 +157,8 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
 
 def kernel_source_sha(stage: str) -> str:
     files = {"gather": ["particles.cuh"], "bin": ["particles.cu"], "scan": ["particles.cu"],
-             "scatter": ["particles.cu"], "fft_x": ["fft.cu"], "fft_yz": ["fft.cu"]}[stage]
+             "scatter": ["particles.cu"], "fft_x": ["fft.cu", "fft_core.cuh"],
+             "fft_yz": ["fft.cu", "fft_core.cuh"]}[stage]
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_1201_4060_gb300", "csrc", f), "rb") as fh:

@@ -114,11 +114,29 @@ int bspline_coeffs(bspline_plan_t plan, const void* u_hat, void* coeffs);
 int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
                    void* out_u, void* out_grad, int flags);
 
-/* Adjoint of bspline_interp and bspline_coeffs: spreads cotangents g_u [P][3]
- * and g_grad [P][3][3] (NULL = zero) onto g_coeffs (accumulated, [3][N][N][N]
- * of the output type), optionally continues through the transposed transform
- * and prefilter into g_u_hat (half spectrum, overwritten; NULL = skip) and
- * writes position gradients g_x [P][3] (NULL = skip). */
+/* Adjoint (reverse-mode derivative) of bspline_coeffs + bspline_interp for
+ * the loss  sum_p g_u[p] . u(x_p) + sum_p g_grad[p] : grad u(x_p).  The paper
+ * has no adjoint; this is the transpose of the maps of Sections 3-4 and 7.
+ *   g_u     device [P][3] of the output type, or NULL (= zero);
+ *   g_grad  device [P][3][3] of the output type, or NULL (= zero);
+ *   g_coeffs device [3][N][N][N] of the OUTPUT type (double for F64 plans,
+ *           float otherwise), or NULL: the spread of the cotangents onto the
+ *           coefficients is ADDED to it (callers zero it for a fresh gradient);
+ *   g_u_hat device half spectrum [3][N][N][N/2+1], complex double (F64) or
+ *           complex float, or NULL: overwritten with the adjoint of the
+ *           coefficient transform applied to g_coeffs (after the spread),
+ *           c(kx) c(ky) c(kz) m(kz) sum_x g_coeffs(x) exp(-2 pi i k.x / N),
+ *           m = 1 for kz = 0 and N/2, else 2 (gradient convention dL/dRe + i dL/dIm);
+ *           requires g_coeffs;
+ *   g_x     device double [P][3], or NULL: overwritten with dL/dx (second
+ *           derivatives of the interpolant enter through g_grad); requires
+ *           coeffs (as written by bspline_coeffs); NaN for non-finite positions.
+ * x is required when P > 0 and g_coeffs or g_x is given.  Non-finite positions
+ * contribute nothing to g_coeffs and are counted in the status word.
+ * FP32 plans accumulate g_coeffs with atomics: the summation order, and so
+ * the last bits, vary between calls.  Uses the plan's particle and transform
+ * workspaces.  BSPLINE_ERR_INVALID_ARG for a missing required pointer, a bad
+ * alignment or P outside [0, 2^31). */
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
                            const void* g_u, const void* g_grad, void* g_coeffs, void* g_u_hat,
                            double* g_x);
@@ -163,7 +181,10 @@ enum {
     BSPLINE_STAGE_SCAN = 3,     /* brick offsets */
     BSPLINE_STAGE_SCATTER = 4,  /* counting-sort scatter */
     BSPLINE_STAGE_GATHER = 5,   /* weights + stencil contraction */
-    BSPLINE_NSTAGES = 6
+    BSPLINE_STAGE_SPREAD = 6,   /* adjoint: cotangents spread onto coefficients */
+    BSPLINE_STAGE_GRAD_X = 7,   /* adjoint: position gradients */
+    BSPLINE_STAGE_ADJ_FFT = 8,  /* adjoint: forward real transform + prefilter */
+    BSPLINE_NSTAGES = 9
 };
 int bspline_plan_set_timing(bspline_plan_t plan, int enable);
 int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);

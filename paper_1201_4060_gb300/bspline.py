@@ -165,8 +165,8 @@ def bspline_status_string(code: int) -> str:
     return status_string(code)
 
 
-NSTAGES = 6
-STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather"]
+NSTAGES = 9
+STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "spread", "grad_x", "adj_fft"]
 TEST_DROP_TRANSFORM_SIGNALS = 0x1
 
 
@@ -278,6 +278,38 @@ class Plan:
                             out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
         _check(rc, "bspline_interp")
         return (out_u, out_grad) if grad else out_u
+
+    def spread_adjoint(self, x, g_u=None, g_grad=None, coef=None, g_coef=None, u_hat_grad: bool = True,
+                       stream=None):
+        """Adjoint of coeffs + interp for the loss sum g_u . u + sum g_grad . grad u.
+
+        Returns (g_u_hat, g_x, g_coef): g_coef [3, N, N, N] (out dtype) is accumulated into
+        (allocated as zeros if None); g_u_hat (half spectrum, u_hat dtype) if u_hat_grad;
+        g_x [P, 3] float64 if coef is given (position gradients need the coefficients).
+        """
+        import torch
+        if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
+        P, N = x.shape[0], self.N
+        for name, tns, shape in (("g_u", g_u, (P, 3)), ("g_grad", g_grad, (P, 3, 3))):
+            if tns is not None and (tns.shape != shape or tns.dtype != self.out_dtype or not tns.is_contiguous()
+                                    or not tns.is_cuda):
+                raise ValueError(f"{name} must be a contiguous CUDA {self.out_dtype} tensor {shape}")
+        if g_coef is None:
+            g_coef = torch.zeros((3, N, N, N), dtype=self.out_dtype, device=x.device)
+        elif g_coef.shape != (3, N, N, N) or g_coef.dtype != self.out_dtype or not g_coef.is_contiguous():
+            raise ValueError("bad g_coef buffer")
+        g_u_hat = torch.empty((3, N, N, N // 2 + 1), dtype=self.uhat_dtype, device=x.device) if u_hat_grad \
+            else None
+        g_x = torch.empty((P, 3), dtype=torch.float64, device=x.device) if coef is not None else None
+        self._stream(stream)
+        rc = bspline_spread_adjoint(self.handle, coef.data_ptr() if coef is not None else 0, x.data_ptr(), P,
+                                    g_u.data_ptr() if g_u is not None else 0,
+                                    g_grad.data_ptr() if g_grad is not None else 0, g_coef.data_ptr(),
+                                    g_u_hat.data_ptr() if g_u_hat is not None else 0,
+                                    g_x.data_ptr() if g_x is not None else 0)
+        _check(rc, "bspline_spread_adjoint")
+        return g_u_hat, g_x, g_coef
 
     def status(self) -> int:
         """Count of non-finite positions of the last interp; raises if the last transform timed out."""

@@ -1,0 +1,291 @@
+// Adjoint of the particle side (differentiation), shared by the adjoint_*.cu
+// translation units that instantiate it per coefficient type.
+//
+// The paper has no adjoint; these kernels transpose the evaluation of
+// Sections 3-4 (Eqs. interpolation, interpolation2) on the same brick sort
+// the forward evaluation uses:
+//
+//   spread:  g_coef[c][node] += g_u[c] w_x w_y w_z
+//                             + (N/L) (g_grad[c][0] w'_x w_y w_z + g_grad[c][1] w_x w'_y w_z
+//                                      + g_grad[c][2] w_x w_y w'_z)
+//            accumulated per work item in a shared-memory tile of the brick
+//            (shared-memory atomics), then added to g_coef with global
+//            atomics (periodic wrap); per node 1 multiply + 1 FMA after the
+//            factorisation  w_z (w_y q0 + w'_y q1) + w'_z (w_y q2),
+//            q0 = g_u w_x + s g0 w'_x, q1 = s g1 w_x, q2 = s g2 w_x;
+//   g_x:     the derivative of sum_c g_u[c] u_c + sum_{c,e} g_grad[c][e] du_c/dx_e
+//            in the position: first and second derivatives of the
+//            interpolant, contracted z first (w, w', w'' per axis).
+#pragma once
+#include "particles.cuh"
+
+namespace bs {
+namespace adjoint_impl {
+
+using namespace gather_impl;
+
+constexpr int kAdjThreads = 256;
+
+// Weights, first and second derivatives of the n stencil nodes (node 0
+// leftmost), from the cardinal B-spline recursion: with v_k[m] = M_k(t + m),
+// B''(t + n - 1 - j) = M_{n-2}(t + m) - 2 M_{n-2}(t + m - 1) + M_{n-2}(t + m - 2), m = n - 1 - j.
+template <int n, typename A>
+__device__ __forceinline__ void bspline_weights2(A t, A (&w)[n], A (&dw)[n], A (&d2w)[n]) {
+    A v[n];
+    v[0] = A(1);
+#pragma unroll
+    for (int m = 1; m < n; ++m) v[m] = A(0);
+    A v2[n];                                            // order n - 2 values (order 1 for n <= 3)
+#pragma unroll
+    for (int m = 0; m < n; ++m) v2[m] = v[m];
+#pragma unroll
+    for (int k = 2; k <= n - 1; ++k) {
+        const A inv = A(1) / A(k - 1);
+#pragma unroll
+        for (int m = k - 1; m >= 0; --m) {
+            const A left = (m > 0) ? v[m - 1] : A(0);
+            v[m] = ((t + A(m)) * v[m] + (A(k - m) - t) * left) * inv;
+        }
+        if (k == n - 2) {
+#pragma unroll
+            for (int m = 0; m < n; ++m) v2[m] = v[m];
+        }
+    }
+    const A inv = A(1) / A(n - 1);
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        const int m = n - 1 - j;
+        const A vm = (m <= n - 2) ? v[m] : A(0);
+        const A vl = (m >= 1) ? v[m - 1] : A(0);
+        w[j] = ((t + A(m)) * vm + (A(n - m) - t) * vl) * inv;
+        dw[j] = vm - vl;
+        if (n <= 2) {
+            d2w[j] = A(0);
+        } else {
+            const A a0 = (m <= n - 3) ? v2[m] : A(0);
+            const A a1 = (m >= 1 && m - 1 <= n - 3) ? v2[m - 1] : A(0);
+            const A a2 = (m >= 2 && m - 2 <= n - 3) ? v2[m - 2] : A(0);
+            d2w[j] = a0 - A(2) * a1 + a2;
+        }
+    }
+}
+
+// Work item -> brick and its particle range [beg, end) in the sorted order.
+template <typename TR>
+__device__ __forceinline__ bool item_range(const Ws<TR>& w, unsigned NB, unsigned item, unsigned* brick,
+                                           unsigned* beg, unsigned* end) {
+    if (item >= w.chunk[NB]) return false;
+    unsigned lo = 0, hi = NB;                           // largest b with chunk[b] <= item
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (w.chunk[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    *brick = lo;
+    *beg = w.offset[lo] + (item - w.chunk[lo]) * kChunk;
+    *end = min(*beg + kChunk, w.offset[lo + 1]);
+    return *beg < *end;
+}
+
+template <int ORD, typename A> constexpr int acc_edge() { return brick_edge(sizeof(A) == 8 ? BSPLINE_F64 : BSPLINE_F32) + ORD - 1; }
+
+template <int ORD, typename A> constexpr size_t acc_bytes() {
+    return sizeof(A) * 3 * (size_t)acc_edge<ORD, A>() * acc_edge<ORD, A>() * acc_edge<ORD, A>();
+}
+
+// One CTA per work item: spread its particles' cotangents into a shared tile,
+// then add the tile to g_coef.
+template <int ORD, typename TR, typename A, bool GRAD>
+__global__ void __launch_bounds__(kAdjThreads)
+spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, const A* __restrict__ g_grad,
+              A* __restrict__ g_coef, A dscale) {
+    constexpr int B = brick_edge(sizeof(A) == 8 ? BSPLINE_F64 : BSPLINE_F32);
+    constexpr int E = acc_edge<ORD, A>();
+    constexpr int E3 = E * E * E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    A* acc = reinterpret_cast<A*>(smem_raw);
+    unsigned brick, beg, end;
+    if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
+    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
+    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) acc[e] = A(0);
+    __syncthreads();
+    for (unsigned i = beg + threadIdx.x; i < end; i += kAdjThreads) {
+        const Rec<TR> rc = w.s_rec[i];
+        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+        const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+        const int oz = (int)(rc.cell & 1023u) - z0;
+        const size_t idx = w.s_idx[i];
+        A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+        bspline_weights<ORD, A>((A)rc.t[0], wx, dwx);
+        bspline_weights<ORD, A>((A)rc.t[1], wy, dwy);
+        bspline_weights<ORD, A>((A)rc.t[2], wz, dwz);
+        A* base = acc + (ox * E + oy) * E + oz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const A gu = g_u ? g_u[3 * idx + c] : A(0);
+            A g0 = A(0), g1 = A(0), g2 = A(0);
+            if (GRAD) {
+                g0 = g_grad[9 * idx + 3 * c + 0] * dscale;
+                g1 = g_grad[9 * idx + 3 * c + 1] * dscale;
+                g2 = g_grad[9 * idx + 3 * c + 2] * dscale;
+            }
+            A* tc = base + c * E3;
+#pragma unroll
+            for (int jx = 0; jx < ORD; ++jx) {
+                const A q0 = GRAD ? fma(g0, dwx[jx], gu * wx[jx]) : gu * wx[jx];
+                const A q1 = g1 * wx[jx], q2 = g2 * wx[jx];
+#pragma unroll
+                for (int jy = 0; jy < ORD; ++jy) {
+                    const A p0 = GRAD ? fma(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
+                    const A p1 = q2 * wy[jy];
+                    A* line = tc + (jx * E + jy) * E;
+#pragma unroll
+                    for (int jz = 0; jz < ORD; ++jz) {
+                        const A v = GRAD ? fma(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz];
+                        atomicAdd(line + jz, v);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int msk = N - 1;
+    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) {
+        const A v = acc[e];
+        if (v != A(0)) {
+            const int c = e / E3, r = e - c * E3;
+            const int ix = r / (E * E), iy = (r / E) % E, iz = r % E;
+            atomicAdd(&g_coef[(((size_t)c * N + ((x0 + ix) & msk)) * N + ((y0 + iy) & msk)) * N + ((z0 + iz) & msk)],
+                      v);
+        }
+    }
+}
+
+// Position gradient: one thread per particle of the work item, coefficients
+// staged as in the forward evaluation.
+template <int ORD, typename CT, typename TR, bool HESS>
+__global__ void __launch_bounds__(kAdjThreads)
+gx_kernel(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w,
+          const typename TileT<CT>::T* __restrict__ g_u, const typename TileT<CT>::T* __restrict__ g_grad,
+          double* __restrict__ g_x, typename TileT<CT>::T dscale) {
+    using A = typename TileT<CT>::T;
+    constexpr int B = brick_edge(sizeof(CT) == 8 ? BSPLINE_F64 : BSPLINE_F32);
+    constexpr int E = tile_edge<ORD, CT>();
+    constexpr int E3 = E * E * E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    A* tile = reinterpret_cast<A*>(smem_raw);
+    unsigned brick, beg, end;
+    if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
+    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
+    stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
+    cp_async_wait_all();
+    __syncthreads();
+    const A s2 = dscale * dscale;
+    for (unsigned i = beg + threadIdx.x; i < end; i += kAdjThreads) {
+        const Rec<TR> rc = w.s_rec[i];
+        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+        const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+        const int oz = (int)(rc.cell & 1023u) - z0;
+        const size_t idx = w.s_idx[i];
+        A wx[ORD], dwx[ORD], d2wx[ORD], wy[ORD], dwy[ORD], d2wy[ORD], wz[ORD], dwz[ORD], d2wz[ORD];
+        bspline_weights2<ORD, A>((A)rc.t[0], wx, dwx, d2wx);
+        bspline_weights2<ORD, A>((A)rc.t[1], wy, dwy, d2wy);
+        bspline_weights2<ORD, A>((A)rc.t[2], wz, dwz, d2wz);
+        const A* base = tile + (ox * E + oy) * E + oz;
+        A gx = A(0), gy = A(0), gz = A(0);
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            const A* tc = base + c * E3;
+            // T_abc = sum over the stencil of a * w^(a)_x w^(b)_y w^(c)_z
+            A t100 = 0, t010 = 0, t001 = 0, t200 = 0, t020 = 0, t002 = 0, t110 = 0, t101 = 0, t011 = 0;
+#pragma unroll
+            for (int jx = 0; jx < ORD; ++jx) {
+                A y00 = 0, y10 = 0, y01 = 0, y20 = 0, y02 = 0, y11 = 0;
+#pragma unroll
+                for (int jy = 0; jy < ORD; ++jy) {
+                    const A* line = tc + (jx * E + jy) * E;
+                    A z0v = 0, z1v = 0, z2v = 0;
+#pragma unroll
+                    for (int jz = 0; jz < ORD; ++jz) {
+                        const A a = line[jz];
+                        z0v = fma(wz[jz], a, z0v);
+                        z1v = fma(dwz[jz], a, z1v);
+                        if (HESS) z2v = fma(d2wz[jz], a, z2v);
+                    }
+                    y00 = fma(wy[jy], z0v, y00);
+                    y10 = fma(dwy[jy], z0v, y10);
+                    y01 = fma(wy[jy], z1v, y01);
+                    if (HESS) {
+                        y20 = fma(d2wy[jy], z0v, y20);
+                        y02 = fma(wy[jy], z2v, y02);
+                        y11 = fma(dwy[jy], z1v, y11);
+                    }
+                }
+                t100 = fma(dwx[jx], y00, t100);
+                t010 = fma(wx[jx], y10, t010);
+                t001 = fma(wx[jx], y01, t001);
+                if (HESS) {
+                    t200 = fma(d2wx[jx], y00, t200);
+                    t020 = fma(wx[jx], y20, t020);
+                    t002 = fma(wx[jx], y02, t002);
+                    t110 = fma(dwx[jx], y10, t110);
+                    t101 = fma(dwx[jx], y01, t101);
+                    t011 = fma(wx[jx], y11, t011);
+                }
+            }
+            const A gu = g_u ? g_u[3 * idx + c] * dscale : A(0);
+            gx = fma(gu, t100, gx);
+            gy = fma(gu, t010, gy);
+            gz = fma(gu, t001, gz);
+            if (HESS) {
+                const A g0 = g_grad[9 * idx + 3 * c + 0] * s2;
+                const A g1 = g_grad[9 * idx + 3 * c + 1] * s2;
+                const A g2 = g_grad[9 * idx + 3 * c + 2] * s2;
+                gx += g0 * t200 + g1 * t110 + g2 * t101;
+                gy += g0 * t110 + g1 * t020 + g2 * t011;
+                gz += g0 * t101 + g1 * t011 + g2 * t002;
+            }
+        }
+        g_x[3 * idx + 0] = (double)gx;
+        g_x[3 * idx + 1] = (double)gy;
+        g_x[3 * idx + 2] = (double)gz;
+    }
+}
+
+// Launch the spread (g_coef != nullptr) and the position gradient (g_x != nullptr)
+// for one order and coefficient type.  items = upper bound of work items.
+template <int ORD, typename CT, typename TR>
+int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, long long items,
+                const void* g_u, const void* g_grad, void* g_coef, double* g_x) {
+    using A = typename TileT<CT>::T;
+    const A dscale = (A)((double)p->N / p->L);
+    int rc;
+    if (g_coef) {
+        const size_t sm = acc_bytes<ORD, A>();
+        auto k = g_grad ? spread_kernel<ORD, TR, A, true> : spread_kernel<ORD, TR, A, false>;
+        if ((rc = set_smem(k, sm))) return rc;
+        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, nbx, NB, w, (const A*)g_u, (const A*)g_grad,
+                                                            (A*)g_coef, dscale);
+    }
+    if (g_x) {
+        const size_t sm = tile_bytes<ORD, CT>();
+        auto k = g_grad ? gx_kernel<ORD, CT, TR, true> : gx_kernel<ORD, CT, TR, false>;
+        if ((rc = set_smem(k, sm))) return rc;
+        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>((const CT*)coeffs, p->N, nbx, NB, w, (const A*)g_u,
+                                                            (const A*)g_grad, g_x, dscale);
+    }
+    return BSPLINE_OK;
+}
+
+}  // namespace adjoint_impl
+
+#define BS_ADJOINT_EXTERN(ORD, CT, TR)                                                                          \
+    extern template int adjoint_impl::run_adjoint<ORD, CT, TR>(bspline_plan_s*, const void*,                   \
+                                                                gather_impl::Ws<TR>, unsigned, int, long long,   \
+                                                                const void*, const void*, void*, double*);
+#define BS_ADJOINT_INSTANTIATE(ORD, CT, TR)                                                                     \
+    template int adjoint_impl::run_adjoint<ORD, CT, TR>(bspline_plan_s*, const void*, gather_impl::Ws<TR>,      \
+                                                         unsigned, int, long long, const void*, const void*,    \
+                                                         void*, double*);
+
+}  // namespace bs

@@ -337,9 +337,26 @@ int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int
 
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, const void* g_u,
                            const void* g_grad, void* g_coeffs, void* g_u_hat, double* g_x) {
-    (void)coeffs; (void)x; (void)g_u; (void)g_grad; (void)g_coeffs; (void)g_u_hat; (void)g_x;
-    if (!valid_plan(plan) || P < 0) return BSPLINE_ERR_INVALID_ARG;
-    return BSPLINE_ERR_NOT_IMPLEMENTED;
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
+    if (g_u_hat && !g_coeffs) return BSPLINE_ERR_INVALID_ARG;
+    const bool particles = P > 0 && (g_coeffs || g_x);
+    if (particles && !x) return BSPLINE_ERR_INVALID_ARG;
+    if (P > 0 && g_x && !coeffs) return BSPLINE_ERR_INVALID_ARG;
+    const size_t ob = out_bytes(plan->dtype);
+    if (!aligned(coeffs, 16) || !aligned(x, 8) || !aligned(g_u, ob) || !aligned(g_grad, ob) ||
+        !aligned(g_coeffs, ob) || !aligned(g_u_hat, 16) || !aligned(g_x, 8))
+        return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    int rc;
+    if (particles && (rc = launch_adjoint_particles(plan, coeffs, x, P, g_u, g_grad, g_coeffs, g_x)))
+        return rc;
+    if (g_u_hat) {
+        if ((rc = plan->work.grow(coeffs_workspace_bytes(plan)))) return rc;
+        if ((rc = launch_adjoint_transform(plan, g_coeffs, g_u_hat))) return rc;
+    }
+    return BSPLINE_OK;
 }
 
 int bspline_workspace_bytes(bspline_plan_t plan, int64_t P, size_t* bytes) {

@@ -1,0 +1,166 @@
+// Building blocks of the shared-memory FFTs: complex helpers, radix-2/4/8
+// butterflies of the inverse DFT (exponent +2 pi i n k / R), the Stockham
+// stage and the tile loads.  Included by the forward path (fft.cu: prefilter
+// + inverse real transform) and by its adjoint (adjoint_fft.cu: forward real
+// transform + prefilter), which runs the inverse stages on conjugated data.
+#pragma once
+#include <algorithm>
+
+#include "internal.h"
+
+namespace bs {
+namespace fftc {
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) { V r; r.x = a; r.y = b; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cmuli(V a) { return mk<V>(-a.y, a.x); }  // a * (+i)
+
+// Inverse DFTs (exponent +2 pi i n k / R) in registers.
+template <typename V> __device__ __forceinline__ void dft2(V& a, V& b) {
+    V t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+template <typename V> __device__ __forceinline__ void dft4(V& x0, V& x1, V& x2, V& x3) {
+    V t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmuli(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+template <typename V> __device__ __forceinline__ void dft8(V* x) {
+    using R = decltype(V::x);
+    V e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    V o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    dft4(e0, e1, e2, e3);
+    dft4(o0, o1, o2, o3);
+    const R s = (R)0.70710678118654752440084436210485;
+    V w1 = mk<V>((o1.x - o1.y) * s, (o1.x + o1.y) * s);     // exp(i pi/4) o1
+    V w2 = cmuli(o2);                                        // exp(i pi/2) o2
+    V w3 = mk<V>((-o3.x - o3.y) * s, (o3.x - o3.y) * s);    // exp(3 i pi/4) o3
+    x[0] = cadd(e0, o0);
+    x[4] = csub(e0, o0);
+    x[1] = cadd(e1, w1);
+    x[5] = csub(e1, w1);
+    x[2] = cadd(e2, w2);
+    x[6] = csub(e2, w2);
+    x[3] = cadd(e3, w3);
+    x[7] = csub(e3, w3);
+}
+template <int R, typename V> __device__ __forceinline__ void butterfly(V* v) {
+    if constexpr (R == 2) dft2(v[0], v[1]);
+    else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+    else dft8(v);
+}
+
+// One radix-R Stockham stage of NLINES inverse transforms of length L, in
+// place in shared memory: element (line b, position q) at s[q * QS + b].
+// Butterfly j of a line reads positions j + r L/R, multiplies by
+// exp(2 pi i r (j mod NS) / (NS R)), and writes positions
+// (j / NS) NS R + (j mod NS) + r NS.  All reads finish before any write.
+template <typename V, int L, int NLINES, int T, int RADIX, int NS, int QS>
+__device__ __forceinline__ void stage(V* s, const V* tw, int twstride) {
+    constexpr int NB = (L / RADIX) * NLINES;
+    constexpr int BPT = (NB + T - 1) / T;
+    V v[BPT][RADIX];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int u = t + i * T;
+        if (NB % T == 0 || u < NB) {
+            const int b = u % NLINES, j = u / NLINES, k = j % NS;
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) {
+                V a = s[(j + r * (L / RADIX)) * QS + b];
+                if (NS > 1 && r > 0) a = cmul(a, tw[(r * k * (L / (NS * RADIX))) * twstride]);
+                v[i][r] = a;
+            }
+            butterfly<RADIX>(v[i]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int u = t + i * T;
+        if (NB % T == 0 || u < NB) {
+            const int b = u % NLINES, j = u / NLINES, k = j % NS;
+            const int d = (j / NS) * NS * RADIX + k;
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) s[(d + r * NS) * QS + b] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename V, int L, int NLINES, int T, int QS, int NS = 1>
+__device__ __forceinline__ void fft_smem(V* s, const V* tw, int twstride) {
+    if constexpr (NS < L) {
+        constexpr int REM = L / NS;
+        constexpr int RADIX = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        stage<V, L, NLINES, T, RADIX, NS, QS>(s, tw, twstride);
+        fft_smem<V, L, NLINES, T, QS, NS * RADIX>(s, tw, twstride);
+    }
+}
+
+template <int L, int NL> constexpr int threads_for() {
+    return (L * NL / 16) < 32 ? 32 : (L * NL / 16);
+}
+
+// Lines per tile: 8 complex float (64-byte row segments), 4 complex double.
+template <typename R> constexpr int tile_lines() { return sizeof(R) == 4 ? 8 : 4; }
+// Row pitch (complex elements) of the x-transformed spectrum and of the ring:
+// H = N/2 + 1 rounded up to a multiple of 8, so every row starts 64-byte aligned.
+constexpr int row_pitch(int N) { return ((N / 2 + 1) + 7) & ~7; }
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+// 16 bytes, cached in L2 only: for data another CTA of the same launch wrote.
+__device__ __forceinline__ void cp_async16_l2(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy a tile of NL-element row segments (row stride `pitch` elements) into
+// s[q * QS + b]; elements with b >= valid are zero.
+template <typename V, int ROWS, int NL, int T, int QS>
+__device__ __forceinline__ void load_tile(V* s, const V* __restrict__ src, long long pitch, int valid) {
+#pragma unroll
+    for (int e = threadIdx.x; e < ROWS * NL; e += T) {
+        const int q = e / NL, b = e % NL;
+        if (b < valid) {
+            if constexpr (sizeof(V) == 8) cp_async8(&s[q * QS + b], src + q * pitch + b);
+            else cp_async16(&s[q * QS + b], src + q * pitch + b);
+        } else {
+            s[q * QS + b] = mk<V>(0, 0);
+        }
+    }
+}
+
+template <typename K> int set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
+    return BSPLINE_OK;
+}
+
+}  // namespace fftc
+}  // namespace bs

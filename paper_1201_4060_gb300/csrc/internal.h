@@ -92,4 +92,13 @@ int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_
 int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs,
                      const double* x, int64_t P, void* out_u, void* out_grad, int flags);
 
+// Adjoint: bin/sort, then spread cotangents into g_coef (accumulate; skipped
+// if NULL) and write position gradients g_x (skipped if NULL).
+int launch_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, const void* g_u,
+                             const void* g_grad, void* g_coef, double* g_x);
+// Adjoint of launch_coeffs: g_u_hat (half spectrum) from g_coef, through the
+// transform workspace (grown by the caller).
+int launch_adjoint_transform(bspline_plan_s* p, const void* g_coef, void* g_u_hat);
+size_t coeffs_workspace_bytes(const bspline_plan_s* p);
+
 }  // namespace bs

@@ -16,7 +16,7 @@
 // Y00 = sum_y w_y Z0, Y10 = sum_y w'_y Z0, Y01 = sum_y w_y Z1 (3 n^2), then
 // u = sum_x w_x Y00, du/dx = sum_x w'_x Y00, du/dy = sum_x w_x Y10,
 // du/dz = sum_x w_x Y01 (4 n), derivatives scaled by N / L.
-#include "particles.cuh"
+#include "adjoint.cuh"
 
 namespace bs {
 
@@ -25,6 +25,11 @@ namespace bs {
 BS_ORDERS(BS_GATHER_EXTERN, double, double, double)
 BS_ORDERS(BS_GATHER_EXTERN, float, float, float)
 BS_ORDERS(BS_GATHER_EXTERN, __nv_bfloat16, float, float)
+#define BS_ADJ_ORDERS(M, CT, TR) M(2, CT, TR) M(3, CT, TR) M(4, CT, TR) M(5, CT, TR) M(6, CT, TR) M(7, CT, TR) \
+    M(8, CT, TR)
+BS_ADJ_ORDERS(BS_ADJOINT_EXTERN, double, double)
+BS_ADJ_ORDERS(BS_ADJOINT_EXTERN, float, float)
+BS_ADJ_ORDERS(BS_ADJOINT_EXTERN, __nv_bfloat16, float)
 
 namespace {
 using namespace gather_impl;
@@ -179,8 +184,10 @@ __global__ void scatter_kernel(long long P, unsigned NB, Ws<TR> w, OT* __restric
         const unsigned k = w.key[p];
         if (k >= NB) {
             const OT nan = (OT)NAN;
+            if (out_u) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) out_u[3 * p + i] = nan;
+                for (int i = 0; i < 3; ++i) out_u[3 * p + i] = nan;
+            }
             if (out_grad) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) out_grad[9 * p + i] = nan;
@@ -276,7 +283,81 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     return set_cuda_error(cudaGetLastError());
 }
 
+template <typename CT, typename TR>
+int adjoint_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, long long items,
+                  const void* g_u, const void* g_grad, void* g_coef, double* g_x) {
+    using adjoint_impl::run_adjoint;
+    switch (p->order) {
+        case 2: return run_adjoint<2, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 3: return run_adjoint<3, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 4: return run_adjoint<4, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 5: return run_adjoint<5, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 6: return run_adjoint<6, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 7: return run_adjoint<7, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 8: return run_adjoint<8, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+    }
+    return BSPLINE_ERR_UNSUPPORTED_ORDER;
+}
+
+// Adjoint of the particle side: the same bin / scan / scatter as run_interp,
+// then the spread into g_coef and the position gradient g_x (either may be
+// skipped).  Non-finite positions contribute nothing and get NaN in g_x.
+template <typename CT, typename TR>
+int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, const void* g_u,
+                          const void* g_grad, void* g_coef, double* g_x) {
+    const int nbx = bricks_per_axis(p->N, p->dtype);
+    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
+    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    Ws<TR> w;
+    const size_t need = carve<TR>(&w, nullptr, NB, P);
+    int rc = p->pws.grow(need);
+    if (rc) return rc;
+    carve<TR>(&w, p->pws.ptr, NB, P);
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
+    {
+        StageTimer tm(p, BSPLINE_STAGE_BIN);
+        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
+                                                         bshift, NB, w, p->d_status);
+    }
+    {
+        StageTimer tm(p, BSPLINE_STAGE_SCAN);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
+    }
+    {
+        StageTimer tm(p, BSPLINE_STAGE_SCATTER);
+        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, g_x, nullptr);
+    }
+    const long long items = (long long)NB + (P + kChunk - 1) / kChunk;
+    if (g_coef) {
+        StageTimer tm(p, BSPLINE_STAGE_SPREAD);
+        rc = adjoint_order<CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, nullptr);
+        if (rc) return rc;
+    }
+    if (g_x) {
+        StageTimer tm(p, BSPLINE_STAGE_GRAD_X);
+        rc = adjoint_order<CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, nullptr, g_x);
+        if (rc) return rc;
+    }
+    return set_cuda_error(cudaGetLastError());
+}
+
 }  // namespace
+
+int launch_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, const void* g_u,
+                             const void* g_grad, void* g_coef, double* g_x) {
+    switch (p->dtype) {
+        case BSPLINE_F64:
+            return run_adjoint_particles<double, double>(p, coeffs, x, P, g_u, g_grad, g_coef, g_x);
+        case BSPLINE_F32:
+            return run_adjoint_particles<float, float>(p, coeffs, x, P, g_u, g_grad, g_coef, g_x);
+        case BSPLINE_BF16:
+            return run_adjoint_particles<__nv_bfloat16, float>(p, coeffs, x, P, g_u, g_grad, g_coef, g_x);
+    }
+    return BSPLINE_ERR_INVALID_ARG;
+}
 
 int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs, const double* x,
                      int64_t P, void* out_u, void* out_grad, int flags) {

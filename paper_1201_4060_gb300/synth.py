@@ -159,6 +159,8 @@ WORKLOADS = {
     "orders256": dict(N=256, order=(2, 4, 6, 8), P=1_000_000, field_seed=1203, particle_seed=4062,
                       particles="uniform_sorted"),
     "throughput512": dict(N=512, order=6, P=1 << 24, field_seed=1204, particle_seed=4063, particles="clustered"),
+    # adjoint (differentiation): N(0, 1) cotangents on u and grad u, seed = particle_seed + 1
+    "adjoint256": dict(N=256, order=4, P=1 << 22, field_seed=1206, particle_seed=4065, particles="uniform"),
 }
 
 

@@ -1,0 +1,285 @@
+"""Parity of the adjoint (differentiation) path with the oracle's adjoint.
+
+bspline_spread_adjoint through the C ABI against oracle.spread,
+oracle.adjoint_transform and oracle.position_gradient on the same seeded
+inputs; at sizes the oracle cannot follow, the inner-product identities
+<g, F a> = <F^T g, a> against the GPU forward path, and finite differences
+of the FP64 forward path.
+
+Tolerances (normwise: max |gpu - oracle| / max |oracle|): 1e-12 for F64
+plans.  F32 plans: the spread sums FP32 products into FP32 (shared-memory
+and global atomics, order not fixed), TOL32_SPREAD; the transposed
+transform has the forward transform's ~log2(N^3) rounding steps,
+TOL32_FFT; the position gradient contracts second-derivative weights that
+sum to zero against FP32 coefficients (cancellation on top of the forward
+contraction), TOL32_GX.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bspline_oracle as O
+from paper_1201_4060_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L = 2.0 * math.pi
+TOL64 = 1e-12
+TOL32_SPREAD = 1e-5
+TOL32_FFT = 2e-5
+TOL32_GX = 2e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1201_4060_gb300 import _build
+    _build.build()
+    from paper_1201_4060_gb300 import bspline
+    assert torch.cuda.is_available()
+    return bspline
+
+
+def normwise(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _cot(plan, P, seed, with_grad=True):
+    gu, gg = synth.cotangents(P, seed)
+    gu_t = _dev(gu, plan.out_dtype)
+    gg_t = _dev(gg, plan.out_dtype) if with_grad else None
+    # the oracle sees exactly the values the GPU sees
+    gu = gu_t.double().cpu().numpy()
+    gg = gg_t.double().cpu().numpy() if with_grad else None
+    return gu_t, gg_t, gu, gg
+
+
+# ----------------------------------------------------------------------- transposed transform
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("kind", ["interp", "l2"])
+def test_adjoint_transform_f64(B, N, order, kind):
+    plan = B.Plan(N, order, "f64", prefilter=kind)
+    g = np.random.default_rng(N + 10 * order).standard_normal((3, N, N, N))
+    gc = _dev(g, torch.float64)
+    x = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    gh, gx, _ = plan.spread_adjoint(x, g_coef=gc)
+    assert gx is None
+    assert normwise(gh.cpu().numpy(), O.adjoint_transform(g, order, kind)) < TOL64
+
+
+@pytest.mark.parametrize("N", [16, 128])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_adjoint_transform_f32(B, N, dtype):
+    plan = B.Plan(N, 6, dtype)
+    g = np.random.default_rng(N).standard_normal((3, N, N, N)).astype(np.float32)
+    gh, _, _ = plan.spread_adjoint(torch.empty((0, 3), dtype=torch.float64, device="cuda"),
+                                   g_coef=_dev(g, torch.float32))
+    assert gh.dtype == torch.complex64
+    assert normwise(gh.cpu().numpy(), O.adjoint_transform(g.astype(np.float64), 6)) < TOL32_FFT
+
+
+# ----------------------------------------------------------------------- spread
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("particles", ["uniform", "clustered"])
+def test_spread_f64(B, order, particles):
+    N, P = 16, 3000
+    x = synth.make_particles(particles, P, seed=order, N=N)
+    plan = B.Plan(N, order, "f64")
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=order + 100)
+    _, _, gc = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, u_hat_grad=False)
+    assert normwise(gc.cpu().numpy(), O.spread(x, gu, gg, N, order)) < TOL64
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_spread_f32(B, order, dtype):
+    N, P = 32, 20000
+    x = synth.clustered_particles(P, seed=order)
+    plan = B.Plan(N, order, dtype)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=order + 200)
+    _, _, gc = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, u_hat_grad=False)
+    assert normwise(gc.cpu().numpy(), O.spread(x, gu, gg, N, order)) < TOL32_SPREAD
+
+
+def test_spread_accumulates_and_optional_cotangents(B):
+    N, order, P = 16, 4, 500
+    x = _dev(synth.uniform_particles(P, seed=3), torch.float64)
+    plan = B.Plan(N, order, "f64")
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=4)
+    xs = x.cpu().numpy()
+    _, _, a = plan.spread_adjoint(x, gu_t, gg_t, u_hat_grad=False)
+    _, _, a2 = plan.spread_adjoint(x, gu_t, gg_t, g_coef=a.clone(), u_hat_grad=False)
+    assert normwise(a2.cpu().numpy(), 2 * a.cpu().numpy()) < TOL64
+    _, _, b = plan.spread_adjoint(x, gu_t, None, u_hat_grad=False)           # g_grad = 0
+    assert normwise(b.cpu().numpy(), O.spread(xs, gu, None, N, order)) < TOL64
+    _, _, c = plan.spread_adjoint(x, None, gg_t, u_hat_grad=False)           # g_u = 0
+    assert normwise(c.cpu().numpy(), O.spread(xs, np.zeros_like(gu), gg, N, order)) < TOL64
+
+
+# ----------------------------------------------------------------------- position gradient
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("with_grad", [True, False])
+def test_position_gradient_f64(B, order, with_grad):
+    N, P = 16, 2000
+    half = synth.kolmogorov_field(N, seed=order).dense()
+    x = synth.clustered_particles(P, seed=order + 5)
+    plan = B.Plan(N, order, "f64")
+    coef = plan.coeffs(_dev(half, torch.complex128))
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=order + 300, with_grad=with_grad)
+    _, gx, _ = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, coef=coef, u_hat_grad=False)
+    ref = O.position_gradient(O.coefficients(half, order), x, gu, gg, order)
+    assert normwise(gx.cpu().numpy(), ref) < TOL64
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_position_gradient_f32(B, order, dtype):
+    N, P = 32, 5000
+    half = synth.kolmogorov_field(N, seed=order).dense()
+    x = synth.clustered_particles(P, seed=order + 7)
+    plan = B.Plan(N, order, dtype)
+    coef = plan.coeffs(_dev(half, torch.complex64))
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=order + 400)
+    _, gx, _ = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, coef=coef, u_hat_grad=False)
+    # against the oracle on the GPU's own (rounded) coefficients: isolates the adjoint's arithmetic
+    c64 = coef.double().cpu().numpy()
+    err = normwise(gx.cpu().numpy(), O.position_gradient(c64, x, gu, gg, order))
+    assert err < (TOL32_GX if dtype == "f32" else 5e-2)
+
+
+def test_position_gradient_matches_fd_of_gpu_forward(B):
+    N, order, P = 32, 6, 4096
+    half = synth.kolmogorov_field(N, seed=8).dense()
+    plan = B.Plan(N, order, "f64")
+    coef = plan.coeffs(_dev(half, torch.complex128))
+    x = synth.uniform_particles(P, seed=9)
+    s = x * N / L - order / 2
+    x = np.where(np.abs(s - np.round(s)) < 0.02, x + 0.05 * L / N, x)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=10)
+    xt = _dev(x, torch.float64)
+    _, gx, _ = plan.spread_adjoint(xt, gu_t, gg_t, coef=coef, u_hat_grad=False)
+    gx = gx.cpu().numpy()
+
+    def loss(xx):
+        u, g = plan.interp(coef, _dev(xx, torch.float64))
+        return (u.cpu().numpy() * gu).sum(axis=1) + (g.cpu().numpy() * gg).sum(axis=(1, 2))
+
+    h = 1e-6
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        fd = (loss(x + e) - loss(x - e)) / (2 * h)
+        assert normwise(gx[:, d], fd) < 1e-6
+
+
+# ----------------------------------------------------------------------- whole chain, autograd
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_autograd_full_chain(B, dtype):
+    from paper_1201_4060_gb300.autograd import interpolate
+    N, order, P = 16, 4, 3000
+    half = synth.kolmogorov_field(N, seed=21).dense()
+    x = synth.clustered_particles(P, seed=22)
+    plan = B.Plan(N, order, dtype)
+    uh = _dev(half, plan.uhat_dtype).requires_grad_(True)
+    xt = _dev(x, torch.float64).requires_grad_(True)
+    u, g = interpolate(uh, xt, plan)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=23)
+    ((u * gu_t).sum() + (g * gg_t).sum()).backward()
+    ref_h, ref_x, _ = O.interpolate_adjoint(uh.detach().cpu().numpy().astype(np.complex128), x, gu, gg, order)
+    tol_h, tol_x = (TOL64, TOL64) if dtype == "f64" else (TOL32_FFT + TOL32_SPREAD, 1e-3)
+    assert uh.grad.dtype == uh.dtype and xt.grad.dtype == torch.float64
+    assert normwise(uh.grad.cpu().numpy(), ref_h) < tol_h
+    assert normwise(xt.grad.cpu().numpy(), ref_x) < tol_x
+
+
+# ----------------------------------------------------------------------- identities at size
+
+def test_inner_product_identities_f32_at_256(B):
+    """<g_u, u> + <g_grad, grad u> = <g_coef, coef> and <g_coef, coeffs(a)> = Re <adj(g_coef), a>."""
+    wl = synth.WORKLOADS["adjoint256"]
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    plan = B.Plan(N, order, "f32")
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    a = _dev(F.dense(), torch.complex64)
+    coef = plan.coeffs(a)
+    x = _dev(synth.make_particles(wl["particles"], P, wl["particle_seed"], N), torch.float64)
+    gu_t, gg_t, _, _ = _cot(plan, P, seed=wl["particle_seed"] + 1)
+    u, g = plan.interp(coef, x)
+    gh, gx, gc = plan.spread_adjoint(x, gu_t, gg_t, coef=coef)
+    lhs = (gu_t.double() * u.double()).sum() + (gg_t.double() * g.double()).sum()
+    rhs = (gc.double() * coef.double()).sum()
+    scale = (gu_t.double() * u.double()).abs().sum() + (gg_t.double() * g.double()).abs().sum()
+    assert abs(float(lhs - rhs)) < 1e-5 * float(scale)
+    lhs2 = (gc.double() * coef.double()).sum()
+    rhs2 = (torch.conj(gh.to(torch.complex128)) * a.to(torch.complex128)).real.sum()
+    scale2 = (gc.double().abs() * coef.double().abs()).sum()
+    assert abs(float(lhs2 - rhs2)) < 1e-5 * float(scale2)
+    assert torch.isfinite(gx).all()
+
+
+def test_workload_position_gradient_sampled_f32(B):
+    """Full-size adjoint launch; position gradients checked on sampled particles against the oracle."""
+    wl = synth.WORKLOADS["adjoint256"]
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    plan = B.Plan(N, order, "f32")
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    half = F.dense()
+    coef = plan.coeffs(_dev(half, torch.complex64))
+    xs = synth.make_particles(wl["particles"], P, wl["particle_seed"], N)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=wl["particle_seed"] + 1)
+    _, gx, _ = plan.spread_adjoint(_dev(xs, torch.float64), gu_t, gg_t, coef=coef, u_hat_grad=False)
+    idx = np.random.default_rng(0).choice(P, 256, replace=False)
+    ref = O.position_gradient(O.coefficients(half, order), xs[idx], gu[idx], gg[idx], order)
+    assert normwise(gx.cpu().numpy()[idx], ref) < 1e-3
+
+
+# ----------------------------------------------------------------------- edge cases
+
+def test_nonfinite_positions(B):
+    N, order, P = 16, 4, 64
+    half = synth.kolmogorov_field(N, seed=2).dense()
+    x = synth.uniform_particles(P, seed=5)
+    x[3, 0] = np.nan
+    x[10, 2] = np.inf
+    plan = B.Plan(N, order, "f64")
+    coef = plan.coeffs(_dev(half, torch.complex128))
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=6)
+    _, gx, gc = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, coef=coef, u_hat_grad=False)
+    assert plan.status() == 2
+    gx = gx.cpu().numpy()
+    assert np.isnan(gx[[3, 10]]).all()
+    ok = np.ones(P, bool)
+    ok[[3, 10]] = False
+    assert normwise(gx[ok], O.position_gradient(O.coefficients(half, order), x[ok], gu[ok], gg[ok], order)) < TOL64
+    assert normwise(gc.cpu().numpy(), O.spread(x, gu, gg, N, order)) < TOL64
+
+
+def test_abi_rejects_bad_adjoint_arguments(B):
+    plan = B.Plan(16, 4, "f32")
+    x = torch.zeros((8, 3), dtype=torch.float64, device="cuda")
+    gu = torch.zeros((8, 3), dtype=torch.float32, device="cuda")
+    gc = torch.zeros((3, 16, 16, 16), dtype=torch.float32, device="cuda")
+    gh = torch.zeros((3, 16, 16, 9), dtype=torch.complex64, device="cuda")
+    gx = torch.zeros((8, 3), dtype=torch.float64, device="cuda")
+    h = plan.handle
+    # g_u_hat needs g_coeffs; g_x needs coefficients; x is required for particle work
+    assert B.bspline_spread_adjoint(h, 0, x.data_ptr(), 8, gu.data_ptr(), 0, 0, gh.data_ptr(), 0) == B.ERR_INVALID_ARG
+    assert B.bspline_spread_adjoint(h, 0, x.data_ptr(), 8, gu.data_ptr(), 0, 0, 0, gx.data_ptr()) == B.ERR_INVALID_ARG
+    assert B.bspline_spread_adjoint(h, 0, 0, 8, gu.data_ptr(), 0, gc.data_ptr(), 0, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_spread_adjoint(h, 0, x.data_ptr(), -1, gu.data_ptr(), 0, gc.data_ptr(), 0, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_spread_adjoint(h, 0, x.data_ptr() + 4, 8, gu.data_ptr(), 0, gc.data_ptr(), 0, 0) \
+        == B.ERR_INVALID_ARG
+    # P = 0 with nothing to do is a no-op
+    assert B.bspline_spread_adjoint(h, 0, 0, 0, 0, 0, 0, 0, 0) == B.OK

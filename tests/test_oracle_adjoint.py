@@ -220,3 +220,22 @@ def test_full_chain_is_exact_linear_response(kind):
     lhs = loss(a + d) - loss(a)
     rhs = (np.conj(g_hat) * d).real.sum()
     assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(rhs))
+
+
+@pytest.mark.parametrize("kind", ["interp", "l2"])
+def test_adjoint_transform_matches_torch_autograd(kind):
+    # an independent transpose: PyTorch's reverse mode through irfftn, with the
+    # prefilter multiply written in torch (gradient convention dL/dRe + i dL/dIm)
+    torch = pytest.importorskip("torch")
+    N, n = 8, 4
+    rng = np.random.default_rng(13)
+    a = _random_half(N, rng)
+    g = rng.standard_normal((3, N, N, N))
+    c = O.prefilter(N, n) if kind == "interp" else O.prefilter_l2(N, n)
+    c3 = c[:, None, None] * c[None, :, None] * c[None, None, :N // 2 + 1]
+    at = torch.tensor(a, requires_grad=True)
+    coef = torch.fft.irfftn(at * torch.tensor(c3)[None], s=(N, N, N), dim=(1, 2, 3), norm="forward")
+    np.testing.assert_allclose(coef.detach().numpy(), O.coefficients(a, n, kind), atol=1e-12)
+    (coef * torch.tensor(g)).sum().backward()
+    ref = at.grad.numpy()
+    np.testing.assert_allclose(O.adjoint_transform(g, n, kind), ref, atol=1e-11 * np.abs(ref).max())
