@@ -219,7 +219,7 @@ def test_abi_rejects_bad_arguments_on_gpu(B):
     assert B.bspline_interp(h, p, p, 10, p, 0, 0) == B.ERR_INVALID_ARG           # grad NULL without flag
     assert B.bspline_interp(h, p, p, 10, p, p, 0x80) == B.ERR_INVALID_ARG        # unknown flag
     assert B.bspline_coeffs(h, p, p) == B.ERR_INVALID_ARG                        # aliasing
-    assert B.bspline_spread_adjoint(h, p, p, 10, p, p, p, 0, 0) == B.ERR_NOT_IMPLEMENTED
+    assert B.bspline_spread_adjoint(h, p, p, 10, p, p, 0, p, 0) == B.ERR_INVALID_ARG   # g_u_hat without g_coeffs
     assert B.bspline_plan_set_length(h, -1.0) == B.ERR_INVALID_ARG
 
 
