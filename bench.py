@@ -358,12 +358,79 @@ def run_ours(args):
                         "fft_ms": sum(st_64[s][0] / max(st_64[s][1], 1) for s in ("fft_x", "fft_yz"))}
         out["forms"] = forms
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=3)
+        out["adjoint"] = run_adjoint(B, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(samples=1 << 17)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_adjoint(B, device, steps=10, warmup=3):
+    """Adjoint (differentiation) workload: 256^3 Kolmogorov field, cubic B-spline, 2^22 uniform particles,
+    N(0, 1) cotangents on u and grad u.  One step = one bspline_spread_adjoint call producing g_u_hat (through
+    the spread onto the coefficients and the transposed transform) and g_x, after zeroing g_coeffs."""
+    import torch
+    from paper_1201_4060_gb300 import synth
+    wl = synth.WORKLOADS["adjoint256"]
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    plan = B.Plan(N, order, "f32")
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
+    coef = plan.coeffs(uh)
+    x = torch.from_numpy(synth.make_particles(wl["particles"], P, wl["particle_seed"], N)).to(device)
+    gu_h, gg_h = synth.cotangents(P, wl["particle_seed"] + 1)
+    gu = torch.from_numpy(gu_h).float().to(device)
+    gg = torch.from_numpy(gg_h).float().to(device)
+    g_coef = torch.zeros((3, N, N, N), dtype=torch.float32, device=device)
+    g_uh = torch.empty((3, N, N, N // 2 + 1), dtype=torch.complex64, device=device)
+    g_x = torch.empty((P, 3), dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream()
+    plan._stream(stream)
+
+    def step():
+        g_coef.zero_()
+        rc = B.bspline_spread_adjoint(plan.handle, coef.data_ptr(), x.data_ptr(), P, gu.data_ptr(), gg.data_ptr(),
+                                      g_coef.data_ptr(), g_uh.data_ptr(), g_x.data_ptr())
+        if rc != B.OK:
+            raise B.BSplineError(rc, "bspline_spread_adjoint")
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = plan.stage_times()
+    plan.set_timing(False)
+    names = ["bin", "scan", "scatter", "spread", "grad_x", "adj_fft"]
+    stages = {s: st[s][0] / max(st[s][1], 1) for s in names}
+    rec = 16
+    coef_b, spec_b = 3 * N ** 3 * 4, 3 * N * N * (N // 2 + 1) * 8
+    hp = ((N // 2 + 1) + 7) // 8 * 8
+    work_b = 3 * N * N * hp * 8
+    abytes = {"spread": P * (rec + 4) + P * 48 + 2 * coef_b,          # records, cotangents, g_coef += (read + write)
+              "grad_x": coef_b + P * (rec + 4) + P * 48 + P * 24,     # coefficients once, records, cotangents, g_x
+              "adj_fft": coef_b + work_b + 2 * work_b + work_b + spec_b}  # z: read g_coef, write; y: rw; x: r, write
+    pk = peaks()
+    out = {"workload": f"{N}^3 x 3-component Kolmogorov field (seed {wl['field_seed']}), order-{order} B-spline, "
+                       f"{P} uniform particles (seed {wl['particle_seed']}), N(0,1) cotangents on u and grad u "
+                       f"(seed {wl['particle_seed'] + 1}), f32 coefficients, f64 positions",
+           "particles_per_s": P / (ms / 1e3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "step": "g_coeffs zeroed, bin+sort, spread onto coefficients, position gradients, transposed transform",
+           "stages_ms": stages,
+           "hbm_frac": {s: abytes[s] / (stages[s] / 1e3) / 1e9 / pk["hbm_gbs"] for s in abytes if stages[s] > 0}}
+    del uh, coef, x, gu, gg, g_coef, g_uh, g_x
+    plan.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(B, wl, F, xs, device, steps):

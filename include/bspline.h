@@ -120,8 +120,9 @@ int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int
  *   g_u     device [P][3] of the output type, or NULL (= zero);
  *   g_grad  device [P][3][3] of the output type, or NULL (= zero);
  *   g_coeffs device [3][N][N][N] of the OUTPUT type (double for F64 plans,
- *           float otherwise), or NULL: the spread of the cotangents onto the
- *           coefficients is ADDED to it (callers zero it for a fresh gradient);
+ *           float otherwise), 16-byte aligned, or NULL: the spread of the
+ *           cotangents onto the coefficients is ADDED to it (callers zero it
+ *           for a fresh gradient);
  *   g_u_hat device half spectrum [3][N][N][N/2+1], complex double (F64) or
  *           complex float, or NULL: overwritten with the adjoint of the
  *           coefficient transform applied to g_coeffs (after the spread),

@@ -345,7 +345,7 @@ int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double
     if (P > 0 && g_x && !coeffs) return BSPLINE_ERR_INVALID_ARG;
     const size_t ob = out_bytes(plan->dtype);
     if (!aligned(coeffs, 16) || !aligned(x, 8) || !aligned(g_u, ob) || !aligned(g_grad, ob) ||
-        !aligned(g_coeffs, ob) || !aligned(g_u_hat, 16) || !aligned(g_x, 8))
+        !aligned(g_coeffs, 16) || !aligned(g_u_hat, 16) || !aligned(g_x, 8))
         return BSPLINE_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     if (!g.ok) return BSPLINE_ERR_CUDA;

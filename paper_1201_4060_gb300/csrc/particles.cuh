@@ -403,23 +403,41 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
         const unsigned j16 = __shfl_sync(0xffffffffu, my_bucket, src16);   // ranks j < j16 hold >= 16
         const unsigned pos16 = __reduce_add_sync(0xffffffffu, min(my_bucket, j16));
         const unsigned njobs = j16 + ((unsigned)n - pos16 + 31u) / 32u;
-        for (unsigned j = warp; j < njobs; j += NW) {
-            unsigned lo, hi;
+        auto job_range = [&](unsigned j, unsigned* lo, unsigned* hi) {
             if (j < j16) {
-                lo = __reduce_add_sync(0xffffffffu, min(my_bucket, j));
-                hi = __reduce_add_sync(0xffffffffu, min(my_bucket, j + 1));
+                *lo = __reduce_add_sync(0xffffffffu, min(my_bucket, j));
+                *hi = __reduce_add_sync(0xffffffffu, min(my_bucket, j + 1));
             } else {
-                lo = pos16 + 32u * (j - j16);
-                hi = min((unsigned)n, lo + 32u);
+                *lo = pos16 + 32u * (j - j16);
+                *hi = min((unsigned)n, *lo + 32u);
             }
+        };
+        // the next job's record and index are loaded while the current one is evaluated
+        Rec<TR> rc_n;
+        unsigned idx_n = 0;
+        bool v_n = false;
+        auto fetch = [&](unsigned j) {
+            unsigned lo, hi;
+            job_range(j, &lo, &hi);
             const unsigned pos = lo + (unsigned)lane;
-            if (pos < hi) {
+            v_n = pos < hi;
+            if (v_n) {
                 const unsigned i = c0 + s_order[pos];
-                const Rec<TR> rc = w.s_rec[i];
+                rc_n = w.s_rec[i];
+                idx_n = w.s_idx[i];
+            }
+        };
+        if ((unsigned)warp < njobs) fetch(warp);
+        for (unsigned j = warp; j < njobs; j += NW) {
+            const Rec<TR> rc = rc_n;
+            const unsigned idx = idx_n;
+            const bool v = v_n;
+            v_n = false;
+            if (j + NW < njobs) fetch(j + NW);
+            if (v) {
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(rc.cell & 1023u) - z0;
-                const unsigned idx = w.s_idx[i];
                 float u[3], g[9];
                 eval_particle_x2<ORD, GRAD, E>(tile + (ox * E + oy) * E + oz, (float)rc.t[0], (float)rc.t[1],
                                                 (float)rc.t[2], dscale, u, g);
