@@ -75,12 +75,7 @@ template <typename TR>
 __device__ __forceinline__ bool item_range(const Ws<TR>& w, unsigned NB, unsigned item, unsigned* brick,
                                            unsigned* beg, unsigned* end) {
     if (item >= w.chunk[NB]) return false;
-    unsigned lo = 0, hi = NB;                           // largest b with chunk[b] <= item
-    while (hi - lo > 1) {
-        const unsigned mid = (lo + hi) >> 1;
-        if (w.chunk[mid] <= item) lo = mid;
-        else hi = mid;
-    }
+    const unsigned lo = w.item[item];
     *brick = lo;
     *beg = w.offset[lo] + (item - w.chunk[lo]) * kChunk;
     *end = min(*beg + kChunk, w.offset[lo + 1]);

@@ -134,9 +134,11 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
 // ------------------------------------------------------------------ scan (single CTA)
 // Exclusive prefix sums over the NB + 1 bins (NB bricks, then the invalid
 // bin): offset[] of the counts, and chunk[] (bricks only) of the number of
-// gather work items per brick, ceil(count / kChunk).
+// gather work items per brick, ceil(count / kChunk); item[] maps each work
+// item back to its brick.
 __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
-                                                    unsigned* __restrict__ chunk, unsigned NB) {
+                                                    unsigned* __restrict__ chunk, unsigned* __restrict__ item,
+                                                    unsigned NB) {
     __shared__ unsigned part[1024], partc[1024];
     const unsigned n = NB + 1;
     const unsigned t = threadIdx.x;
@@ -166,7 +168,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
         run += ci;
         if (i < NB) {
             chunk[i] = runc;
-            runc += (ci + kChunk - 1) / kChunk;
+            const unsigned nc = (ci + kChunk - 1) / kChunk;
+            for (unsigned k = 0; k < nc; ++k) item[runc + k] = i;
+            runc += nc;
         }
     }
     if (t == 1023) {
@@ -244,7 +248,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, w.item, NB);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
@@ -276,7 +280,7 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
                                                      bshift, NB, w, status);
-    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
+    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, w.item, NB);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
     if (rc) return rc;
@@ -324,7 +328,7 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, NB);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, w.item, NB);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);

@@ -26,6 +26,7 @@ template <typename TR> struct Ws {
     unsigned* count;    // [NB + 1]  particles per brick; slot NB = invalid positions
     unsigned* offset;   // [NB + 2]  exclusive prefix sum of count
     unsigned* chunk;    // [NB + 1]  exclusive prefix sum of ceil(count / kChunk): first work item of a brick
+    unsigned* item;     // [NB + ceil(P / kChunk)]  brick of each work item (the first chunk[NB] are set)
     long long P;        // particles
     unsigned* key;      // [P]
     unsigned* rank;     // [P]
@@ -47,6 +48,7 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     w->count = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 2));
     w->chunk = (unsigned*)take(sizeof(unsigned) * (NB + 1));
+    w->item = (unsigned*)take(sizeof(unsigned) * (NB + (P + kChunk - 1) / kChunk));
     w->key = (unsigned*)take(sizeof(unsigned) * P);
     w->rank = (unsigned*)take(sizeof(unsigned) * P);
     w->rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
@@ -343,13 +345,7 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
     __shared__ unsigned short s_order[kChunk];
     const unsigned item = blockIdx.x;
     if (item >= w.chunk[NB]) return;
-    unsigned lo_b = 0, hi_b = NB;                         // largest b with chunk[b] <= item
-    while (hi_b - lo_b > 1) {
-        const unsigned mid = (lo_b + hi_b) >> 1;
-        if (w.chunk[mid] <= item) lo_b = mid;
-        else hi_b = mid;
-    }
-    const unsigned brick = lo_b;
+    const unsigned brick = w.item[item];
     const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * kChunk;
     const unsigned end = w.offset[brick + 1];
     const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
@@ -358,8 +354,7 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
     {
         const int n = (int)min(kChunk, end - c0);
         if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
-        cp_async_wait_all();
-        __syncthreads();                                  // also orders the tile staging before first use
+        __syncthreads();                                  // the tile copies stay in flight while bucketing
         for (int i = threadIdx.x; i < n; i += kGatherThreads) {
             const unsigned cp = w.s_rec[c0 + i].cell;
             const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
@@ -385,7 +380,8 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
             }
             s_order[pos] = (unsigned short)i;
         }
-        __syncthreads();
+        cp_async_wait_all();
+        __syncthreads();                                  // tile and order ready
         // Warp jobs over that order.  Rank j holds #{banks with more than j
         // particles} particles, non-increasing in j.  While a rank holds at
         // least 16 particles it is one job (every load conflict-free); the
