@@ -39,39 +39,40 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
                 const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
-    constexpr int QS = NL;
+    static_assert(T % NL == 0, "each thread stays on one line");
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
     constexpr long long NH = (long long)N * H;
     constexpr long long TILES = (NH + NL - 1) / NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* s = tws + N;
-    R* cyz = reinterpret_cast<R*>(s + N * QS);
     const int t = threadIdx.x;
     const int comp = (int)(blockIdx.x / TILES);
     const long long b0 = (blockIdx.x % TILES) * NL;
     const int valid = (int)std::min<long long>(NL, NH - b0);
-    load_tile<V, N, NL, T, QS>(s, in + (long long)comp * N * NH + b0, NH, valid);
     for (int m = t; m < N; m += T) tws[m] = tw[m];
-    if (t < NL) cyz[t] = (t < valid) ? c[(int)((b0 + t) / H)] * c[(int)((b0 + t) % H)] : R(0);
-    cp_async_wait_all();
-    __syncthreads();
-    for (int e = t; e < N * NL; e += T) {                 // prefilter c(kx) c(ky) c(kz)
-        const int q = e / NL, b = e % NL;
-        const R f = __ldg(&c[q]) * cyz[b];
-        V& a = s[q * QS + b];
-        a = mk<V>(a.x * f, a.y * f);
-    }
-    __syncthreads();
-    fft_smem<V, N, NL, T, QS>(s, tws, 1);
-    V* dst = out + (long long)comp * N * N * HP;
-    for (int e = t; e < N * NL; e += T) {
-        const int q = e / NL, b = e % NL;
-        if (b < valid) {
-            const long long bb = b0 + b;
-            const int ky = (int)(bb / H), kz = (int)(bb % H);
-            dst[((long long)q * N + ky) * HP + kz] = s[q * QS + b];
-        }
+    // this thread's line: batch index b0 + bl = ky H + kz; prefilter c(ky) c(kz) of the line
+    const int bl = t % NL;
+    const long long bb = b0 + bl;
+    const int ky = (int)(bb / H), kz = (int)(bb % H);
+    const R cyz = (bl < valid) ? c[ky] * c[kz] : R(0);
+    const V* src = in + (long long)comp * N * NH + b0;
+    V* dst = out + (long long)comp * N * N * HP + (long long)ky * HP + kz;
+    auto ld = [&](int q, int b) -> V {                   // prefilter c(kx) c(ky) c(kz) on load
+        if (b >= valid) return mk<V>(R(0), R(0));
+        const V a = src[(long long)q * NH + b];
+        const R f = __ldg(&c[q]) * cyz;
+        return mk<V>(a.x * f, a.y * f);
+    };
+    auto st = [&](int q, int b, V v) {
+        if (b < valid) dst[(long long)q * N * HP] = v;
+    };
+    if constexpr (radix_for(N) == N) {
+        stage_single<V, N, NL, T>(ld, st);
+    } else {
+        stage_first<V, N, NL, T, NL>(s, ld);            // its barrier also publishes the twiddles
+        stages_mid<V, N, NL, T, NL, radix_for(N)>(s, tws, 1);
+        stage_last<V, N, NL, T, NL, false>(s, tws, 1, st);
     }
 }
 
@@ -170,11 +171,17 @@ __device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, 
 
 template <int N, int NL> constexpr int z_rows() { return (2 * NL < N) ? 2 * NL : N; }
 
+// Row pitch of the staged ring rows of a Z item: HP plus 16 bytes of skew, so
+// that the rows of one warp access spread over all banks (row stride an odd
+// multiple of 16 bytes modulo 128).
+template <typename V, int N> constexpr int z_row_pitch() { return row_pitch(N) + 16 / (int)sizeof(V); }
+
 template <typename R, int N, int NL>
 constexpr size_t yz_smem_elems() {
-    constexpr int HP = row_pitch(N), NR = z_rows<N, NL>();
+    using V = typename Cx<R>::T;
+    constexpr int NR = z_rows<N, NL>();
     constexpr size_t y = (size_t)N * NL;
-    constexpr size_t z = (size_t)NR * HP + (size_t)(N / 2) * (NR + 1);
+    constexpr size_t z = (size_t)NR * z_row_pitch<V, N>() + (size_t)(N / 2) * (NR + 1);
     return N + (y > z ? y : z);
 }
 
@@ -199,11 +206,12 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     constexpr int IPP = TPZ + ZPP;
     constexpr long long PLANES = 3LL * N;
     constexpr int CHUNKS = HP * (int)sizeof(V) / 16;    // 16-byte pieces of one ring row
+    constexpr int RP = z_row_pitch<V, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* buf = tws + N;                                   // Y: [N][QY] tile
-    V* raw = buf;                                       // Z: NR ring rows, pitch HP
-    V* trans = buf + NR * HP;                           // Z: [M][QZ] transform buffer
+    V* raw = buf;                                       // Z: NR ring rows, pitch RP
+    V* trans = buf + NR * RP;                           // Z: [M][QZ] transform buffer
     __shared__ unsigned s_item, s_ok;
     unsigned* next = ctr;
     unsigned* done_y = ctr + 1;
@@ -224,15 +232,21 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
             const int kz0 = r * NL;
             const int valid = std::min(NL, H - kz0);
-            load_tile<V, N, NL, T, QY>(buf, w + pl * N * HP + kz0, HP, valid);
-            cp_async_wait_all();
-            __syncthreads();
-            fft_smem<V, N, NL, T, QY>(buf, tws, 1);
-            // the slot is free once the Z items of the plane that used it before have read it
-            if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
-            for (int e = t; e < N * NL; e += T) {
-                const int q = e / NL, b = e % NL;
-                if (b < valid) slot[(long long)q * HP + kz0 + b] = buf[q * QY + b];
+            const V* src = w + pl * N * HP + kz0;
+            V* dst = slot + kz0;
+            auto ld = [&](int q, int b) -> V { return (b < valid) ? src[(long long)q * HP + b] : mk<V>(R(0), R(0)); };
+            auto st = [&](int q, int b, V v) {
+                if (b < valid) dst[(long long)q * HP + b] = v;
+            };
+            if constexpr (radix_for(N) == N) {
+                if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
+                stage_single<V, N, NL, T>(ld, st);
+            } else {
+                stage_first<V, N, NL, T, QY>(buf, ld);
+                stages_mid<V, N, NL, T, QY, radix_for(N)>(buf, tws, 1);
+                // the slot is free once the Z items of the plane that used it before have read it
+                if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
+                stage_last<V, N, NL, T, QY, false>(buf, tws, 1, st);
             }
             __syncthreads();
             if (t == 0 && !drop_signals) {
@@ -245,34 +259,33 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             const int y0 = (r - TPZ) * NR;
             const unsigned char* src = reinterpret_cast<const unsigned char*>(slot + (long long)y0 * HP);
             unsigned char* dstb = reinterpret_cast<unsigned char*>(raw);
-            for (int j = t; j < NR * CHUNKS; j += T) cp_async16_l2(dstb + 16 * j, src + 16 * j);
+            for (int j = t; j < NR * CHUNKS; j += T) {
+                const int row = j / CHUNKS, k = j - row * CHUNKS;
+                cp_async16_l2(dstb + (size_t)row * RP * sizeof(V) + 16 * k, src + (size_t)row * HP * sizeof(V) + 16 * k);
+            }
             cp_async_wait_all();
             __syncthreads();                            // the slot's rows are read: release it
             if (t == 0) {
                 __threadfence();
                 atomicAdd(&done_z[pl], 1u);
             }
-            for (int e = t; e < NR * M; e += T) {
-                const int b = e / M, k = e % M;
-                const V* row = raw + b * HP;
+            auto ld = [&](int k, int b) -> V {          // even/odd split of the half spectrum
+                const V* row = raw + b * RP;
                 const V a = row[k], c = row[M - k];     // k = 0: X[0] and X[M]
-                V z;
-                if (k == 0) {
-                    z = mk<V>(a.x + c.x, a.x - c.x);
-                } else {
-                    const V bb = mk<V>(c.x, -c.y);
-                    const V E = cadd(a, bb);
-                    const V O = cmul(csub(a, bb), tws[k]);
-                    z = mk<V>(E.x - O.y, E.y + O.x);
-                }
-                trans[k * QZ + b] = z;
-            }
-            __syncthreads();
-            fft_smem<V, M, NR, T, QZ>(trans, tws, 2);
+                if (k == 0) return mk<V>(a.x + c.x, a.x - c.x);
+                const V bb = mk<V>(c.x, -c.y);
+                const V E = cadd(a, bb);
+                const V O = cmul(csub(a, bb), tws[k]);
+                return mk<V>(E.x - O.y, E.y + O.x);
+            };
             OutT* dst = out + (pl * N + y0) * (long long)N;
-            for (int e = t; e < NR * M; e += T) {
-                const int b = e / M, m = e % M;
-                store_pair<OutT, V>(dst + (long long)b * N + 2 * m, trans[m * QZ + b]);
+            auto st = [&](int m, int b, V z) { store_pair<OutT, V>(dst + (long long)b * N + 2 * m, z); };
+            if constexpr (radix_for(M) == M) {
+                stage_single<V, M, NR, T>(ld, st);
+            } else {
+                stage_first<V, M, NR, T, QZ>(trans, ld);
+                stages_mid<V, M, NR, T, QZ, radix_for(M)>(trans, tws, 2);
+                stage_last<V, M, NR, T, QZ, true>(trans, tws, 2, st);
             }
             __syncthreads();                            // smem is reused by the next item
         }
@@ -305,7 +318,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
     int rc;
     {
         auto k = fft_x_prefilter<R, N, NL>;
-        const size_t sm = sizeof(V) * (N + (size_t)N * NL) + sizeof(R) * NL;
+        const size_t sm = sizeof(V) * (N + (size_t)N * NL);
         if ((rc = set_smem(k, sm))) return rc;
         const long long tiles = ((long long)N * H + NL - 1) / NL;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);

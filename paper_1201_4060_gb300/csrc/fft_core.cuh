@@ -110,6 +110,111 @@ __device__ __forceinline__ void fft_smem(V* s, const V* tw, int twstride) {
     }
 }
 
+// ---- the same transform with its first stage fed from registers and its
+// last stage written to registers, so the data make one trip through shared
+// memory fewer at each end (and the prefilter or pre/post-processing ride
+// along with the loads and stores).  The radix sequence is fixed by L:
+// radix_for(L / NS) at each stage, as in fft_smem.
+constexpr int radix_for(int rem) { return (rem % 8 == 0) ? 8 : ((rem % 4 == 0) ? 4 : 2); }
+
+// NS of the last stage (NS * radix_for(L / NS) == L).
+constexpr int ns_last(int L) {
+    int ns = 1;
+    while (ns * radix_for(L / ns) < L) ns *= radix_for(L / ns);
+    return ns;
+}
+
+// First stage (NS = 1): butterfly j of line b takes positions j + r L/R from
+// ld(position, line) and writes s[(j R + r) QS + b].  Ends with a barrier.
+template <typename V, int L, int NLINES, int T, int QS, typename Ld>
+__device__ __forceinline__ void stage_first(V* s, Ld ld) {
+    constexpr int RADIX = radix_for(L);
+    constexpr int NB = (L / RADIX) * NLINES;
+    constexpr int BPT = (NB + T - 1) / T;
+    V v[BPT][RADIX];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int u = t + i * T;
+        if (NB % T == 0 || u < NB) {
+            const int b = u % NLINES, j = u / NLINES;
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) v[i][r] = ld(j + r * (L / RADIX), b);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int u = t + i * T;
+        if (NB % T == 0 || u < NB) {
+            const int b = u % NLINES, j = u / NLINES;
+            butterfly<RADIX>(v[i]);
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) s[(j * RADIX + r) * QS + b] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Stages after the first, up to (not including) the last.
+template <typename V, int L, int NLINES, int T, int QS, int NS>
+__device__ __forceinline__ void stages_mid(V* s, const V* tw, int twstride) {
+    if constexpr (NS < ns_last(L)) {
+        constexpr int RADIX = radix_for(L / NS);
+        stage<V, L, NLINES, T, RADIX, NS, QS>(s, tw, twstride);
+        stages_mid<V, L, NLINES, T, QS, NS * RADIX>(s, tw, twstride);
+    }
+}
+
+// Last stage (NS = L / R): butterfly j reads positions j + r NS, twiddles by
+// exp(2 pi i r j / L), and hands output position j + r NS of line b to st.
+// Consecutive threads take consecutive lines (JFAST = false) or consecutive
+// butterflies of one line (JFAST = true: stores along a line coalesce).
+template <typename V, int L, int NLINES, int T, int QS, bool JFAST, typename St>
+__device__ __forceinline__ void stage_last(const V* s, const V* tw, int twstride, St st) {
+    constexpr int NS = ns_last(L);
+    constexpr int RADIX = L / NS;
+    constexpr int NB = NS * NLINES;
+    constexpr int BPT = (NB + T - 1) / T;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int u = t + i * T;
+        if (NB % T == 0 || u < NB) {
+            const int b = JFAST ? u / NS : u % NLINES, j = JFAST ? u % NS : u / NLINES;
+            V v[RADIX];
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) {
+                V a = s[(j + r * NS) * QS + b];
+                if (r > 0) a = cmul(a, tw[(r * j) * twstride]);
+                v[r] = a;
+            }
+            butterfly<RADIX>(v);
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) st(j + r * NS, b, v[r]);
+        }
+    }
+}
+
+// A transform of length L = RADIX (one stage): registers only, no shared memory.
+template <typename V, int L, int NLINES, int T, typename Ld, typename St>
+__device__ __forceinline__ void stage_single(Ld ld, St st) {
+    constexpr int NB = NLINES;
+    constexpr int BPT = (NB + T - 1) / T;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = t + i * T;
+        if (NB % T == 0 || b < NB) {
+            V v[L];
+#pragma unroll
+            for (int r = 0; r < L; ++r) v[r] = ld(r, b);
+            butterfly<L>(v);
+#pragma unroll
+            for (int r = 0; r < L; ++r) st(r, b, v[r]);
+        }
+    }
+}
+
 template <int L, int NL> constexpr int threads_for() {
     return (L * NL / 16) < 32 ? 32 : (L * NL / 16);
 }
