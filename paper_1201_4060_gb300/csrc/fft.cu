@@ -317,12 +317,14 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
     cudaStream_t st = p->stream;
     int rc;
     {
-        auto k = fft_x_prefilter<R, N, NL>;
-        const size_t sm = sizeof(V) * (N + (size_t)N * NL);
+        // twice the lines of a y/z tile: 128-byte row segments per kx in HBM
+        constexpr int NLX = 2 * NL;
+        auto k = fft_x_prefilter<R, N, NLX>;
+        const size_t sm = sizeof(V) * (N + (size_t)N * NLX);
         if ((rc = set_smem(k, sm))) return rc;
-        const long long tiles = ((long long)N * H + NL - 1) / NL;
+        const long long tiles = ((long long)N * H + NLX - 1) / NLX;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);
-        k<<<(unsigned)(3 * tiles), T, sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw);
+        k<<<(unsigned)(3 * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw);
     }
     {
         auto k = fft_yz_fused<R, OutT, N, NL>;
