@@ -140,18 +140,26 @@ __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT
     // planes (c, ix): E * 3 of them, each E rows along y; warps take planes round-robin
     for (int pl = warp; pl < 3 * E; pl += nw) {
         const int c = pl / E, ix = pl - c * E;
-        const CT* src = coef + ((size_t)c * N + ((x0 + ix) & msk)) * (size_t)N * N + gz;
+        const CT* plane = coef + ((size_t)c * N + ((x0 + ix) & msk)) * (size_t)N * N + gz;
         TT* dst = tile + (size_t)pl * E * E + lane;
-        int gy = y0;
-#pragma unroll 7
-        for (int iy = 0; iy < E; ++iy, ++gy) {
-            const CT* s = src + (size_t)(gy & msk) * N;
+        auto copy = [&](int iy, const CT* s) {
             if constexpr (sizeof(CT) == sizeof(TT)) {
                 if constexpr (sizeof(CT) == 4) cp_async4(dst + iy * E, s);
                 else cp_async8(dst + iy * E, s);
             } else {
                 dst[iy * E] = widen<CT>(*s);
             }
+        };
+        if (N >= E) {
+            // rows y0.. up to the end of the period advance by N; the rest wrap to row 0
+            const int nrun = min(E, N - y0);
+            const CT* s = plane + (size_t)y0 * N;
+#pragma unroll 7
+            for (int iy = 0; iy < nrun; ++iy, s += N) copy(iy, s);
+            s = plane;
+            for (int iy = nrun; iy < E; ++iy, s += N) copy(iy, s);
+        } else {
+            for (int iy = 0; iy < E; ++iy) copy(iy, plane + (size_t)((y0 + iy) & msk) * N);
         }
     }
 }
@@ -283,6 +291,83 @@ __device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base,
             out_grad[3 * c + 1] = gy * dscale;
             out_grad[3 * c + 2] = gz * dscale;
         }
+    }
+}
+
+// One component of eval_particle in FP32 with packed two-way FMAs
+// (fma.rn.f32x2): adjacent y-lines jy, jy + 1 are contracted along z together
+// (their loads form the pair, the z weight is duplicated), and their y-sums
+// are kept as (even, odd) pairs that are added at the end of each x-plane.
+// Same arithmetic per term as eval_particle; the sums are grouped by parity
+// of jy.  base points at the component's first stencil node.
+template <int ORD, bool GRAD, int E>
+__device__ __forceinline__ void eval_component_x2(const float* __restrict__ base, float tx, float ty, float tz,
+                                                  float dscale, float* __restrict__ out_u,
+                                                  float* __restrict__ out_grad) {
+    constexpr int NP = ORD / 2;                       // pairs of y-lines
+    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+    bspline_weights<ORD, float>(tx, wx, dwx);
+    bspline_weights<ORD, float>(ty, wy, dwy);
+    bspline_weights<ORD, float>(tz, wz, dwz);
+    float2 wz2[ORD], dwz2[ORD], wyp[NP > 0 ? NP : 1], dwyp[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int j = 0; j < ORD; ++j) {
+        wz2[j] = make_float2(wz[j], wz[j]);
+        dwz2[j] = make_float2(dwz[j], dwz[j]);
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        wyp[p] = make_float2(wy[2 * p], wy[2 * p + 1]);
+        dwyp[p] = make_float2(dwy[2 * p], dwy[2 * p + 1]);
+    }
+    float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int jx = 0; jx < ORD; ++jx) {
+        float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const float* l0 = base + (jx * E + 2 * p) * E;
+            const float* l1 = l0 + E;
+            float2 z0 = make_float2(0.f, 0.f), z1 = z0;
+#pragma unroll
+            for (int jz = 0; jz < ORD; ++jz) {
+                const float2 a = make_float2(l0[jz], l1[jz]);
+                z0 = __ffma2_rn(wz2[jz], a, z0);
+                if (GRAD) z1 = __ffma2_rn(dwz2[jz], a, z1);
+            }
+            y00 = __ffma2_rn(wyp[p], z0, y00);
+            if (GRAD) {
+                y10 = __ffma2_rn(dwyp[p], z0, y10);
+                y01 = __ffma2_rn(wyp[p], z1, y01);
+            }
+        }
+        if constexpr (ORD % 2 == 1) {               // the unpaired last line
+            const float* l = base + (jx * E + ORD - 1) * E;
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+            for (int jz = 0; jz < ORD; ++jz) {
+                z0 = fmaf(wz[jz], l[jz], z0);
+                if (GRAD) z1 = fmaf(dwz[jz], l[jz], z1);
+            }
+            y00.x = fmaf(wy[ORD - 1], z0, y00.x);
+            if (GRAD) {
+                y10.x = fmaf(dwy[ORD - 1], z0, y10.x);
+                y01.x = fmaf(wy[ORD - 1], z1, y01.x);
+            }
+        }
+        const float s00 = y00.x + y00.y;
+        u = fmaf(wx[jx], s00, u);
+        if (GRAD) {
+            gx = fmaf(dwx[jx], s00, gx);
+            gy = fmaf(wx[jx], y10.x + y10.y, gy);
+            gz = fmaf(wx[jx], y01.x + y01.y, gz);
+        }
+    }
+    *out_u = u;
+    if (GRAD) {
+        out_grad[0] = gx * dscale;
+        out_grad[1] = gy * dscale;
+        out_grad[2] = gz * dscale;
     }
 }
 
@@ -423,13 +508,19 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
                 idx_n = w.s_idx[i];
             }
         };
-        if ((unsigned)warp < njobs) fetch(warp);
-        for (unsigned j = warp; j < njobs; j += NW) {
+        // Jobs are dealt to the NW warps in rounds.  A last, partly filled round
+        // of m <= 2 NW / 3 jobs is run per component instead: 3 m shorter warp
+        // tasks (one component of the job's 32 particles each), so the item
+        // does not wait a whole job time on a few warps.
+        const unsigned m_tail = njobs % NW;
+        const unsigned jfull = (m_tail != 0 && 3 * m_tail <= 2 * NW) ? njobs - m_tail : njobs;
+        if ((unsigned)warp < jfull) fetch(warp);
+        for (unsigned j = warp; j < jfull; j += NW) {
             const Rec<TR> rc = rc_n;
             const unsigned idx = idx_n;
             const bool v = v_n;
             v_n = false;
-            if (j + NW < njobs) fetch(j + NW);
+            if (j + NW < jfull) fetch(j + NW);
             if (v) {
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
@@ -442,6 +533,28 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
                 if (GRAD) {
 #pragma unroll
                     for (int k = 0; k < 9; ++k) out_grad[9 * (size_t)idx + k] = g[k];
+                }
+            }
+        }
+        for (unsigned q = warp; q < 3 * (njobs - jfull); q += NW) {
+            const unsigned c = q % 3;
+            unsigned lo, hi;
+            job_range(jfull + q / 3, &lo, &hi);
+            const unsigned pos = lo + (unsigned)lane;
+            if (pos < hi) {
+                const unsigned i = c0 + s_order[pos];
+                const Rec<TR> rc = w.s_rec[i];
+                const unsigned idx = w.s_idx[i];
+                const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+                const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+                const int oz = (int)(rc.cell & 1023u) - z0;
+                float u, g[3];
+                eval_component_x2<ORD, GRAD, E>(tile + c * (E * E * E) + (ox * E + oy) * E + oz, (float)rc.t[0],
+                                                (float)rc.t[1], (float)rc.t[2], dscale, &u, g);
+                out_u[3 * (size_t)idx + c] = u;
+                if (GRAD) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) out_grad[9 * (size_t)idx + 3 * c + k] = g[k];
                 }
             }
         }
