@@ -359,6 +359,7 @@ def run_ours(args):
         out["forms"] = forms
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=3)
         out["adjoint"] = run_adjoint(B, device)
+        out["batch"] = run_batch(B, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(samples=1 << 17)
     if world > 1:
@@ -429,6 +430,68 @@ def run_adjoint(B, device, steps=10, warmup=3):
            "hbm_frac": {s: abytes[s] / (stages[s] / 1e3) / 1e9 / pk["hbm_gbs"] for s in abytes if stages[s] > 0}}
     del uh, coef, x, gu, gg, g_coef, g_uh, g_x
     plan.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(B, device, steps=10, warmup=3):
+    """64 independent small fields (grids 32..192 including 3 * 2^k, log-uniform 1e3..1e6 particles each),
+    cubic, FP32: the whole batch replayed as one CUDA graph launch (streams chosen by the autotuner), and
+    the same work as eager per-field calls for comparison.  One step = every field once."""
+    import torch
+    from paper_1201_4060_gb300 import synth
+    wl = synth.WORKLOADS["batch64"]
+    spec = synth.batch_workload(wl["nfields"], wl["field_seed"], wl["particle_seed"])
+    order = wl["order"]
+    plans, uh, co, xs, ou, og = [], [], [], [], [], []
+    for f in spec:
+        plan = B.Plan(f["N"], order, "f32")
+        F = synth.kolmogorov_field(f["N"], seed=f["field_seed"])
+        plans.append(plan)
+        uh.append(dense_field_on_gpu(F, plan.uhat_dtype, device))
+        co.append(plan.empty_coeffs())
+        xs.append(torch.from_numpy(synth.uniform_particles(f["P"], seed=f["particle_seed"])).to(device))
+        ou.append(torch.empty((f["P"], 3), dtype=torch.float32, device=device))
+        og.append(torch.empty((f["P"], 3, 3), dtype=torch.float32, device=device))
+    total = sum(f["P"] for f in spec)
+    stream = torch.cuda.current_stream()
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=4)
+    k, _ = batch.autotune(stream)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_graph = timed(lambda: batch.launch(stream))
+
+    def eager():
+        for i in range(len(plans)):
+            plans[i].coeffs(uh[i], co[i])
+            plans[i].interp(co[i], xs[i], ou[i], og[i])
+
+    ms_eager = timed(eager)
+    grids = sorted(set(f["N"] for f in spec))
+    out = {"workload": f"{len(spec)} fields, grids {grids} (field i: grid {list(synth.BATCH_GRIDS)}[i mod 6], "
+                       f"seed {wl['field_seed']} + i), order-{order} B-spline, f32 coefficients, uniform particles "
+                       f"log-uniform 1e3..1e6 per field (seed {wl['particle_seed']}), {total} in all",
+           "particles": total, "particles_per_s": total / (ms_graph / 1e3), "ms_per_batch": ms_graph,
+           "graph_streams": k, "launches_per_batch": 1,
+           "eager_ms_per_batch": ms_eager, "eager_particles_per_s": total / (ms_eager / 1e3),
+           "steps": steps, "warmup": warmup}
+    batch.close()
+    for p in plans:
+        p.close()
+    del uh, co, xs, ou, og
     torch.cuda.empty_cache()
     return out
 

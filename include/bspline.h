@@ -77,7 +77,8 @@ enum {
 
 /* Create a plan for an N^3 periodic grid, B-spline order `order` (the
  * paper's N: stencil width, degree order-1), coefficient type `dtype`.
- * N: even power of two, 8 <= N <= 1024.  order: 2..8.  L = 2 pi.
+ * N: a power of two from 8 to 1024, or 3 * 2^k from 48 to 768 (the
+ * transforms add a radix-3 stage).  order: 2..8.  L = 2 pi.
  * Allocates device tables on the current CUDA device.  On success *out
  * receives the plan; on failure *out is set to NULL. */
 int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype);
@@ -225,6 +226,37 @@ int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks);
 int bspline_interp_noalloc(const void* coeffs, int N, int order, bspline_dtype dtype, double L,
                            const double* x, int64_t P, void* out_u, void* out_grad, int flags,
                            void* stream);
+
+/* ---- Batches of independent fields.  No counterpart in the paper: a launch
+ * structure for many small fields (grid size, order and dtype may differ per
+ * field), whose short kernels would otherwise leave the GPU idle.
+ * bspline_batch_create: nfields >= 1 plans (all on one device; one plan may
+ * serve several fields, which then run one after another).  The batch keeps
+ * the plan handles, not ownership: destroy it before its plans.
+ * bspline_batch_capture: records bspline_coeffs(u_hat[i] -> coeffs[i]) and
+ * bspline_interp(coeffs[i], x[i], P[i] -> out_u[i], out_grad[i]) for every
+ * field into one CUDA graph, the fields spread round-robin over `streams`
+ * concurrent streams by plan.  Arrays of nfields device pointers (host arrays
+ * of pointers; out_grad may be NULL for u only, or hold NULL entries); the
+ * same argument rules as the single-field calls; plan workspaces are grown
+ * here, outside the graph.  Nothing runs until a launch.
+ * bspline_batch_launch: replays the graph with one launch on `stream`
+ * (cudaStream_t, NULL = legacy stream); every launch rereads u_hat and x and
+ * rewrites coeffs and the outputs named at capture.  Status words of the
+ * plans are read with bspline_status as usual.
+ * bspline_batch_autotune: captures with 1, 2, 4, 8, 16 streams (up to the
+ * number of distinct plans), times three graph launches of each on `stream`,
+ * keeps the fastest graph; best_streams and best_ms (mean time of one launch)
+ * may be NULL.  Requires an earlier capture (its arguments are reused).
+ * Errors: BSPLINE_ERR_INVALID_ARG for bad arguments or a launch before a
+ * capture; BSPLINE_ERR_CUDA / OUT_OF_MEMORY from the runtime. */
+typedef struct bspline_batch_s* bspline_batch_t;
+int bspline_batch_create(bspline_batch_t* out, int nfields, const bspline_plan_t* plans);
+int bspline_batch_capture(bspline_batch_t batch, int streams, const void* const* u_hat, void* const* coeffs,
+                          const double* const* x, const int64_t* P, void* const* out_u, void* const* out_grad);
+int bspline_batch_launch(bspline_batch_t batch, void* stream);
+int bspline_batch_autotune(bspline_batch_t batch, void* stream, int* best_streams, double* best_ms);
+int bspline_batch_destroy(bspline_batch_t batch);
 
 #ifdef __cplusplus
 }

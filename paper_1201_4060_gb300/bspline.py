@@ -71,6 +71,12 @@ def _load() -> ctypes.CDLL:
         "bspline_plan_set_test_hooks": (i32, [vp, i32]),
         "bspline_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
         "bspline_interp_noalloc": (i32, [vp, i32, i32, i32, ctypes.c_double, vp, i64, vp, vp, i32, vp]),
+        "bspline_batch_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]),
+        "bspline_batch_capture": (i32, [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "bspline_batch_launch": (i32, [vp, vp]),
+        "bspline_batch_autotune": (i32, [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]),
+        "bspline_batch_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -341,3 +347,63 @@ class Plan:
         rc = bspline_run_host(self.handle, u_hat_host.data_ptr(), x_host.data_ptr(), x_host.shape[0],
                               u_host.data_ptr(), grad_host.data_ptr() if grad_host is not None else 0)
         _check(rc, "bspline_run_host")
+
+
+# ---- batches of independent fields (one CUDA graph launch) -------------------------
+
+def _ptr_array(vals):
+    arr = (ctypes.c_void_p * len(vals))()
+    for i, v in enumerate(vals):
+        arr[i] = v
+    return arr
+
+
+class Batch:
+    """Many fields, each with its own Plan, evaluated by one graph launch (bspline_batch_*).
+
+    capture() takes lists (one entry per field) of u_hat, coefficient buffers, positions and output
+    tensors, as Plan.coeffs / Plan.interp would; launch() replays the graph on the current stream.
+    """
+
+    def __init__(self, plans):
+        self.plans = list(plans)          # keeps the plans alive while the batch exists
+        h = ctypes.c_void_p()
+        arr = _ptr_array([p.handle for p in self.plans])
+        _check(_load().bspline_batch_create(ctypes.byref(h), len(self.plans), arr), "bspline_batch_create")
+        self.handle = h.value
+        self._keep = None
+
+    def capture(self, u_hats, coeffs, xs, outs_u, outs_grad=None, streams: int = 4):
+        n = len(self.plans)
+        assert len(u_hats) == len(coeffs) == len(xs) == len(outs_u) == n
+        P = (ctypes.c_int64 * n)(*[int(x.shape[0]) for x in xs])
+        args = [_ptr_array([t.data_ptr() for t in lst]) for lst in (u_hats, coeffs, xs, outs_u)]
+        g = _ptr_array([t.data_ptr() if t is not None else 0 for t in outs_grad]) if outs_grad is not None else None
+        self._keep = (u_hats, coeffs, xs, outs_u, outs_grad)
+        rc = _load().bspline_batch_capture(self.handle, streams, args[0], args[1], args[2], P, args[3], g)
+        _check(rc, "bspline_batch_capture")
+
+    def launch(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(_load().bspline_batch_launch(self.handle, s.cuda_stream), "bspline_batch_launch")
+
+    def autotune(self, stream=None) -> tuple[int, float]:
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        k = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(_load().bspline_batch_autotune(self.handle, s.cuda_stream, ctypes.byref(k), ctypes.byref(ms)),
+               "bspline_batch_autotune")
+        return k.value, ms.value
+
+    def close(self) -> None:
+        if getattr(self, "handle", 0):
+            _load().bspline_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

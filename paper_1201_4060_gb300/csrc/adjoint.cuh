@@ -144,25 +144,24 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
         }
     }
     __syncthreads();
-    const int msk = N - 1;
     if constexpr (sizeof(A) == 4) {
         // per tile row: the brick's B nodes as B/4 aligned 16-byte vector atomics
-        // (z0 is a multiple of B, and 4 consecutive z stay inside one period),
+        // (z0 and N are multiples of 4, so 4 consecutive z stay inside one period),
         // then the E - B halo nodes one by one
         constexpr int U = B / 4 + (E - B);
         for (int e = threadIdx.x; e < 3 * E * E * U; e += kAdjThreads) {
             const int row = e / U, k = e - row * U;
             const int c = row / (E * E), ix = (row / E) % E, iy = row % E;
             const A* src = acc + (size_t)row * E;
-            A* dst = g_coef + (((size_t)c * N + ((x0 + ix) & msk)) * N + ((y0 + iy) & msk)) * N;
+            A* dst = g_coef + (((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N;
             if (k < B / 4) {
                 const float4 v = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
                 if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
-                    atomicAdd(reinterpret_cast<float4*>(dst + ((z0 + 4 * k) & msk)), v);
+                    atomicAdd(reinterpret_cast<float4*>(dst + wrap_index(z0 + 4 * k, N)), v);
             } else {
                 const int iz = B + (k - B / 4);
                 const A v = src[iz];
-                if (v != A(0)) atomicAdd(dst + ((z0 + iz) & msk), v);
+                if (v != A(0)) atomicAdd(dst + wrap_index(z0 + iz, N), v);
             }
         }
     } else {
@@ -171,8 +170,8 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
             if (v != A(0)) {
                 const int c = e / E3, r = e - c * E3;
                 const int ix = r / (E * E), iy = (r / E) % E, iz = r % E;
-                atomicAdd(&g_coef[(((size_t)c * N + ((x0 + ix) & msk)) * N + ((y0 + iy) & msk)) * N +
-                                  ((z0 + iz) & msk)],
+                atomicAdd(&g_coef[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N +
+                                  wrap_index(z0 + iz, N)],
                           v);
             }
         }

@@ -195,6 +195,11 @@ int launch_adjoint_transform(bspline_plan_s* p, const void* g_coef, void* g_u_ha
         case 256: return adj_n<256>(p, g_coef, g_u_hat);
         case 512: return adj_n<512>(p, g_coef, g_u_hat);
         case 1024: return adj_n<1024>(p, g_coef, g_u_hat);
+        case 48: return adj_n<48>(p, g_coef, g_u_hat);
+        case 96: return adj_n<96>(p, g_coef, g_u_hat);
+        case 192: return adj_n<192>(p, g_coef, g_u_hat);
+        case 384: return adj_n<384>(p, g_coef, g_u_hat);
+        case 768: return adj_n<768>(p, g_coef, g_u_hat);
     }
     return BSPLINE_ERR_UNSUPPORTED_N;
 }

@@ -242,7 +242,7 @@ int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype) {
     if (!out) return BSPLINE_ERR_INVALID_ARG;
     *out = nullptr;
     if (dtype != BSPLINE_F64 && dtype != BSPLINE_F32 && dtype != BSPLINE_BF16) return BSPLINE_ERR_INVALID_ARG;
-    if (N < 8 || N > 1024 || (N & (N - 1)) != 0) return BSPLINE_ERR_UNSUPPORTED_N;
+    if (!bs::supported_grid(N)) return BSPLINE_ERR_UNSUPPORTED_N;
     if (order < 2 || order > 8) return BSPLINE_ERR_UNSUPPORTED_ORDER;
     bspline_plan_s* p = new (std::nothrow) bspline_plan_s();
     if (!p) return BSPLINE_ERR_OUT_OF_MEMORY;

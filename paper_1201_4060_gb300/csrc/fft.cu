@@ -381,6 +381,11 @@ int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         case 256: return run_n<256>(p, u_hat, coeffs);
         case 512: return run_n<512>(p, u_hat, coeffs);
         case 1024: return run_n<1024>(p, u_hat, coeffs);
+        case 48: return run_n<48>(p, u_hat, coeffs);
+        case 96: return run_n<96>(p, u_hat, coeffs);
+        case 192: return run_n<192>(p, u_hat, coeffs);
+        case 384: return run_n<384>(p, u_hat, coeffs);
+        case 768: return run_n<768>(p, u_hat, coeffs);
     }
     return BSPLINE_ERR_UNSUPPORTED_N;
 }

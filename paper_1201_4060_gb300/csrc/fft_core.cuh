@@ -1,4 +1,4 @@
-// Building blocks of the shared-memory FFTs: complex helpers, radix-2/4/8
+// Building blocks of the shared-memory FFTs: complex helpers, radix-2/3/4/8
 // butterflies of the inverse DFT (exponent +2 pi i n k / R), the Stockham
 // stage and the tile loads.  Included by the forward path (fft.cu: prefilter
 // + inverse real transform) and by its adjoint (adjoint_fft.cu: forward real
@@ -55,8 +55,21 @@ template <typename V> __device__ __forceinline__ void dft8(V* x) {
     x[3] = cadd(e3, w3);
     x[7] = csub(e3, w3);
 }
+// Length 3: with w = exp(2 pi i / 3) = -1/2 + i sqrt(3)/2, X1 and X2 are
+// a - (b + c)/2 +- i (sqrt(3)/2) (b - c).
+template <typename V> __device__ __forceinline__ void dft3(V& a, V& b, V& c) {
+    using R = decltype(V::x);
+    const R h = (R)0.86602540378443864676372317075294;   // sqrt(3) / 2
+    const V s = cadd(b, c), d = csub(b, c);
+    const V m = mk<V>(a.x - (R)0.5 * s.x, a.y - (R)0.5 * s.y);
+    const V id = mk<V>(-h * d.y, h * d.x);
+    a = cadd(a, s);
+    b = cadd(m, id);
+    c = csub(m, id);
+}
 template <int R, typename V> __device__ __forceinline__ void butterfly(V* v) {
     if constexpr (R == 2) dft2(v[0], v[1]);
+    else if constexpr (R == 3) dft3(v[0], v[1], v[2]);
     else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
     else dft8(v);
 }
@@ -100,11 +113,16 @@ __device__ __forceinline__ void stage(V* s, const V* tw, int twstride) {
     __syncthreads();
 }
 
+// Radix of the stage that has rem = L / NS points left: 8, 4 or 2 while the
+// power of two lasts, then 3 (L = 2^a 3^b).
+constexpr int radix_for(int rem) {
+    return (rem % 8 == 0) ? 8 : ((rem % 4 == 0) ? 4 : ((rem % 2 == 0) ? 2 : 3));
+}
+
 template <typename V, int L, int NLINES, int T, int QS, int NS = 1>
 __device__ __forceinline__ void fft_smem(V* s, const V* tw, int twstride) {
     if constexpr (NS < L) {
-        constexpr int REM = L / NS;
-        constexpr int RADIX = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : 2);
+        constexpr int RADIX = radix_for(L / NS);
         stage<V, L, NLINES, T, RADIX, NS, QS>(s, tw, twstride);
         fft_smem<V, L, NLINES, T, QS, NS * RADIX>(s, tw, twstride);
     }
@@ -115,7 +133,6 @@ __device__ __forceinline__ void fft_smem(V* s, const V* tw, int twstride) {
 // memory fewer at each end (and the prefilter or pre/post-processing ride
 // along with the loads and stores).  The radix sequence is fixed by L:
 // radix_for(L / NS) at each stage, as in fft_smem.
-constexpr int radix_for(int rem) { return (rem % 8 == 0) ? 8 : ((rem % 4 == 0) ? 4 : 2); }
 
 // NS of the last stage (NS * radix_for(L / NS) == L).
 constexpr int ns_last(int L) {

@@ -20,6 +20,15 @@ namespace bs {
 constexpr int brick_edge(int dtype) { return dtype == BSPLINE_F64 ? 8 : 16; }
 inline int bricks_per_axis(int N, int dtype) { return N >= brick_edge(dtype) ? N / brick_edge(dtype) : 1; }
 
+// Grid sizes with compiled transforms: powers of two 8..1024, and 3 * 2^k
+// from 48 to 768 (radix-3 stage; multiples of the 16-cell brick).
+inline bool supported_grid(int N) {
+    if (N < 8 || N > 1024) return false;
+    if ((N & (N - 1)) == 0) return true;
+    const int q = N / 3;
+    return N % 3 == 0 && (q & (q - 1)) == 0 && N % 16 == 0;
+}
+
 struct PendingTiming {
     int stage;
     cudaEvent_t start, stop;

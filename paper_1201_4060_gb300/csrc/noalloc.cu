@@ -57,7 +57,7 @@ extern "C" int bspline_interp_noalloc(const void* coeffs, int N, int order, bspl
                                       const double* x, int64_t P, void* out_u, void* out_grad, int flags,
                                       void* stream) {
     if (dtype != BSPLINE_F64 && dtype != BSPLINE_F32 && dtype != BSPLINE_BF16) return BSPLINE_ERR_INVALID_ARG;
-    if (N < 8 || N > 1024 || (N & (N - 1)) != 0) return BSPLINE_ERR_UNSUPPORTED_N;
+    if (!bs::supported_grid(N)) return BSPLINE_ERR_UNSUPPORTED_N;
     if (order < 2 || order > 8) return BSPLINE_ERR_UNSUPPORTED_ORDER;
     if (!(L > 0.0) || !(L < 1e300)) return BSPLINE_ERR_INVALID_ARG;
     if (flags & ~BSPLINE_INTERP_NO_GRAD) return BSPLINE_ERR_INVALID_ARG;

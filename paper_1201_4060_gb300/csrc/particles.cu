@@ -83,6 +83,13 @@ __device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, 
     return true;
 }
 
+// First stencil node modulo N (N a power of two, or 3 times one).
+__device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
+    if ((N & (N - 1)) == 0) return (unsigned)(a & (long long)(N - 1));
+    long long r = a % N;
+    return (unsigned)(r < 0 ? r + N : r);
+}
+
 template <typename TR>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                            int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
@@ -99,7 +106,7 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
                 float tf;
                 if (locate_nonneg(s, order, &base, &tf)) {
                     tt[a] = tf;
-                    anc[a] = (unsigned)((base + 1) & (long long)(N - 1));
+                    anc[a] = wrap_anchor(base + 1, N);
                     continue;
                 }
             }
@@ -112,7 +119,7 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
             }
             const double f = floor(sh);
             tt[a] = (TR)(sh - f);
-            anc[a] = (unsigned)(((long long)f + 1) & (long long)(N - 1));
+            anc[a] = wrap_anchor((long long)f + 1, N);
         }
         unsigned k = NB;
         if (ok) {

@@ -57,6 +57,9 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     return off;
 }
 
+// Periodic grid index of i >= 0 (a single subtraction in the common case i < 2N).
+__device__ __forceinline__ int wrap_index(int i, int N) { return i < N ? i : (i < 2 * N ? i - N : i % N); }
+
 // ------------------------------------------------------------------ weights
 // v[m] = M_k(t + m), m = 0..k-1, for the cardinal B-spline of order k.
 // Node j (0-based, j = 0 leftmost) of an order-n stencil has weight
@@ -133,14 +136,13 @@ __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT
     using TT = typename TileT<CT>::T;
     constexpr int E = tile_edge<ORD, CT>();
     static_assert(E <= 32, "one z-row per warp step");
-    const int msk = N - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane >= E) return;
-    const int gz = (z0 + lane) & msk;
+    const int gz = wrap_index(z0 + lane, N);
     // planes (c, ix): E * 3 of them, each E rows along y; warps take planes round-robin
     for (int pl = warp; pl < 3 * E; pl += nw) {
         const int c = pl / E, ix = pl - c * E;
-        const CT* plane = coef + ((size_t)c * N + ((x0 + ix) & msk)) * (size_t)N * N + gz;
+        const CT* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N + gz;
         TT* dst = tile + (size_t)pl * E * E + lane;
         auto copy = [&](int iy, const CT* s) {
             if constexpr (sizeof(CT) == sizeof(TT)) {
@@ -159,7 +161,7 @@ __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT
             s = plane;
             for (int iy = nrun; iy < E; ++iy, s += N) copy(iy, s);
         } else {
-            for (int iy = 0; iy < E; ++iy) copy(iy, plane + (size_t)((y0 + iy) & msk) * N);
+            for (int iy = 0; iy < E; ++iy) copy(iy, plane + (size_t)wrap_index(y0 + iy, N) * N);
         }
     }
 }

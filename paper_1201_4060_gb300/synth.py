@@ -161,7 +161,24 @@ WORKLOADS = {
     "throughput512": dict(N=512, order=6, P=1 << 24, field_seed=1204, particle_seed=4063, particles="clustered"),
     # adjoint (differentiation): N(0, 1) cotangents on u and grad u, seed = particle_seed + 1
     "adjoint256": dict(N=256, order=4, P=1 << 22, field_seed=1206, particle_seed=4065, particles="uniform"),
+    # 64 independent small fields (batch_workload), cubic, FP32 coefficients
+    "batch64": dict(nfields=64, order=4, field_seed=1205, particle_seed=4064, particles="uniform"),
 }
+
+
+BATCH_GRIDS = (32, 48, 64, 96, 128, 192)
+
+
+def batch_workload(nfields: int = 64, field_seed: int = 1205, particle_seed: int = 4064,
+                   p_range: tuple[float, float] = (1e3, 1e6)) -> list[dict]:
+    """Many independent small fields: field i has grid BATCH_GRIDS[i % 6], field seed field_seed + i,
+    uniform particles (seed particle_seed + i) whose count is log-uniform over p_range
+    (mean (hi - lo) / ln(hi / lo), about 1.45e5 for the default range)."""
+    rng = np.random.Generator(np.random.PCG64(particle_seed))
+    lo, hi = np.log10(p_range[0]), np.log10(p_range[1])
+    counts = np.floor(10.0 ** rng.uniform(lo, hi, nfields)).astype(np.int64)
+    return [dict(N=BATCH_GRIDS[i % len(BATCH_GRIDS)], field_seed=field_seed + i, particle_seed=particle_seed + i,
+                 P=int(counts[i])) for i in range(nfields)]
 
 
 def make_particles(kind: str, P: int, seed: int, N: int, L: float = L_DEFAULT) -> np.ndarray:

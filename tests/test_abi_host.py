@@ -41,7 +41,7 @@ def test_status_strings_and_version():
 
 def test_plan_argument_checks_before_cuda():
     assert B.lib().bspline_plan(None, 32, 4, B.F32) == B.ERR_INVALID_ARG
-    for N in (0, 4, 7, 12, 48, 2048):
+    for N in (0, 4, 7, 12, 24, 36, 80, 1536, 2048):      # 3 * 2^k grids start at 48
         rc, h = B.bspline_plan(N, 4, B.F32)
         assert rc == B.ERR_UNSUPPORTED_N and h == 0
     for order in (0, 1, 9, -3):
@@ -67,3 +67,13 @@ def test_null_plan_is_rejected_everywhere():
     assert B.bspline_plan_set_timing(0, 1) == B.ERR_INVALID_ARG
     assert B.bspline_stage_times(0)[0] == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_test_hooks(0, 1) == B.ERR_INVALID_ARG
+    lib = B.lib()
+    assert lib.bspline_batch_create(None, 1, None) == B.ERR_INVALID_ARG
+    h = B.ctypes.c_void_p()
+    assert lib.bspline_batch_create(B.ctypes.byref(h), 0, None) == B.ERR_INVALID_ARG and not h.value
+    plans = (B.ctypes.c_void_p * 2)(0, 0)
+    assert lib.bspline_batch_create(B.ctypes.byref(h), 2, plans) == B.ERR_INVALID_ARG and not h.value
+    assert lib.bspline_batch_launch(None, None) == B.ERR_INVALID_ARG
+    assert lib.bspline_batch_autotune(None, None, None, None) == B.ERR_INVALID_ARG
+    assert lib.bspline_batch_capture(None, 1, None, None, None, None, None, None) == B.ERR_INVALID_ARG
+    assert lib.bspline_batch_destroy(None) == B.OK

@@ -283,3 +283,18 @@ def test_abi_rejects_bad_adjoint_arguments(B):
         == B.ERR_INVALID_ARG
     # P = 0 with nothing to do is a no-op
     assert B.bspline_spread_adjoint(h, 0, 0, 0, 0, 0, 0, 0, 0) == B.OK
+
+
+@pytest.mark.parametrize("N", [48, 96])
+def test_radix3_adjoint_f64(B, N):
+    order, P = 4, 1500
+    plan = B.Plan(N, order, "f64")
+    half = synth.kolmogorov_field(N, seed=N).dense()
+    coef = plan.coeffs(_dev(half, torch.complex128))
+    x = synth.clustered_particles(P, seed=N + 1)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=N + 2)
+    gh, gx, gc = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, coef=coef)
+    ref_h, ref_x, ref_c = O.interpolate_adjoint(half, x, gu, gg, order)
+    assert normwise(gc.cpu().numpy(), ref_c) < TOL64
+    assert normwise(gh.cpu().numpy(), ref_h) < TOL64
+    assert normwise(gx.cpu().numpy(), ref_x) < TOL64

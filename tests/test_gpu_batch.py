@@ -1,0 +1,140 @@
+"""Batches of independent fields replayed as one CUDA graph (bspline_batch_*).
+
+The graph runs the same kernels on the same inputs as the single-field calls,
+so its outputs must equal theirs bit for bit (the forward path has no
+atomics); one field per grid size is also held to the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bspline_oracle as O
+from paper_1201_4060_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L = 2.0 * math.pi
+TOL32 = {"u": 2e-5, "grad": 5e-5}
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1201_4060_gb300 import _build
+    _build.build()
+    from paper_1201_4060_gb300 import bspline
+    assert torch.cuda.is_available()
+    return bspline
+
+
+def normwise(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _fields(B, spec, dtype="f32", order=4):
+    plans, uh, co, xs, ou, og, halves, xnp = [], [], [], [], [], [], [], []
+    shared = {}
+    for f in spec:
+        key = f.get("share")
+        if key is not None and key in shared:
+            plan = shared[key]
+        else:
+            plan = B.Plan(f["N"], order, dtype)
+            if key is not None:
+                shared[key] = plan
+        half = synth.kolmogorov_field(f["N"], seed=f["field_seed"]).dense()
+        x = synth.uniform_particles(f["P"], seed=f["particle_seed"])
+        plans.append(plan)
+        halves.append(half)
+        xnp.append(x)
+        uh.append(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
+        co.append(plan.empty_coeffs())
+        xs.append(torch.from_numpy(x).cuda())
+        ou.append(torch.full((f["P"], 3), float("nan"), dtype=plan.out_dtype, device="cuda"))
+        og.append(torch.full((f["P"], 3, 3), float("nan"), dtype=plan.out_dtype, device="cuda"))
+    return plans, uh, co, xs, ou, og, halves, xnp
+
+
+SPEC = [dict(N=16, field_seed=1, particle_seed=11, P=700),
+        dict(N=48, field_seed=2, particle_seed=12, P=5000),
+        dict(N=32, field_seed=3, particle_seed=13, P=1, share="a"),
+        dict(N=32, field_seed=4, particle_seed=14, P=20000, share="a"),   # same plan as the previous field
+        dict(N=96, field_seed=5, particle_seed=15, P=3000),
+        dict(N=64, field_seed=6, particle_seed=16, P=0),
+        dict(N=192, field_seed=7, particle_seed=17, P=12000)]
+
+
+@pytest.mark.parametrize("streams", [1, 3])
+def test_batch_graph_equals_single_field_calls(B, streams):
+    plans, uh, co, xs, ou, og, halves, xnp = _fields(B, SPEC)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=streams)
+    batch.launch()
+    torch.cuda.synchronize()
+    for i, f in enumerate(SPEC):
+        c = plans[i].coeffs(uh[i])
+        if f["P"] == 0:
+            assert torch.equal(c, co[i])
+            continue
+        u, g = plans[i].interp(c, xs[i])
+        torch.cuda.synchronize()
+        assert torch.equal(c, co[i])
+        assert torch.equal(u, ou[i]) and torch.equal(g, og[i])
+    # one field of each grid size against the oracle
+    for i in (1, 3, 4, 6):
+        ru, rg = O.interpolate(halves[i].astype(np.complex64).astype(np.complex128), xnp[i], 4)
+        assert normwise(ou[i].cpu().numpy(), ru) < TOL32["u"]
+        assert normwise(og[i].cpu().numpy(), rg) < TOL32["grad"]
+    batch.close()
+
+
+def test_batch_relaunch_and_autotune(B):
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, SPEC)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=2)
+    batch.launch()
+    torch.cuda.synchronize()
+    ref_u = [t.clone() for t in ou]
+    ref_g = [t.clone() for t in og]
+    for t in ou + og:
+        t.fill_(float("nan"))
+    k, ms = batch.autotune()
+    assert 1 <= k <= 16 and ms > 0
+    for t in ou + og:
+        t.fill_(float("nan"))
+    batch.launch()
+    batch.launch()
+    torch.cuda.synchronize()
+    for i in range(len(SPEC)):
+        assert torch.equal(ou[i], ref_u[i]) and torch.equal(og[i], ref_g[i])
+        assert plans[i].status() == 0
+    batch.close()
+
+
+def test_batch_u_only_and_f64(B):
+    spec = SPEC[:3]
+    plans, uh, co, xs, ou, og, halves, xnp = _fields(B, spec, dtype="f64", order=6)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, None, streams=2)           # u only
+    batch.launch()
+    torch.cuda.synchronize()
+    for i in range(len(spec)):
+        ru, _ = O.interpolate(halves[i], xnp[i], 6)
+        assert normwise(ou[i].cpu().numpy(), ru) < 1e-12
+        assert torch.isnan(og[i]).all()                      # untouched
+    batch.close()
+
+
+def test_batch_rejects_bad_arguments(B):
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, SPEC[:2])
+    batch = B.Batch(plans)
+    lib = B.lib()
+    assert lib.bspline_batch_launch(batch.handle, None) == B.ERR_INVALID_ARG          # not captured
+    assert lib.bspline_batch_autotune(batch.handle, None, None, None) == B.ERR_INVALID_ARG
+    with pytest.raises(B.BSplineError):
+        batch.capture(uh, co, xs, ou, og, streams=0)
+    co_bad = [co[0], uh[1]]                                  # coefficients aliasing u_hat
+    with pytest.raises(B.BSplineError):
+        batch.capture(uh, co_bad, xs, ou, og, streams=1)
+    batch.close()

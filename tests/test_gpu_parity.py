@@ -267,3 +267,29 @@ def test_custom_domain_length(B):
     ru, rg = O.evaluate(O.coefficients(half, order), x, order, L=Lc)
     assert normwise(u.cpu().numpy(), ru) < TOL64
     assert normwise(g.cpu().numpy(), rg) < TOL64
+
+
+# ----------------------------------------------------------------------- 3 * 2^k grids (radix-3 stage)
+
+@pytest.mark.parametrize("N", [48, 96, 192])
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_radix3_grids_f64(B, N, order):
+    half = synth.random_half_spectrum(N, seed=N + order, hermitian=False)
+    x = np.random.default_rng(N).uniform(-L, 2 * L, (2001, 3))
+    c, u, g, nf = gpu_path(B, half, x, N, order, "f64")
+    assert normwise(c, O.coefficients(half, order)) < TOL64
+    ru, rg = O.interpolate(half, x, order)
+    assert nf == 0
+    assert normwise(u, ru) < TOL64
+    assert normwise(g, rg) < TOL64
+
+
+@pytest.mark.parametrize("N", [48, 192])
+def test_radix3_grids_f32(B, N):
+    half = synth.kolmogorov_field(N, seed=7).dense().astype(np.complex64)
+    x = synth.clustered_particles(20000, seed=8)
+    _, u, g, nf = gpu_path(B, half, x, N, 4, "f32")
+    ru, rg = O.interpolate(half.astype(np.complex128), x, 4)
+    assert nf == 0
+    assert normwise(u, ru) < TOL32["u"]
+    assert normwise(g, rg) < TOL32["grad"]
