@@ -169,29 +169,36 @@ __device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, 
     return *s_ok != 0u;
 }
 
-template <int N, int NL> constexpr int z_rows() { return (2 * NL < N) ? 2 * NL : N; }
+// Z rows per item: NL (FP32), 2 NL (FP64); fewer rows keep the shared memory
+// of a CTA small enough for four CTAs per SM in FP32.
+template <typename R, int N, int NL> constexpr int z_rows() {
+    return ((sizeof(R) == 4 ? 1 : 2) * NL < N) ? (sizeof(R) == 4 ? 1 : 2) * NL : N;
+}
 
 // Row pitch of the staged ring rows of a Z item: HP plus 16 bytes of skew, so
 // that the rows of one warp access spread over all banks (row stride an odd
 // multiple of 16 bytes modulo 128).
 template <typename V, int N> constexpr int z_row_pitch() { return row_pitch(N) + 16 / (int)sizeof(V); }
 
-template <typename R, int N, int NL>
+// The fused kernel runs threads_for<N, TL> threads (TL = tile_lines) on Y
+// items of NLY columns and Z items of z_rows<R, N, TL> rows.
+template <typename R, int N, int TL, int NLY>
 constexpr size_t yz_smem_elems() {
     using V = typename Cx<R>::T;
-    constexpr int NR = z_rows<N, NL>();
-    constexpr size_t y = (size_t)N * NL;
+    constexpr int NR = z_rows<R, N, TL>();
+    constexpr size_t y = (size_t)N * NLY;
     constexpr size_t z = (size_t)NR * z_row_pitch<V, N>() + (size_t)(N / 2) * (NR + 1);
     return N + (y > z ? y : z);
 }
 
-// CTAs per SM the fused kernel is compiled for: about 24 warps per SM.
-template <int N, int NL> constexpr int yz_min_blocks() {
-    return (768 / threads_for<N, NL>()) < 1 ? 1 : (768 / threads_for<N, NL>());
+// CTAs per SM the fused kernel is compiled for: 32 warps per SM (FP32), 24 (FP64).
+template <typename R, int N, int NL> constexpr int yz_min_blocks() {
+    constexpr int W = sizeof(R) == 4 ? 1024 : 768;
+    return (W / threads_for<N, NL>()) < 1 ? 1 : (W / threads_for<N, NL>());
 }
 
-template <typename R, typename OutT, int N, int NL>
-__global__ void __launch_bounds__(threads_for<N, NL>(), yz_min_blocks<N, NL>())
+template <typename R, typename OutT, int N, int NL, int NLY>
+__global__ void __launch_bounds__(threads_for<N, NL>(), yz_min_blocks<R, N, NL>())
 fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
              const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int lag, int ring_slots,
              int drop_signals) {
@@ -199,9 +206,9 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     constexpr int T = threads_for<N, NL>();
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
     constexpr int M = N / 2;
-    constexpr int NR = z_rows<N, NL>();                 // Z rows per item: same thread count as a Y item
-    constexpr int QY = NL, QZ = NR + 1;
-    constexpr int TPZ = (H + NL - 1) / NL;              // Y items per plane
+    constexpr int NR = z_rows<R, N, NL>();              // Z rows per item: same thread count as a Y item
+    constexpr int QY = NLY, QZ = NR + 1;
+    constexpr int TPZ = (H + NLY - 1) / NLY;            // Y items per plane
     constexpr int ZPP = N / NR;                         // Z items per plane
     constexpr int IPP = TPZ + ZPP;
     constexpr long long PLANES = 3LL * N;
@@ -209,7 +216,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     constexpr int RP = z_row_pitch<V, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tws = reinterpret_cast<V*>(smem_raw);
-    V* buf = tws + N;                                   // Y: [N][QY] tile
+    V* buf = tws + N;                                   // Y: [N][QY] tile of NLY columns
     V* raw = buf;                                       // Z: NR ring rows, pitch RP
     V* trans = buf + NR * RP;                           // Z: [M][QZ] transform buffer
     __shared__ unsigned s_item, s_ok;
@@ -230,8 +237,8 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
         V* slot = ring + (pl % ring_slots) * (long long)N * HP;
         if (r < TPZ) {
             // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
-            const int kz0 = r * NL;
-            const int valid = std::min(NL, H - kz0);
+            const int kz0 = r * NLY;
+            const int valid = std::min(NLY, H - kz0);
             const V* src = w + pl * N * HP + kz0;
             V* dst = slot + kz0;
             auto ld = [&](int q, int b) -> V { return (b < valid) ? src[(long long)q * HP + b] : mk<V>(R(0), R(0)); };
@@ -240,13 +247,13 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             };
             if constexpr (radix_for(N) == N) {
                 if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
-                stage_single<V, N, NL, T>(ld, st);
+                stage_single<V, N, NLY, T>(ld, st);
             } else {
-                stage_first<V, N, NL, T, QY>(buf, ld);
-                stages_mid<V, N, NL, T, QY, radix_for(N)>(buf, tws, 1);
+                stage_first<V, N, NLY, T, QY>(buf, ld);
+                stages_mid<V, N, NLY, T, QY, radix_for(N)>(buf, tws, 1);
                 // the slot is free once the Z items of the plane that used it before have read it
                 if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
-                stage_last<V, N, NL, T, QY, false>(buf, tws, 1, st);
+                stage_last<V, N, NLY, T, QY, false>(buf, tws, 1, st);
             }
             __syncthreads();
             if (t == 0 && !drop_signals) {
@@ -298,6 +305,9 @@ template <typename V> size_t transform_workspace(int N) {
     return sizeof(V) * (3ull * N * N * HP + (size_t)kRingMax * N * HP) + sizeof(unsigned) * (1 + 6ull * N);
 }
 
+// Y-item columns in units of tile_lines.
+constexpr int kYCols = 1;
+
 template <typename R, typename OutT, int N>
 int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
     using V = typename Cx<R>::T;
@@ -327,14 +337,14 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         k<<<(unsigned)(3 * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw);
     }
     {
-        auto k = fft_yz_fused<R, OutT, N, NL>;
-        constexpr int NR = z_rows<N, NL>();
-        const size_t sm = sizeof(V) * yz_smem_elems<R, N, NL>();
+        auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
+        constexpr int NR = z_rows<R, N, NL>();
+        const size_t sm = sizeof(V) * yz_smem_elems<R, N, NL, kYCols * NL>();
         if ((rc = set_smem(k, sm))) return rc;
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, sm);
         if (e != cudaSuccess) return set_cuda_error(e);
-        const int ipp = (H + NL - 1) / NL + N / NR;
+        const int ipp = (H + kYCols * NL - 1) / (kYCols * NL) + N / NR;
         const long long items = 3LL * N * ipp;
         const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
         // planes in progress at once ~ grid / items-per-plane; consumers trail by that plus a margin
