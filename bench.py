@@ -148,9 +148,9 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
     return {
         "fft_x": 2 * spec,                       # read u_hat, write the x-transformed spectrum
         "fft_yz": spec + coef,                   # read that spectrum, write coefficients (ring stays in L2)
-        "bin": P * (24 + 8 + rec),               # positions in; key, rank, record out
-        "scan": 2 * 4 * (nb + 1),
-        "scatter": P * (8 + rec) + P * (rec + 4),          # key, rank, record in; sorted record, index out
+        "bin": P * 24,                           # positions in (per-brick counts stay in L2)
+        "scan": 4 * 4 * (nb + 1),
+        "scatter": P * 24 + P * (rec + 4),       # positions in again; sorted record and index out
         "gather": coef + P * (rec + 4) + P * 12 * outb,    # coefficients once, sorted records, u and grad out
     }[stage]
 

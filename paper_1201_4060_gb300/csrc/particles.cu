@@ -90,62 +90,68 @@ __device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
     return (unsigned)(r < 0 ? r + N : r);
 }
 
+// Locate one particle (Eq. alg-int-6): its brick key and record; the key is NB
+// for a non-finite position or one with no fractional bits left.
+template <typename TR>
+__device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
+                                                    int order, int nbx, int bshift, unsigned NB, Rec<TR>* r) {
+    unsigned anc[3];
+    TR tt[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double s = x[3 * p + a] * scale;
+        if constexpr (sizeof(TR) == 4) {
+            long long base;
+            float tf;
+            if (locate_nonneg(s, order, &base, &tf)) {
+                tt[a] = tf;
+                anc[a] = wrap_anchor(base + 1, N);
+                continue;
+            }
+        }
+        const double sh = s - 0.5 * order;
+        if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
+            ok = false;
+            anc[a] = 0;
+            tt[a] = 0;
+            continue;
+        }
+        const double f = floor(sh);
+        tt[a] = (TR)(sh - f);
+        anc[a] = wrap_anchor((long long)f + 1, N);
+    }
+    if (!ok) return NB;
+    r->cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
+    r->t[0] = tt[0];
+    r->t[1] = tt[1];
+    r->t[2] = tt[2];
+    return ((anc[0] >> bshift) * nbx + (anc[1] >> bshift)) * nbx + (anc[2] >> bshift);
+}
+
+// Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
+// counted in the status word).
 template <typename TR>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                            int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
-        unsigned anc[3];
-        TR tt[3];
-        bool ok = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double s = x[3 * p + a] * scale;
-            if constexpr (sizeof(TR) == 4) {
-                long long base;
-                float tf;
-                if (locate_nonneg(s, order, &base, &tf)) {
-                    tt[a] = tf;
-                    anc[a] = wrap_anchor(base + 1, N);
-                    continue;
-                }
-            }
-            const double sh = s - 0.5 * order;
-            if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
-                ok = false;
-                anc[a] = 0;
-                tt[a] = 0;
-                continue;
-            }
-            const double f = floor(sh);
-            tt[a] = (TR)(sh - f);
-            anc[a] = wrap_anchor((long long)f + 1, N);
-        }
-        unsigned k = NB;
-        if (ok) {
-            k = ((anc[0] >> bshift) * nbx + (anc[1] >> bshift)) * nbx + (anc[2] >> bshift);
-            Rec<TR> r;
-            r.cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
-            r.t[0] = tt[0];
-            r.t[1] = tt[1];
-            r.t[2] = tt[2];
-            w.rec[p] = r;
-        } else {
-            atomicAdd(status, 1ULL);
-        }
-        w.key[p] = k;
-        w.rank[p] = atomicAdd(&w.count[k], 1u);
+        Rec<TR> r;
+        const unsigned k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
+        if (k == NB) atomicAdd(status, 1ULL);
+        atomicAdd(&w.count[k], 1u);
     }
 }
 
 // ------------------------------------------------------------------ scan (single CTA)
 // Exclusive prefix sums over the NB + 1 bins (NB bricks, then the invalid
-// bin): offset[] of the counts, and chunk[] (bricks only) of the number of
+// bin): offset[] of the counts (and a copy, cursor[], for the placement
+// pass), and chunk[] (bricks only) of the number of
 // gather work items per brick, ceil(count / kChunk); item[] maps each work
 // item back to its brick.
 __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
-                                                    unsigned* __restrict__ chunk, unsigned* __restrict__ item,
-                                                    unsigned NB) {
+                                                    unsigned* __restrict__ cursor, unsigned* __restrict__ chunk,
+                                                    unsigned* __restrict__ item, unsigned NB) {
     __shared__ unsigned part[1024], partc[1024];
     const unsigned n = NB + 1;
     const unsigned t = threadIdx.x;
@@ -172,6 +178,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
     for (unsigned i = b; i < e; ++i) {
         const unsigned ci = count[i];
         offset[i] = run;
+        cursor[i] = run;
         run += ci;
         if (i < NB) {
             chunk[i] = runc;
@@ -186,13 +193,17 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
     }
 }
 
-// ------------------------------------------------------------------ scatter
+// ------------------------------------------------------------------ place
+// Counting sort, pass 2: locate again (cheaper than storing and re-reading the
+// records) and write each record and its original index to the next free slot
+// of its brick.  Invalid positions get NaN outputs.
 template <typename TR, typename OT>
-__global__ void scatter_kernel(long long P, unsigned NB, Ws<TR> w, OT* __restrict__ out_u,
-                               OT* __restrict__ out_grad) {
+__global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order, int nbx,
+                               int bshift, unsigned NB, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
-        const unsigned k = w.key[p];
+        Rec<TR> r;
+        const unsigned k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
         if (k >= NB) {
             const OT nan = (OT)NAN;
             if (out_u) {
@@ -205,8 +216,8 @@ __global__ void scatter_kernel(long long P, unsigned NB, Ws<TR> w, OT* __restric
             }
             continue;
         }
-        const unsigned d = w.offset[k] + w.rank[p];
-        w.s_rec[d] = w.rec[p];
+        const unsigned d = atomicAdd(&w.cursor[k], 1u);
+        w.s_rec[d] = r;
         w.s_idx[d] = (unsigned)p;
     }
 }
@@ -255,11 +266,12 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, w.item, NB);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u,
+        scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
+                                                                 bshift, NB, w, (AT*)out_u,
                                                                  grad ? (AT*)out_grad : nullptr);
     }
     {
@@ -287,8 +299,9 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
                                                      bshift, NB, w, status);
-    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, w.item, NB);
-    scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
+    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
+    scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx, bshift,
+                                                             NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
@@ -335,11 +348,12 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.chunk, w.item, NB);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(P, NB, w, g_x, nullptr);
+        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
+                                                                     bshift, NB, w, g_x, nullptr);
     }
     const long long items = (long long)NB + (P + kChunk - 1) / kChunk;
     if (g_coef) {

@@ -25,13 +25,11 @@ constexpr unsigned kChunk = 1024;
 template <typename TR> struct Ws {
     unsigned* count;    // [NB + 1]  particles per brick; slot NB = invalid positions
     unsigned* offset;   // [NB + 2]  exclusive prefix sum of count
+    unsigned* cursor;   // [NB + 1]  next free sorted slot of each brick (starts at offset)
     unsigned* chunk;    // [NB + 1]  exclusive prefix sum of ceil(count / kChunk): first work item of a brick
     unsigned* item;     // [NB + ceil(P / kChunk)]  brick of each work item (the first chunk[NB] are set)
     long long P;        // particles
-    unsigned* key;      // [P]
-    unsigned* rank;     // [P]
-    Rec<TR>* rec;       // [P]       located records in input order
-    Rec<TR>* s_rec;     // [P]       sorted by brick
+    Rec<TR>* s_rec;     // [P]       located records sorted by brick
     unsigned* s_idx;    // [P]       original particle index of each sorted record
 };
 
@@ -47,11 +45,9 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     w->P = P;
     w->count = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 2));
+    w->cursor = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->chunk = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->item = (unsigned*)take(sizeof(unsigned) * (NB + (P + kChunk - 1) / kChunk));
-    w->key = (unsigned*)take(sizeof(unsigned) * P);
-    w->rank = (unsigned*)take(sizeof(unsigned) * P);
-    w->rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
     w->s_rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
     w->s_idx = (unsigned*)take(sizeof(unsigned) * P);
     return off;
