@@ -152,44 +152,60 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
 __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
                                                     unsigned* __restrict__ cursor, unsigned* __restrict__ chunk,
                                                     unsigned* __restrict__ item, unsigned NB) {
-    __shared__ unsigned part[1024], partc[1024];
+    __shared__ unsigned ws[32], wc[32];
     const unsigned n = NB + 1;
-    const unsigned t = threadIdx.x;
-    const unsigned per = (n + 1023) / 1024;
-    const unsigned b = min(n, t * per), e = min(n, b + per);
-    unsigned s = 0, sc = 0;
-    for (unsigned i = b; i < e; ++i) {
-        const unsigned ci = count[i];
-        s += ci;
-        if (i < NB) sc += (ci + kChunk - 1) / kChunk;
-    }
-    part[t] = s;
-    partc[t] = sc;
-    __syncthreads();
-    for (unsigned d = 1; d < 1024; d <<= 1) {
-        const unsigned v = (t >= d) ? part[t - d] : 0;
-        const unsigned vc = (t >= d) ? partc[t - d] : 0;
-        __syncthreads();
-        part[t] += v;
-        partc[t] += vc;
-        __syncthreads();
-    }
-    unsigned run = part[t] - s, runc = partc[t] - sc;      // exclusive
-    for (unsigned i = b; i < e; ++i) {
-        const unsigned ci = count[i];
-        offset[i] = run;
-        cursor[i] = run;
-        run += ci;
-        if (i < NB) {
-            chunk[i] = runc;
-            const unsigned nc = (ci + kChunk - 1) / kChunk;
-            for (unsigned k = 0; k < nc; ++k) item[runc + k] = i;
-            runc += nc;
+    const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned carry = 0, carryc = 0;
+    // tiles of 1024 consecutive bins, one per thread: warp scans, then a scan of the 32 warp totals
+    for (unsigned b0 = 0; b0 < n; b0 += 1024) {
+        const unsigned i = b0 + t;
+        const unsigned ci = i < n ? count[i] : 0u;
+        const unsigned nc = i < NB ? (ci + kChunk - 1) / kChunk : 0u;
+        unsigned v = ci, vc = nc;
+#pragma unroll
+        for (unsigned d = 1; d < 32; d <<= 1) {
+            const unsigned a = __shfl_up_sync(0xffffffffu, v, d), ac = __shfl_up_sync(0xffffffffu, vc, d);
+            if (lane >= d) {
+                v += a;
+                vc += ac;
+            }
         }
+        if (lane == 31) {
+            ws[warp] = v;
+            wc[warp] = vc;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            unsigned x = ws[lane], xc = wc[lane];
+#pragma unroll
+            for (unsigned d = 1; d < 32; d <<= 1) {
+                const unsigned a = __shfl_up_sync(0xffffffffu, x, d), ac = __shfl_up_sync(0xffffffffu, xc, d);
+                if (lane >= d) {
+                    x += a;
+                    xc += ac;
+                }
+            }
+            ws[lane] = x;
+            wc[lane] = xc;
+        }
+        __syncthreads();
+        const unsigned ex = carry + (warp ? ws[warp - 1] : 0u) + v - ci;         // exclusive
+        const unsigned exc = carryc + (warp ? wc[warp - 1] : 0u) + vc - nc;
+        if (i < n) {
+            offset[i] = ex;
+            cursor[i] = ex;
+        }
+        if (i < NB) {
+            chunk[i] = exc;
+            for (unsigned k = 0; k < nc; ++k) item[exc + k] = i;
+        }
+        carry += ws[31];
+        carryc += wc[31];
+        __syncthreads();                                  // the totals are read before the next tile
     }
-    if (t == 1023) {
-        offset[n] = part[1023];
-        chunk[NB] = partc[1023];
+    if (t == 0) {
+        offset[n] = carry;
+        chunk[NB] = carryc;
     }
 }
 
