@@ -20,7 +20,7 @@ template <typename TR> struct __align__(16) Rec {
 
 // Particles per gather work item: a brick with more particles is split into
 // several items, each staging the brick's tile, so no CTA serialises a clump.
-constexpr unsigned kChunk = 1024;
+constexpr unsigned kChunk = 2048;
 
 template <typename TR> struct Ws {
     unsigned* count;    // [NB + 1]  particles per brick; slot NB = invalid positions
@@ -424,7 +424,6 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* tile = reinterpret_cast<float*>(smem_raw);
     __shared__ unsigned s_bucket[32];
-    __shared__ unsigned short s_rank[kChunk];
     __shared__ unsigned short s_order[kChunk];
     const unsigned item = blockIdx.x;
     if (item >= w.chunk[NB]) return;
@@ -438,30 +437,36 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
         const int n = (int)min(kChunk, end - c0);
         if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
         __syncthreads();                                  // the tile copies stay in flight while bucketing
-        for (int i = threadIdx.x; i < n; i += kGatherThreads) {
-            const unsigned cp = w.s_rec[c0 + i].cell;
-            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
-            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
-            const int oz = (int)(cp & 1023u) - z0;
-            const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
-            s_rank[i] = (unsigned short)atomicAdd(&s_bucket[r], 1u);
+        // bucket (bank residue of the stencil origin) and rank within it, kept in registers
+        constexpr int KT = (kChunk + kGatherThreads - 1) / kGatherThreads;
+        unsigned packed[KT];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int i = threadIdx.x + k * kGatherThreads;
+            if (i < n) {
+                const unsigned cp = w.s_rec[c0 + i].cell;
+                const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
+                const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
+                const int oz = (int)(cp & 1023u) - z0;
+                const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
+                packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
+            }
         }
         __syncthreads();
         // job-sorted position: all particles of smaller rank, then the same rank in smaller buckets
-        for (int i = threadIdx.x; i < n; i += kGatherThreads) {
-            const unsigned cp = w.s_rec[c0 + i].cell;
-            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
-            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
-            const int oz = (int)(cp & 1023u) - z0;
-            const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
-            const unsigned k = s_rank[i];
-            unsigned pos = 0;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int i = threadIdx.x + k * kGatherThreads;
+            if (i < n) {
+                const unsigned r = packed[k] & 31u, rk = packed[k] >> 5;
+                unsigned pos = 0;
 #pragma unroll 8
-            for (unsigned q = 0; q < 32; ++q) {
-                const unsigned bq = s_bucket[q];
-                pos += min(bq, k) + ((q < r && bq > k) ? 1u : 0u);
+                for (unsigned q = 0; q < 32; ++q) {
+                    const unsigned bq = s_bucket[q];
+                    pos += min(bq, rk) + ((q < r && bq > rk) ? 1u : 0u);
+                }
+                s_order[pos] = (unsigned short)i;
             }
-            s_order[pos] = (unsigned short)i;
         }
         cp_async_wait_all();
         __syncthreads();                                  // tile and order ready
