@@ -225,8 +225,14 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     unsigned* done_z = ctr + 1 + PLANES;
     const int t = threadIdx.x;
     for (int m = t; m < N; m += T) tws[m] = tw[m];
+    // thread 0 claims the following item while this one runs (its counter round trip overlaps the work);
+    // a claimed item depends only on earlier items, so the smallest running item can always proceed
+    unsigned claimed = (t == 0) ? atomicAdd(next, 1u) : 0u;
     for (;;) {
-        if (t == 0) s_item = (ld_acquire(error) != 0u) ? 0xffffffffu : atomicAdd(next, 1u);
+        if (t == 0) {
+            s_item = (ld_acquire(error) != 0u) ? 0xffffffffu : claimed;
+            claimed = atomicAdd(next, 1u);
+        }
         __syncthreads();
         const unsigned item = s_item;
         __syncthreads();
@@ -347,8 +353,9 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         const int ipp = (H + kYCols * NL - 1) / (kYCols * NL) + N / NR;
         const long long items = 3LL * N * ipp;
         const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
-        // planes in progress at once ~ grid / items-per-plane; consumers trail by that plus a margin
-        const int lag = (int)std::min<long long>(kRingMax / 2, (grid + ipp - 1) / ipp + 2);
+        // planes in progress at once ~ 2 grid / items-per-plane (each CTA runs one item and has claimed
+        // the next); consumers trail by that plus a margin
+        const int lag = (int)std::min<long long>(kRingMax / 2, (2 * grid + ipp - 1) / ipp + 2);
         const int ring_slots = 2 * lag;
         V* ring = w + 3LL * N * N * HP;
         unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRingMax * N * HP);
