@@ -219,7 +219,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     V* buf = tws + N;                                   // Y: [N][QY] tile of NLY columns
     V* raw = buf;                                       // Z: NR ring rows, pitch RP
     V* trans = buf + NR * RP;                           // Z: [M][QZ] transform buffer
-    __shared__ unsigned s_item, s_ok;
+    __shared__ unsigned s_item[2], s_ok;
     unsigned* next = ctr;
     unsigned* done_y = ctr + 1;
     unsigned* done_z = ctr + 1 + PLANES;
@@ -228,14 +228,14 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     // thread 0 claims the following item while this one runs (its counter round trip overlaps the work);
     // a claimed item depends only on earlier items, so the smallest running item can always proceed
     unsigned claimed = (t == 0) ? atomicAdd(next, 1u) : 0u;
-    for (;;) {
+    for (unsigned it = 0;; ++it) {
+        // alternate slots: the slot written now was last read two items ago, before this item's barriers
         if (t == 0) {
-            s_item = (ld_acquire(error) != 0u) ? 0xffffffffu : claimed;
+            s_item[it & 1u] = (ld_acquire(error) != 0u) ? 0xffffffffu : claimed;
             claimed = atomicAdd(next, 1u);
         }
         __syncthreads();
-        const unsigned item = s_item;
-        __syncthreads();
+        const unsigned item = s_item[it & 1u];
         if (item >= (unsigned)(PLANES * IPP)) return;
         long long pl;
         int r;
