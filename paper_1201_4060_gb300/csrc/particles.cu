@@ -131,15 +131,47 @@ __device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x
 
 // Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
 // counted in the status word).
+// Below this many bricks, particles of one warp often share a brick: aggregate their counter updates.
+constexpr unsigned kAggregateBricks = 4096;
+
+// Warp-aggregated increment of counter[key] for the lanes of `active`: one
+// atomic per distinct key in the warp (few bricks, many particles: small
+// grids); returns this lane's slot (old value + its rank among equal keys).
+__device__ __forceinline__ unsigned warp_increment(unsigned* counter, unsigned key, unsigned active, bool need_old) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned peers = __match_any_sync(active, key);
+    const unsigned leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = need_old ? atomicAdd(&counter[key], (unsigned)__popc(peers))
+                                        : (atomicAdd(&counter[key], (unsigned)__popc(peers)), 0u);
+    base = __shfl_sync(peers, base, leader);
+    return base + (unsigned)__popc(peers & ((1u << lane) - 1u));
+}
+
+// Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
+// counted in the status word).  The grid-stride loop runs warp-uniformly so that
+// lanes can aggregate their increments (aggregate = few bricks).
 template <typename TR>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
-                           int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status) {
+                           int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status,
+                           int aggregate) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
-        Rec<TR> r;
-        const unsigned k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
-        if (k == NB) atomicAdd(status, 1ULL);
-        atomicAdd(&w.count[k], 1u);
+    const long long lane = threadIdx.x & 31;
+    for (long long pw = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; pw < P; pw += stride) {
+        const long long p = pw + lane;
+        const bool valid = p < P;
+        unsigned k = 0;
+        if (valid) {
+            Rec<TR> r;
+            k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
+            if (k == NB) atomicAdd(status, 1ULL);
+        }
+        if (aggregate) {
+            const unsigned active = __ballot_sync(0xffffffffu, valid);
+            if (valid) warp_increment(w.count, k, active, false);
+        } else if (valid) {
+            atomicAdd(&w.count[k], 1u);
+        }
     }
 }
 
@@ -215,12 +247,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
 // of its brick.  Invalid positions get NaN outputs.
 template <typename TR, typename OT>
 __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order, int nbx,
-                               int bshift, unsigned NB, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad) {
+                               int bshift, unsigned NB, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
+                               int aggregate) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+    const long long lane = threadIdx.x & 31;
+    for (long long pw = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; pw < P; pw += stride) {
+        const long long p = pw + lane;
         Rec<TR> r;
-        const unsigned k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
-        if (k >= NB) {
+        unsigned k = NB;
+        if (p < P) k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
+        if (p < P && k >= NB) {
             const OT nan = (OT)NAN;
             if (out_u) {
 #pragma unroll
@@ -230,11 +266,19 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
 #pragma unroll
                 for (int i = 0; i < 9; ++i) out_grad[9 * p + i] = nan;
             }
-            continue;
         }
-        const unsigned d = atomicAdd(&w.cursor[k], 1u);
-        w.s_rec[d] = r;
-        w.s_idx[d] = (unsigned)p;
+        const bool place = p < P && k < NB;
+        unsigned d = 0;
+        if (aggregate) {
+            const unsigned active = __ballot_sync(0xffffffffu, place);
+            if (place) d = warp_increment(w.cursor, k, active, true);
+        } else if (place) {
+            d = atomicAdd(&w.cursor[k], 1u);
+        }
+        if (place) {
+            w.s_rec[d] = r;
+            w.s_idx[d] = (unsigned)p;
+        }
     }
 }
 
@@ -278,7 +322,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
         bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                         bshift, NB, w, p->d_status);
+                                                         bshift, NB, w, p->d_status, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -288,7 +332,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
         scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
                                                                  bshift, NB, w, (AT*)out_u,
-                                                                 grad ? (AT*)out_grad : nullptr);
+                                                                 grad ? (AT*)out_grad : nullptr, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_GATHER);
@@ -314,10 +358,11 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                     bshift, NB, w, status);
+                                                     bshift, NB, w, status, NB < kAggregateBricks);
     scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx, bshift,
-                                                             NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr);
+                                                             NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
+                                                             NB < kAggregateBricks);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
@@ -360,7 +405,7 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
         bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                         bshift, NB, w, p->d_status);
+                                                         bshift, NB, w, p->d_status, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -369,7 +414,7 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
         scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                                     bshift, NB, w, g_x, nullptr);
+                                                                     bshift, NB, w, g_x, nullptr, NB < kAggregateBricks);
     }
     const long long items = (long long)NB + (P + kChunk - 1) / kChunk;
     if (g_coef) {
