@@ -222,6 +222,9 @@ void free_plan(bspline_plan_s* p) {
     if (p->d_status) cudaFree(p->d_status);
     p->work.release();
     p->pws.release();
+    if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
+    if (p->ev_sorted) cudaEventDestroy(p->ev_sorted);
     p->host_uhat.release();
     p->host_coef.release();
     p->host_x.release();
@@ -384,6 +387,11 @@ int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {
     return BSPLINE_OK;
 }
 
+// Copies and compute overlap on two streams: the positions go first on the
+// second stream and are sorted there while u_hat is copied component by
+// component on the plan's stream, each component transformed as soon as it
+// has arrived; the gather waits for the sort and the last component, then the
+// results are copied back.
 int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P, void* u_host,
                      void* grad_host) {
     if (!valid_plan(plan) || !u_hat_host || !u_host || (P > 0 && !x_host)) return BSPLINE_ERR_INVALID_ARG;
@@ -397,23 +405,38 @@ int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* 
     if ((rc = plan->host_x.grow(sizeof(double) * 3 * (size_t)(P ? P : 1)))) return rc;
     if ((rc = plan->host_u.grow(ob * 3 * (size_t)(P ? P : 1)))) return rc;
     if ((rc = plan->host_grad.grow(ob * 9 * (size_t)(P ? P : 1)))) return rc;
-    cudaStream_t st = plan->stream;
-    cudaError_t e = cudaMemcpyAsync(plan->host_uhat.ptr, u_hat_host, uhat_bytes_of(plan), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && P)
-        e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaSuccess;
+    if (!plan->aux_stream) e = cudaStreamCreateWithFlags(&plan->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !plan->ev_start) e = cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess && !plan->ev_sorted) e = cudaEventCreateWithFlags(&plan->ev_sorted, cudaEventDisableTiming);
     if (e != cudaSuccess) return set_cuda_error(e);
-    if ((rc = launch_coeffs(plan, plan->host_uhat.ptr, plan->host_coef.ptr))) return rc;
+    cudaStream_t st = plan->stream, aux = plan->aux_stream;
+    // the second stream starts after everything already queued on the plan's stream
+    e = cudaEventRecord(plan->ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, plan->ev_start, 0);
+    if (e == cudaSuccess && P)
+        e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, aux);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    const size_t comp = uhat_bytes_of(plan) / 3;
+    for (int c = 0; c < 3; ++c) {
+        e = cudaMemcpyAsync((char*)plan->host_uhat.ptr + c * comp, (const char*)u_hat_host + c * comp, comp,
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        if ((rc = launch_coeffs_range(plan, plan->host_uhat.ptr, plan->host_coef.ptr, c, c + 1))) return rc;
+    }
     if (P) {
         const int flags = grad_host ? 0 : BSPLINE_INTERP_NO_GRAD;
-        if ((rc = launch_interp(plan, plan->host_coef.ptr, (const double*)plan->host_x.ptr, P, plan->host_u.ptr,
-                                plan->host_grad.ptr, flags)))
+        if ((rc = launch_interp_split(plan, plan->host_coef.ptr, (const double*)plan->host_x.ptr, P, plan->host_u.ptr,
+                                      plan->host_grad.ptr, flags, aux, plan->ev_sorted)))
             return rc;
         e = cudaMemcpyAsync(u_host, plan->host_u.ptr, ob * 3 * P, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && grad_host)
             e = cudaMemcpyAsync(grad_host, plan->host_grad.ptr, ob * 9 * P, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
-    return set_cuda_error(cudaStreamSynchronize(st));
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(aux);
+    return set_cuda_error(e);
 }
 
 int bspline_destroy(bspline_plan_t plan) {

@@ -36,7 +36,7 @@ using namespace fftc;
 template <typename R, int N, int NL>
 __global__ void __launch_bounds__(threads_for<N, NL>())
 fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __restrict__ out,
-                const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw) {
+                const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw, int comp0) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     static_assert(T % NL == 0, "each thread stays on one line");
@@ -47,7 +47,7 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* s = tws + N;
     const int t = threadIdx.x;
-    const int comp = (int)(blockIdx.x / TILES);
+    const int comp = comp0 + (int)(blockIdx.x / TILES);
     const long long b0 = (blockIdx.x % TILES) * NL;
     const int valid = (int)std::min<long long>(NL, NH - b0);
     for (int m = t; m < N; m += T) tws[m] = tw[m];
@@ -201,7 +201,7 @@ template <typename R, typename OutT, int N, int NL, int NLY>
 __global__ void __launch_bounds__(threads_for<N, NL>(), yz_min_blocks<R, N, NL>())
 fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
              const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int lag, int ring_slots,
-             int drop_signals) {
+             int drop_signals, long long plane0, long long planes) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
@@ -211,7 +211,6 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     constexpr int TPZ = (H + NLY - 1) / NLY;            // Y items per plane
     constexpr int ZPP = N / NR;                         // Z items per plane
     constexpr int IPP = TPZ + ZPP;
-    constexpr long long PLANES = 3LL * N;
     constexpr int CHUNKS = HP * (int)sizeof(V) / 16;    // 16-byte pieces of one ring row
     constexpr int RP = z_row_pitch<V, N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -222,7 +221,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     __shared__ unsigned s_item[2], s_ok;
     unsigned* next = ctr;
     unsigned* done_y = ctr + 1;
-    unsigned* done_z = ctr + 1 + PLANES;
+    unsigned* done_z = ctr + 1 + planes;
     const int t = threadIdx.x;
     for (int m = t; m < N; m += T) tws[m] = tw[m];
     // thread 0 claims the following item while this one runs (its counter round trip overlaps the work);
@@ -236,11 +235,12 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
         }
         __syncthreads();
         const unsigned item = s_item[it & 1u];
-        if (item >= (unsigned)(PLANES * IPP)) return;
-        long long pl;
+        if (item >= (unsigned)(planes * IPP)) return;
+        long long lp;                                   // plane within this launch; pl = plane0 + lp
         int r;
-        item_to_plane<TPZ, ZPP>(item, PLANES, lag, &pl, &r);
-        V* slot = ring + (pl % ring_slots) * (long long)N * HP;
+        item_to_plane<TPZ, ZPP>(item, planes, lag, &lp, &r);
+        const long long pl = plane0 + lp;
+        V* slot = ring + (lp % ring_slots) * (long long)N * HP;
         if (r < TPZ) {
             // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
             const int kz0 = r * NLY;
@@ -252,23 +252,23 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
                 if (b < valid) dst[(long long)q * HP + b] = v;
             };
             if constexpr (radix_for(N) == N) {
-                if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
+                if (lp >= ring_slots && !cta_wait(&done_z[lp - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
                 stage_single<V, N, NLY, T>(ld, st);
             } else {
                 stage_first<V, N, NLY, T, QY>(buf, ld);
                 stages_mid<V, N, NLY, T, QY, radix_for(N)>(buf, tws, 1);
                 // the slot is free once the Z items of the plane that used it before have read it
-                if (pl >= ring_slots && !cta_wait(&done_z[pl - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
+                if (lp >= ring_slots && !cta_wait(&done_z[lp - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
                 stage_last<V, N, NLY, T, QY, false>(buf, tws, 1, st);
             }
             __syncthreads();
             if (t == 0 && !drop_signals) {
                 __threadfence();
-                atomicAdd(&done_y[pl], 1u);
+                atomicAdd(&done_y[lp], 1u);
             }
         } else {
             // ---- Z item: rows y0..y0+NR-1 of the plane, c2r along kz
-            if (!cta_wait(&done_y[pl], (unsigned)TPZ, error, &s_ok)) return;
+            if (!cta_wait(&done_y[lp], (unsigned)TPZ, error, &s_ok)) return;
             const int y0 = (r - TPZ) * NR;
             const unsigned char* src = reinterpret_cast<const unsigned char*>(slot + (long long)y0 * HP);
             unsigned char* dstb = reinterpret_cast<unsigned char*>(raw);
@@ -280,7 +280,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             __syncthreads();                            // the slot's rows are read: release it
             if (t == 0) {
                 __threadfence();
-                atomicAdd(&done_z[pl], 1u);
+                atomicAdd(&done_z[lp], 1u);
             }
             auto ld = [&](int k, int b) -> V {          // even/odd split of the half spectrum
                 const V* row = raw + b * RP;
@@ -315,7 +315,7 @@ template <typename V> size_t transform_workspace(int N) {
 constexpr int kYCols = 1;
 
 template <typename R, typename OutT, int N>
-int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
+int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) {
     using V = typename Cx<R>::T;
     constexpr int NL = tile_lines<R>();
     constexpr int T = threads_for<N, NL>();
@@ -340,7 +340,8 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         if ((rc = set_smem(k, sm))) return rc;
         const long long tiles = ((long long)N * H + NLX - 1) / NLX;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);
-        k<<<(unsigned)(3 * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c, tw);
+        k<<<(unsigned)((c1 - c0) * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c,
+                                                                             tw, c0);
     }
     {
         auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
@@ -351,29 +352,32 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, sm);
         if (e != cudaSuccess) return set_cuda_error(e);
         const int ipp = (H + kYCols * NL - 1) / (kYCols * NL) + N / NR;
-        const long long items = 3LL * N * ipp;
+        const long long planes = (long long)(c1 - c0) * N;
+        const long long items = planes * ipp;
         const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
         // planes in progress at once ~ 2 grid / items-per-plane (each CTA runs one item and has claimed
         // the next); consumers trail by that plus a margin
-        const int lag = (int)std::min<long long>(kRingMax / 2, (2 * grid + ipp - 1) / ipp + 2);
+        const int lag = (int)std::min<long long>(std::min<long long>(kRingMax / 2, planes),
+                                                 (2 * grid + ipp - 1) / ipp + 2);
         const int ring_slots = 2 * lag;
         V* ring = w + 3LL * N * N * HP;
         unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRingMax * N * HP);
-        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 6LL * N), st);
+        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 2 * planes), st);
         if (e != cudaSuccess) return set_cuda_error(e);
         StageTimer tm(p, BSPLINE_STAGE_FFT_YZ);
         k<<<(unsigned)grid, T, sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), ring, tw, ctr,
                                          reinterpret_cast<unsigned*>(p->d_status + 1), lag, ring_slots,
-                                         (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0);
+                                         (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0,
+                                         (long long)c0 * N, planes);
     }
     return set_cuda_error(cudaGetLastError());
 }
 
-template <int N> int run_n(bspline_plan_s* p, const void* u_hat, void* coeffs) {
+template <int N> int run_n(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) {
     switch (p->dtype) {
-        case BSPLINE_F64: return run_fft<double, double, N>(p, u_hat, coeffs);
-        case BSPLINE_F32: return run_fft<float, float, N>(p, u_hat, coeffs);
-        case BSPLINE_BF16: return run_fft<float, __nv_bfloat16, N>(p, u_hat, coeffs);
+        case BSPLINE_F64: return run_fft<double, double, N>(p, u_hat, coeffs, c0, c1);
+        case BSPLINE_F32: return run_fft<float, float, N>(p, u_hat, coeffs, c0, c1);
+        case BSPLINE_BF16: return run_fft<float, __nv_bfloat16, N>(p, u_hat, coeffs, c0, c1);
     }
     return BSPLINE_ERR_INVALID_ARG;
 }
@@ -384,27 +388,31 @@ size_t coeffs_workspace_bytes(const bspline_plan_s* p) {
     return p->dtype == BSPLINE_F64 ? transform_workspace<double2>(p->N) : transform_workspace<float2>(p->N);
 }
 
-int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs) {
+int launch_coeffs_range(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) {
     int rc = p->work.grow(coeffs_workspace_bytes(p));
     if (rc) return rc;
-    cudaError_t e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(unsigned long long), p->stream);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    if (c0 == 0) {
+        cudaError_t e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(unsigned long long), p->stream);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
     switch (p->N) {
-        case 8: return run_n<8>(p, u_hat, coeffs);
-        case 16: return run_n<16>(p, u_hat, coeffs);
-        case 32: return run_n<32>(p, u_hat, coeffs);
-        case 64: return run_n<64>(p, u_hat, coeffs);
-        case 128: return run_n<128>(p, u_hat, coeffs);
-        case 256: return run_n<256>(p, u_hat, coeffs);
-        case 512: return run_n<512>(p, u_hat, coeffs);
-        case 1024: return run_n<1024>(p, u_hat, coeffs);
-        case 48: return run_n<48>(p, u_hat, coeffs);
-        case 96: return run_n<96>(p, u_hat, coeffs);
-        case 192: return run_n<192>(p, u_hat, coeffs);
-        case 384: return run_n<384>(p, u_hat, coeffs);
-        case 768: return run_n<768>(p, u_hat, coeffs);
+        case 8: return run_n<8>(p, u_hat, coeffs, c0, c1);
+        case 16: return run_n<16>(p, u_hat, coeffs, c0, c1);
+        case 32: return run_n<32>(p, u_hat, coeffs, c0, c1);
+        case 64: return run_n<64>(p, u_hat, coeffs, c0, c1);
+        case 128: return run_n<128>(p, u_hat, coeffs, c0, c1);
+        case 256: return run_n<256>(p, u_hat, coeffs, c0, c1);
+        case 512: return run_n<512>(p, u_hat, coeffs, c0, c1);
+        case 1024: return run_n<1024>(p, u_hat, coeffs, c0, c1);
+        case 48: return run_n<48>(p, u_hat, coeffs, c0, c1);
+        case 96: return run_n<96>(p, u_hat, coeffs, c0, c1);
+        case 192: return run_n<192>(p, u_hat, coeffs, c0, c1);
+        case 384: return run_n<384>(p, u_hat, coeffs, c0, c1);
+        case 768: return run_n<768>(p, u_hat, coeffs, c0, c1);
     }
     return BSPLINE_ERR_UNSUPPORTED_N;
 }
+
+int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs) { return launch_coeffs_range(p, u_hat, coeffs, 0, 3); }
 
 }  // namespace bs

@@ -68,8 +68,10 @@ struct bspline_plan_s {
     unsigned long long* d_status = nullptr;
     int sms = 1;            // streaming multiprocessors of the plan's device
     int test_hooks = 0;     // BSPLINE_TEST_* flags
-    // Buffers of bspline_run_host.
+    // Buffers, second stream and events of bspline_run_host.
     bs::DeviceBuffer host_uhat, host_coef, host_x, host_u, host_grad;
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_sorted = nullptr;
     // Per-kernel timing (bspline_plan_set_timing): event pairs recorded on the
     // plan's stream around each launch, resolved by bspline_stage_times.
     bool timing = false;
@@ -93,10 +95,17 @@ struct StageTimer {
 // Transform: u_hat -> coefficients (prefilter fused into the first pass).
 int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs);
 
+// Transform of components c0..c1-1 only (launch_coeffs = 0..3).
+int launch_coeffs_range(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1);
+
 // Particles: bin, sort and evaluate u and grad u.
 size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P);
 int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u,
                   void* out_grad, int flags);
+// The same, with the sort on sort_stream (recording `sorted` there) and the
+// gather on the plan's stream once `sorted` has been reached.
+int launch_interp_split(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u,
+                        void* out_grad, int flags, cudaStream_t sort_stream, cudaEvent_t sorted);
 // The same sequence on a caller-supplied workspace (interp_workspace_bytes bytes) and status word.
 int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs,
                      const double* x, int64_t P, void* out_u, void* out_grad, int flags);

@@ -303,9 +303,11 @@ inline unsigned grid_for(long long P, int threads) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// The sort (bin, scan, scatter) runs on sort_stream when one is given (it
+// needs only the positions) and the gather on the plan's stream after `sorted`.
 template <typename CT, typename AT, typename TR>
 int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
-               int flags) {
+               int flags, cudaStream_t sort_stream, cudaEvent_t sorted) {
     const int nbx = bricks_per_axis(p->N, p->dtype);
     const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
     const unsigned NB = (unsigned)nbx * nbx * nbx;
@@ -314,7 +316,14 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     int rc = p->pws.grow(need);
     if (rc) return rc;
     carve<TR>(&w, p->pws.ptr, NB, P);
-    cudaStream_t st = p->stream;
+    const cudaStream_t main_stream = p->stream;
+    cudaStream_t st = sort_stream ? sort_stream : main_stream;
+    p->stream = st;                                     // stage timers follow the sort's stream
+    struct Restore {
+        bspline_plan_s* p;
+        cudaStream_t s;
+        ~Restore() { p->stream = s; }
+    } restore{p, main_stream};
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
@@ -334,6 +343,11 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
                                                                  bshift, NB, w, (AT*)out_u,
                                                                  grad ? (AT*)out_grad : nullptr, NB < kAggregateBricks);
     }
+    if (sort_stream) {
+        if ((e = cudaEventRecord(sorted, sort_stream)) != cudaSuccess) return set_cuda_error(e);
+        if ((e = cudaStreamWaitEvent(main_stream, sorted, 0)) != cudaSuccess) return set_cuda_error(e);
+    }
+    p->stream = main_stream;
     {
         StageTimer tm(p, BSPLINE_STAGE_GATHER);
         rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
@@ -470,14 +484,23 @@ size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P) {
     return carve<float>(&w, nullptr, NB, P);
 }
 
-int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
-                  int flags) {
+int launch_interp_split(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u,
+                        void* out_grad, int flags, cudaStream_t sort_stream, cudaEvent_t sorted) {
     switch (p->dtype) {
-        case BSPLINE_F64: return run_interp<double, double, double>(p, coeffs, x, P, out_u, out_grad, flags);
-        case BSPLINE_F32: return run_interp<float, float, float>(p, coeffs, x, P, out_u, out_grad, flags);
-        case BSPLINE_BF16: return run_interp<__nv_bfloat16, float, float>(p, coeffs, x, P, out_u, out_grad, flags);
+        case BSPLINE_F64:
+            return run_interp<double, double, double>(p, coeffs, x, P, out_u, out_grad, flags, sort_stream, sorted);
+        case BSPLINE_F32:
+            return run_interp<float, float, float>(p, coeffs, x, P, out_u, out_grad, flags, sort_stream, sorted);
+        case BSPLINE_BF16:
+            return run_interp<__nv_bfloat16, float, float>(p, coeffs, x, P, out_u, out_grad, flags, sort_stream,
+                                                           sorted);
     }
     return BSPLINE_ERR_INVALID_ARG;
+}
+
+int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
+                  int flags) {
+    return launch_interp_split(p, coeffs, x, P, out_u, out_grad, flags, nullptr, nullptr);
 }
 
 }  // namespace bs
