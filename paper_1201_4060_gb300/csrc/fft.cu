@@ -77,14 +77,16 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
 }
 
 template <typename OutT, typename V> __device__ __forceinline__ void store_pair(OutT* p, V z);
+// Coefficient stores stream past L2 (evict first): the ring of plane buffers is what should stay there.
 template <> __device__ __forceinline__ void store_pair<double, double2>(double* p, double2 z) {
-    *reinterpret_cast<double2*>(p) = z;
+    __stcs(reinterpret_cast<double2*>(p), z);
 }
 template <> __device__ __forceinline__ void store_pair<float, float2>(float* p, float2 z) {
-    *reinterpret_cast<float2*>(p) = z;
+    __stcs(reinterpret_cast<float2*>(p), z);
 }
 template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__nv_bfloat16* p, float2 z) {
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(z.x, z.y);
+    const __nv_bfloat162 v = __floats2bfloat162_rn(z.x, z.y);
+    __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&v));
 }
 
 // ---------------------------------------------------------------- passes Y + Z fused
@@ -247,7 +249,9 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             const int valid = std::min(NLY, H - kz0);
             const V* src = w + pl * N * HP + kz0;
             V* dst = slot + kz0;
-            auto ld = [&](int q, int b) -> V { return (b < valid) ? src[(long long)q * HP + b] : mk<V>(R(0), R(0)); };
+            auto ld = [&](int q, int b) -> V {
+                return (b < valid) ? __ldcs(&src[(long long)q * HP + b]) : mk<V>(R(0), R(0));
+            };
             auto st = [&](int q, int b, V v) {
                 if (b < valid) dst[(long long)q * HP + b] = v;
             };
