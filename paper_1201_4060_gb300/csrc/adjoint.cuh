@@ -82,26 +82,28 @@ __device__ __forceinline__ bool item_range(const Ws<TR>& w, unsigned NB, unsigne
     return *beg < *end;
 }
 
-template <int ORD, typename A> constexpr int acc_edge() { return brick_edge(sizeof(A) == 8 ? BSPLINE_F64 : BSPLINE_F32) + ORD - 1; }
-
+// Accumulation tile of the spread: the brick plus halo, [c][x][y][z], unpadded.
 template <int ORD, typename A> constexpr size_t acc_bytes() {
-    return sizeof(A) * 3 * (size_t)acc_edge<ORD, A>() * acc_edge<ORD, A>() * acc_edge<ORD, A>();
+    using S = Shape<A, ORD>;
+    return sizeof(A) * 3 * (size_t)S::EX * S::EY * S::EZ;
 }
 
 // One CTA per work item: spread its particles' cotangents into a shared tile,
 // then add the tile to g_coef.
 template <int ORD, typename TR, typename A, bool GRAD>
 __global__ void __launch_bounds__(kAdjThreads)
-spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, const A* __restrict__ g_grad,
+spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A* __restrict__ g_grad,
               A* __restrict__ g_coef, A dscale) {
-    constexpr int B = brick_edge(sizeof(A) == 8 ? BSPLINE_F64 : BSPLINE_F32);
-    constexpr int E = acc_edge<ORD, A>();
-    constexpr int E3 = E * E * E;
+    using S = Shape<A, ORD>;
+    constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ, BZ = S::BZ;
+    constexpr int E3 = EX * EY * EZ;                    // one component
+    const unsigned NB = bg.NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A* acc = reinterpret_cast<A*>(smem_raw);
     unsigned brick, beg, end;
     if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
-    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
+    int x0, y0, z0;
+    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
     __shared__ unsigned s_bucket[32];
     __shared__ unsigned short s_order[kChunk];
     const unsigned n = end - beg;
@@ -122,7 +124,7 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
                 const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(cp & 1023u) - z0;
-                const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
+                const unsigned r = (unsigned)((ox * EY + oy) * EZ + oz) & 31u;
                 packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
             }
         }
@@ -154,7 +156,7 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
         bspline_weights<ORD, A>((A)rc.t[0], wx, dwx);
         bspline_weights<ORD, A>((A)rc.t[1], wy, dwy);
         bspline_weights<ORD, A>((A)rc.t[2], wz, dwz);
-        A* base = acc + (ox * E + oy) * E + oz;
+        A* base = acc + (ox * EY + oy) * EZ + oz;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const A gu = g_u ? g_u[3 * idx + c] : A(0);
@@ -173,7 +175,7 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
                 for (int jy = 0; jy < ORD; ++jy) {
                     const A p0 = GRAD ? fma(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
                     const A p1 = q2 * wy[jy];
-                    A* line = tc + (jx * E + jy) * E;
+                    A* line = tc + (jx * EY + jy) * EZ;
 #pragma unroll
                     for (int jz = 0; jz < ORD; ++jz) {
                         const A v = GRAD ? fma(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz];
@@ -187,19 +189,19 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
     if constexpr (sizeof(A) == 4) {
         // per tile row: the brick's B nodes as B/4 aligned 16-byte vector atomics
         // (z0 and N are multiples of 4, so 4 consecutive z stay inside one period),
-        // then the E - B halo nodes one by one
-        constexpr int U = B / 4 + (E - B);
-        for (int e = threadIdx.x; e < 3 * E * E * U; e += kAdjThreads) {
+        // then the EZ - BZ halo nodes one by one
+        constexpr int U = BZ / 4 + (EZ - BZ);
+        for (int e = threadIdx.x; e < 3 * EX * EY * U; e += kAdjThreads) {
             const int row = e / U, k = e - row * U;
-            const int c = row / (E * E), ix = (row / E) % E, iy = row % E;
-            const A* src = acc + (size_t)row * E;
+            const int c = row / (EX * EY), ix = (row / EY) % EX, iy = row % EY;
+            const A* src = acc + (size_t)row * EZ;
             A* dst = g_coef + (((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N;
-            if (k < B / 4) {
+            if (k < BZ / 4) {
                 const float4 v = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
                 if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
                     atomicAdd(reinterpret_cast<float4*>(dst + wrap_index(z0 + 4 * k, N)), v);
             } else {
-                const int iz = B + (k - B / 4);
+                const int iz = BZ + (k - BZ / 4);
                 const A v = src[iz];
                 if (v != A(0)) atomicAdd(dst + wrap_index(z0 + iz, N), v);
             }
@@ -209,7 +211,7 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
             const A v = acc[e];
             if (v != A(0)) {
                 const int c = e / E3, r = e - c * E3;
-                const int ix = r / (E * E), iy = (r / E) % E, iz = r % E;
+                const int ix = r / (EY * EZ), iy = (r / EZ) % EY, iz = r % EZ;
                 atomicAdd(&g_coef[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N +
                                   wrap_index(z0 + iz, N)],
                           v);
@@ -222,19 +224,19 @@ spread_kernel(int N, int nbx, unsigned NB, Ws<TR> w, const A* __restrict__ g_u, 
 // staged as in the forward evaluation.
 template <int ORD, typename CT, typename TR, bool HESS>
 __global__ void __launch_bounds__(kAdjThreads)
-gx_kernel(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w,
+gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
           const typename TileT<CT>::T* __restrict__ g_u, const typename TileT<CT>::T* __restrict__ g_grad,
           double* __restrict__ g_x, typename TileT<CT>::T dscale) {
     using A = typename TileT<CT>::T;
-    constexpr int B = brick_edge(sizeof(CT) == 8 ? BSPLINE_F64 : BSPLINE_F32);
-    constexpr int E = tile_edge<ORD, CT>();
-    constexpr int E3 = E * E * E;
+    using S = Shape<CT, ORD>;
+    const unsigned NB = bg.NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A* tile = reinterpret_cast<A*>(smem_raw);
     unsigned brick, beg, end;
     if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
-    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
-    stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
+    int x0, y0, z0;
+    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
+    stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
     cp_async_wait_all();
     __syncthreads();
     const A s2 = dscale * dscale;
@@ -248,11 +250,11 @@ gx_kernel(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w,
         bspline_weights2<ORD, A>((A)rc.t[0], wx, dwx, d2wx);
         bspline_weights2<ORD, A>((A)rc.t[1], wy, dwy, d2wy);
         bspline_weights2<ORD, A>((A)rc.t[2], wz, dwz, d2wz);
-        const A* base = tile + (ox * E + oy) * E + oz;
+        const A* base = tile + ox * S::SX + oy * S::SY + oz;
         A gx = A(0), gy = A(0), gz = A(0);
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
-            const A* tc = base + c * E3;
+            const A* tc = base + c * S::TS;
             // T_abc = sum over the stencil of a * w^(a)_x w^(b)_y w^(c)_z
             A t100 = 0, t010 = 0, t001 = 0, t200 = 0, t020 = 0, t002 = 0, t110 = 0, t101 = 0, t011 = 0;
 #pragma unroll
@@ -260,7 +262,7 @@ gx_kernel(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w,
                 A y00 = 0, y10 = 0, y01 = 0, y20 = 0, y02 = 0, y11 = 0;
 #pragma unroll
                 for (int jy = 0; jy < ORD; ++jy) {
-                    const A* line = tc + (jx * E + jy) * E;
+                    const A* line = tc + jx * S::SX + jy * S::SY;
                     A z0v = 0, z1v = 0, z2v = 0;
 #pragma unroll
                     for (int jz = 0; jz < ORD; ++jz) {
@@ -312,7 +314,7 @@ gx_kernel(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w,
 // Launch the spread (g_coef != nullptr) and the position gradient (g_x != nullptr)
 // for one order and coefficient type.  items = upper bound of work items.
 template <int ORD, typename CT, typename TR>
-int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, long long items,
+int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, long long items,
                 const void* g_u, const void* g_grad, void* g_coef, double* g_x) {
     using A = typename TileT<CT>::T;
     const A dscale = (A)((double)p->N / p->L);
@@ -321,14 +323,14 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, in
         const size_t sm = acc_bytes<ORD, A>();
         auto k = g_grad ? spread_kernel<ORD, TR, A, true> : spread_kernel<ORD, TR, A, false>;
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, nbx, NB, w, (const A*)g_u, (const A*)g_grad,
+        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, g, w, (const A*)g_u, (const A*)g_grad,
                                                             (A*)g_coef, dscale);
     }
     if (g_x) {
         const size_t sm = tile_bytes<ORD, CT>();
         auto k = g_grad ? gx_kernel<ORD, CT, TR, true> : gx_kernel<ORD, CT, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>((const CT*)coeffs, p->N, nbx, NB, w, (const A*)g_u,
+        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>((const CT*)coeffs, p->N, g, w, (const A*)g_u,
                                                             (const A*)g_grad, g_x, dscale);
     }
     return BSPLINE_OK;
@@ -338,11 +340,11 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, in
 
 #define BS_ADJOINT_EXTERN(ORD, CT, TR)                                                                          \
     extern template int adjoint_impl::run_adjoint<ORD, CT, TR>(bspline_plan_s*, const void*,                   \
-                                                                gather_impl::Ws<TR>, unsigned, int, long long,   \
+                                                                gather_impl::Ws<TR>, BrickGrid, long long,       \
                                                                 const void*, const void*, void*, double*);
 #define BS_ADJOINT_INSTANTIATE(ORD, CT, TR)                                                                     \
     template int adjoint_impl::run_adjoint<ORD, CT, TR>(bspline_plan_s*, const void*, gather_impl::Ws<TR>,      \
-                                                         unsigned, int, long long, const void*, const void*,    \
+                                                         BrickGrid, long long, const void*, const void*,        \
                                                          void*, double*);
 
 }  // namespace bs

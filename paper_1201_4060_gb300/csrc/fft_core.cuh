@@ -277,7 +277,7 @@ __device__ __forceinline__ void load_tile(V* s, const V* __restrict__ src, long 
 }
 
 template <typename K> int set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) {
+    if (bytes > 32 * 1024) {           // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return set_cuda_error(e);
     }

@@ -12,13 +12,34 @@
 
 namespace bs {
 
-// Cells per brick edge: particles are binned by the brick that holds the first
-// node of their stencil, and one CTA stages one brick (plus the order-1 halo)
-// of coefficients in shared memory.  16^3 bricks for FP32/BF16 (enough
-// particles per brick to assemble bank-conflict-free warps, and a 21^3 x 3
-// FP32 tile at order 6 still fits two CTAs per SM); 8^3 for FP64.
-constexpr int brick_edge(int dtype) { return dtype == BSPLINE_F64 ? 8 : 16; }
-inline int bricks_per_axis(int N, int dtype) { return N >= brick_edge(dtype) ? N / brick_edge(dtype) : 1; }
+// Bricks of the particle sort: particles are binned by the brick that holds
+// the first node of their stencil, and one CTA stages one brick (plus the
+// order-1 halo) of coefficients in shared memory.  FP64: 8^3 cells.
+// FP32/BF16: 16 x BY x 16 cells with BY = 12 up to order 6 and 8 above, so
+// that the FP32 tile, its z rows padded to a multiple of 16 bytes for 16-byte
+// copies, still fits two CTAs per SM (order 6: 3 x 21 x 17 x 24 floats).
+constexpr int brick_x(int dtype) { return dtype == BSPLINE_F64 ? 8 : 16; }
+constexpr int brick_y(int dtype, int order) { return dtype == BSPLINE_F64 ? 8 : (order <= 6 ? 12 : 8); }
+constexpr int brick_z(int dtype) { return brick_x(dtype); }
+
+// Bricks per axis (partial bricks at the high end count) and their total.
+struct BrickGrid {
+    int nbx, nby, nbz;
+    int by;            // brick edge along y (x and z: brick_x)
+    int bshift;        // log2 of the x and z edge
+    unsigned NB;
+};
+inline BrickGrid brick_grid(int N, int dtype, int order) {
+    BrickGrid g;
+    const int bx = brick_x(dtype), by = brick_y(dtype, order);
+    g.nbx = (N + bx - 1) / bx;
+    g.nby = (N + by - 1) / by;
+    g.nbz = g.nbx;
+    g.by = by;
+    g.bshift = bx == 16 ? 4 : 3;
+    g.NB = (unsigned)g.nbx * g.nby * g.nbz;
+    return g;
+}
 
 // Grid sizes with compiled transforms: powers of two 8..1024, and 3 * 2^k
 // from 48 to 768 (radix-3 stage; multiples of the 16-cell brick).

@@ -94,7 +94,8 @@ __device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
 // for a non-finite position or one with no fractional bits left.
 template <typename TR>
 __device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
-                                                    int order, int nbx, int bshift, unsigned NB, Rec<TR>* r) {
+                                                    int order, const BrickGrid& g, Rec<TR>* r) {
+    const unsigned NB = g.NB;
     unsigned anc[3];
     TR tt[3];
     bool ok = true;
@@ -126,7 +127,7 @@ __device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x
     r->t[0] = tt[0];
     r->t[1] = tt[1];
     r->t[2] = tt[2];
-    return ((anc[0] >> bshift) * nbx + (anc[1] >> bshift)) * nbx + (anc[2] >> bshift);
+    return ((anc[0] >> g.bshift) * (unsigned)g.nby + anc[1] / (unsigned)g.by) * (unsigned)g.nbz + (anc[2] >> g.bshift);
 }
 
 // Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
@@ -153,8 +154,8 @@ __device__ __forceinline__ unsigned warp_increment(unsigned* counter, unsigned k
 // lanes can aggregate their increments (aggregate = few bricks).
 template <typename TR>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
-                           int nbx, int bshift, unsigned NB, Ws<TR> w, unsigned long long* __restrict__ status,
-                           int aggregate) {
+                           BrickGrid g, Ws<TR> w, unsigned long long* __restrict__ status, int aggregate) {
+    const unsigned NB = g.NB;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long lane = threadIdx.x & 31;
     for (long long pw = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; pw < P; pw += stride) {
@@ -163,7 +164,7 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
         unsigned k = 0;
         if (valid) {
             Rec<TR> r;
-            k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
+            k = locate_particle<TR>(x, p, N, scale, order, g, &r);
             if (k == NB) atomicAdd(status, 1ULL);
         }
         if (aggregate) {
@@ -246,16 +247,17 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
 // records) and write each record and its original index to the next free slot
 // of its brick.  Invalid positions get NaN outputs.
 template <typename TR, typename OT>
-__global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order, int nbx,
-                               int bshift, unsigned NB, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
+__global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
+                               BrickGrid g, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
                                int aggregate) {
+    const unsigned NB = g.NB;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long lane = threadIdx.x & 31;
     for (long long pw = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; pw < P; pw += stride) {
         const long long p = pw + lane;
         Rec<TR> r;
         unsigned k = NB;
-        if (p < P) k = locate_particle<TR>(x, p, N, scale, order, nbx, bshift, NB, &r);
+        if (p < P) k = locate_particle<TR>(x, p, N, scale, order, g, &r);
         if (p < P && k >= NB) {
             const OT nan = (OT)NAN;
             if (out_u) {
@@ -283,16 +285,16 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
 }
 
 template <typename CT, typename AT, typename TR>
-int dispatch_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, void* out_u,
+int dispatch_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u,
                    void* out_grad, bool grad) {
     switch (p->order) {
-        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
-        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
-        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
-        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
-        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
-        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
-        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     }
     return BSPLINE_ERR_UNSUPPORTED_ORDER;
 }
@@ -308,9 +310,8 @@ inline unsigned grid_for(long long P, int threads) {
 template <typename CT, typename AT, typename TR>
 int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u, void* out_grad,
                int flags, cudaStream_t sort_stream, cudaEvent_t sorted) {
-    const int nbx = bricks_per_axis(p->N, p->dtype);
-    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
-    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    const BrickGrid g = brick_grid(p->N, p->dtype, p->order);
+    const unsigned NB = g.NB;
     Ws<TR> w;
     const size_t need = carve<TR>(&w, nullptr, NB, P);
     int rc = p->pws.grow(need);
@@ -330,8 +331,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                         bshift, NB, w, p->d_status, NB < kAggregateBricks);
+        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -339,8 +339,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                                 bshift, NB, w, (AT*)out_u,
+        scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u,
                                                                  grad ? (AT*)out_grad : nullptr, NB < kAggregateBricks);
     }
     if (sort_stream) {
@@ -350,7 +349,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     p->stream = main_stream;
     {
         StageTimer tm(p, BSPLINE_STAGE_GATHER);
-        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     }
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
@@ -361,9 +360,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
 template <typename CT, typename AT, typename TR>
 int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs, const double* x,
                   int64_t P, void* out_u, void* out_grad, int flags) {
-    const int nbx = bricks_per_axis(p->N, p->dtype);
-    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
-    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    const BrickGrid g = brick_grid(p->N, p->dtype, p->order);
+    const unsigned NB = g.NB;
     Ws<TR> w;
     carve<TR>(&w, ws, NB, P);
     cudaStream_t st = p->stream;
@@ -371,29 +369,27 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
-    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                     bshift, NB, w, status, NB < kAggregateBricks);
+    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status, NB < kAggregateBricks);
     scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
-    scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx, bshift,
-                                                             NB, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
+    scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
                                                              NB < kAggregateBricks);
-    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, NB, nbx, out_u, out_grad, grad);
+    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
 }
 
 template <typename CT, typename TR>
-int adjoint_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, long long items,
+int adjoint_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, long long items,
                   const void* g_u, const void* g_grad, void* g_coef, double* g_x) {
     using adjoint_impl::run_adjoint;
     switch (p->order) {
-        case 2: return run_adjoint<2, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
-        case 3: return run_adjoint<3, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
-        case 4: return run_adjoint<4, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
-        case 5: return run_adjoint<5, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
-        case 6: return run_adjoint<6, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
-        case 7: return run_adjoint<7, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
-        case 8: return run_adjoint<8, CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, g_x);
+        case 2: return run_adjoint<2, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 3: return run_adjoint<3, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 4: return run_adjoint<4, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 5: return run_adjoint<5, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 6: return run_adjoint<6, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 7: return run_adjoint<7, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 8: return run_adjoint<8, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
     }
     return BSPLINE_ERR_UNSUPPORTED_ORDER;
 }
@@ -404,9 +400,8 @@ int adjoint_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, 
 template <typename CT, typename TR>
 int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, const void* g_u,
                           const void* g_grad, void* g_coef, double* g_x) {
-    const int nbx = bricks_per_axis(p->N, p->dtype);
-    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
-    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    const BrickGrid g = brick_grid(p->N, p->dtype, p->order);
+    const unsigned NB = g.NB;
     Ws<TR> w;
     const size_t need = carve<TR>(&w, nullptr, NB, P);
     int rc = p->pws.grow(need);
@@ -418,8 +413,7 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                         bshift, NB, w, p->d_status, NB < kAggregateBricks);
+        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -427,18 +421,17 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, nbx,
-                                                                     bshift, NB, w, g_x, nullptr, NB < kAggregateBricks);
+        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, g_x, nullptr, NB < kAggregateBricks);
     }
     const long long items = (long long)NB + (P + kChunk - 1) / kChunk;
     if (g_coef) {
         StageTimer tm(p, BSPLINE_STAGE_SPREAD);
-        rc = adjoint_order<CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, g_coef, nullptr);
+        rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, nullptr);
         if (rc) return rc;
     }
     if (g_x) {
         StageTimer tm(p, BSPLINE_STAGE_GRAD_X);
-        rc = adjoint_order<CT, TR>(p, coeffs, w, NB, nbx, items, g_u, g_grad, nullptr, g_x);
+        rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, nullptr, g_x);
         if (rc) return rc;
     }
     return set_cuda_error(cudaGetLastError());
@@ -473,9 +466,8 @@ int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, co
 }
 
 size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P) {
-    const int nbx = bricks_per_axis(p->N, p->dtype);
-    const int bshift = brick_edge(p->dtype) == 16 ? 4 : 3;
-    const unsigned NB = (unsigned)nbx * nbx * nbx;
+    const BrickGrid g = brick_grid(p->N, p->dtype, p->order);
+    const unsigned NB = g.NB;
     if (p->dtype == BSPLINE_F64) {
         Ws<double> w;
         return carve<double>(&w, nullptr, NB, P);

@@ -89,20 +89,39 @@ __device__ __forceinline__ void bspline_weights(A t, A (&w)[n], A (&dw)[n]) {
 }
 
 // ------------------------------------------------------------------ gather
-// Coefficient tile of one brick: (BRICK + ORD - 1)^3 nodes per component,
-// [c][x][y][z] with z fastest, periodic wrap of the grid indices on staging.
-// FP32 and BF16 coefficients are staged as FP32 (BF16 widened on load).
+// Coefficient tile of one brick: (BX + ORD - 1) x (BY + ORD - 1) x (BZ + ORD - 1)
+// nodes per component, [c][x][y][z] with z fastest and z rows of PZ entries
+// (FP32/BF16: padded to a multiple of 4 so every row starts 16-byte
+// aligned), periodic wrap of the grid indices on staging.  FP32 and BF16
+// coefficients are staged as FP32 (BF16 widened on load).
 template <typename CT> struct TileT { using T = float; };
 template <> struct TileT<double> { using T = double; };
 
 template <typename CT> __device__ __forceinline__ typename TileT<CT>::T widen(CT v) { return v; }
 template <> __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <int ORD, typename CT> constexpr int tile_edge() { return brick_edge(sizeof(CT) == 8 ? BSPLINE_F64 : BSPLINE_F32) + ORD - 1; }
+template <typename CT, int ORD> struct Shape {
+    static constexpr bool F64 = sizeof(CT) == 8;
+    static constexpr int BX = brick_x(F64 ? BSPLINE_F64 : BSPLINE_F32);
+    static constexpr int BY = brick_y(F64 ? BSPLINE_F64 : BSPLINE_F32, ORD);
+    static constexpr int BZ = BX;
+    static constexpr int EX = BX + ORD - 1, EY = BY + ORD - 1, EZ = BZ + ORD - 1;
+    static constexpr int PZ = F64 ? EZ : ((EZ + 3) & ~3);
+    static constexpr int SY = PZ, SX = EY * PZ, TS = EX * EY * PZ;   // strides of y, x and the component
+};
 
 template <int ORD, typename CT>
 constexpr size_t tile_bytes() {
-    return sizeof(typename TileT<CT>::T) * 3 * (size_t)tile_edge<ORD, CT>() * tile_edge<ORD, CT>() * tile_edge<ORD, CT>();
+    return sizeof(typename TileT<CT>::T) * 3 * (size_t)Shape<CT, ORD>::TS;
+}
+
+// Brick index -> first cell of the brick.
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ void brick_origin(unsigned brick, const BrickGrid& g, int* x0, int* y0, int* z0) {
+    const unsigned bz = brick % (unsigned)g.nbz, t = brick / (unsigned)g.nbz;
+    *z0 = (int)bz * BZ;
+    *y0 = (int)(t % (unsigned)g.nby) * BY;
+    *x0 = (int)(t / (unsigned)g.nby) * BX;
 }
 
 constexpr int kGatherThreads = 384;
@@ -117,71 +136,117 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
                  "l"(src)
                  : "memory");
 }
+// 16 bytes, cached in L2 only (each tile is read once per work item).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Copy the brick's tile into shared memory, one z-row of E nodes per warp
-// step: lane = z offset (lanes >= E idle), so each step reads E consecutive
-// coefficients and writes E consecutive tile entries.  Rows are walked in
-// (c, ix, iy) order with incremental global addresses; indices wrap
-// periodically.  Same-type coefficients go through cp.async (no register
+// Copy the brick's tile into shared memory, one z-row per warp step: lane =
+// z offset (lanes >= EZ idle).  Rows are walked in (c, ix, iy) order; indices
+// wrap periodically.  Same-type coefficients go through cp.async (no register
 // round trip); BF16 is widened to FP32 through registers.  The caller
 // synchronises the CTA after cp_async_wait_all.
 template <int ORD, typename CT>
 __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                            int y0, int z0) {
     using TT = typename TileT<CT>::T;
-    constexpr int E = tile_edge<ORD, CT>();
-    static_assert(E <= 32, "one z-row per warp step");
+    using S = Shape<CT, ORD>;
+    static_assert(S::EZ <= 32, "one z-row per warp step");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane >= E) return;
+    if (lane >= S::EZ) return;
     const int gz = wrap_index(z0 + lane, N);
-    // planes (c, ix): E * 3 of them, each E rows along y; warps take planes round-robin
-    for (int pl = warp; pl < 3 * E; pl += nw) {
-        const int c = pl / E, ix = pl - c * E;
+    // planes (c, ix): 3 EX of them, each EY rows along y; warps take planes round-robin
+    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
+        const int c = pl / S::EX, ix = pl - c * S::EX;
         const CT* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N + gz;
-        TT* dst = tile + (size_t)pl * E * E + lane;
+        TT* dst = tile + (size_t)pl * S::SX + lane;
         auto copy = [&](int iy, const CT* s) {
             if constexpr (sizeof(CT) == sizeof(TT)) {
-                if constexpr (sizeof(CT) == 4) cp_async4(dst + iy * E, s);
-                else cp_async8(dst + iy * E, s);
+                if constexpr (sizeof(CT) == 4) cp_async4(dst + iy * S::SY, s);
+                else cp_async8(dst + iy * S::SY, s);
             } else {
-                dst[iy * E] = widen<CT>(*s);
+                dst[iy * S::SY] = widen<CT>(*s);
             }
         };
-        if (N >= E) {
+        if (N >= S::EY) {
             // rows y0.. up to the end of the period advance by N; the rest wrap to row 0
-            const int nrun = min(E, N - y0);
+            const int nrun = min(S::EY, N - y0);
             const CT* s = plane + (size_t)y0 * N;
 #pragma unroll 7
             for (int iy = 0; iy < nrun; ++iy, s += N) copy(iy, s);
             s = plane;
-            for (int iy = nrun; iy < E; ++iy, s += N) copy(iy, s);
+            for (int iy = nrun; iy < S::EY; ++iy, s += N) copy(iy, s);
         } else {
-            for (int iy = 0; iy < E; ++iy) copy(iy, plane + (size_t)wrap_index(y0 + iy, N) * N);
+            for (int iy = 0; iy < S::EY; ++iy) copy(iy, plane + (size_t)wrap_index(y0 + iy, N) * N);
         }
     }
 }
 
+// FP32 tiles with 16-byte copies: a tile row is PZ / 4 chunks of 4
+// coefficients, 16-byte aligned in both memories (z0 and N are multiples of
+// 4, so a chunk never straddles the periodic wrap).  Within a (c, ix) plane
+// the lane -> (row, chunk) assignment and its offsets are the same for every
+// plane, so they are computed once.
+template <int ORD>
+__device__ __forceinline__ void stage_tile16(float* tile, const float* __restrict__ coef, int N, int x0, int y0,
+                                             int z0) {
+    using S = Shape<float, ORD>;
+    constexpr int CH = S::PZ / 4;                     // chunks per row
+    constexpr int PER = S::EY * CH;                   // chunks per plane
+    constexpr int NI = (PER + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int goff[NI], soff[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int f = lane + 32 * i;
+        const int iy = f / CH, ch = f - iy * CH;
+        goff[i] = f < PER ? wrap_index(y0 + iy, N) * N + wrap_index(z0 + 4 * ch, N) : -1;
+        soff[i] = iy * S::SY + 4 * ch;
+    }
+    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
+        const int c = pl / S::EX, ix = pl - c * S::EX;
+        const float* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
+        float* dst = tile + (size_t)pl * S::SX;
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+            if (goff[i] >= 0) cp_async16(dst + soff[i], plane + goff[i]);
+    }
+}
+
+template <int ORD, typename CT>
+__device__ __forceinline__ void stage_brick(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
+                                            int y0, int z0) {
+    if constexpr (sizeof(CT) == 4) {
+        if (N >= 16) {
+            stage_tile16<ORD>(tile, coef, N, x0, y0, z0);
+            return;
+        }
+    }
+    stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
+}
+
 // u and grad u of one particle from the staged tile (Table 1 contraction,
 // z axis first).  base points at the particle's first stencil node.
-template <int ORD, typename A, bool GRAD, int E>
+template <int ORD, typename A, bool GRAD, int SX, int SY, int TS>
 __device__ __forceinline__ void eval_particle(const A* __restrict__ base, A tx, A ty, A tz, A dscale,
                                               A* __restrict__ out_u, A* __restrict__ out_grad) {
-    constexpr int E3 = E * E * E;
     A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
     bspline_weights<ORD, A>(tx, wx, dwx);
     bspline_weights<ORD, A>(ty, wy, dwy);
     bspline_weights<ORD, A>(tz, wz, dwz);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const A* tc = base + c * E3;
+        const A* tc = base + c * TS;
         A u = 0, gx = 0, gy = 0, gz = 0;
 #pragma unroll
         for (int jx = 0; jx < ORD; ++jx) {
             A y00 = 0, y10 = 0, y01 = 0;
 #pragma unroll
             for (int jy = 0; jy < ORD; ++jy) {
-                const A* line = tc + (jx * E + jy) * E;
+                const A* line = tc + jx * SX + jy * SY;
                 A z0v = 0, z1v = 0;
 #pragma unroll
                 for (int jz = 0; jz < ORD; ++jz) {
@@ -216,11 +281,10 @@ __device__ __forceinline__ void eval_particle(const A* __restrict__ base, A tx, 
 // form the pair, the z weight is duplicated), and their y-sums are kept as
 // (even, odd) pairs that are added at the end of each x-plane.  Same
 // arithmetic per term as eval_particle; the sums are grouped by parity of jy.
-template <int ORD, bool GRAD, int E>
+template <int ORD, bool GRAD, int SX, int SY, int TS>
 __device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base, float tx, float ty, float tz,
                                                  float dscale, float* __restrict__ out_u,
                                                  float* __restrict__ out_grad) {
-    constexpr int E3 = E * E * E;
     constexpr int NP = ORD / 2;                       // pairs of y-lines
     float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
     bspline_weights<ORD, float>(tx, wx, dwx);
@@ -239,15 +303,15 @@ __device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base,
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float* tc = base + c * E3;
+        const float* tc = base + c * TS;
         float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
         for (int jx = 0; jx < ORD; ++jx) {
             float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                const float* l0 = tc + (jx * E + 2 * p) * E;
-                const float* l1 = l0 + E;
+                const float* l0 = tc + jx * SX + 2 * p * SY;
+                const float* l1 = l0 + SY;
                 float2 z0 = make_float2(0.f, 0.f), z1 = z0;
 #pragma unroll
                 for (int jz = 0; jz < ORD; ++jz) {
@@ -262,7 +326,7 @@ __device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base,
                 }
             }
             if constexpr (ORD % 2 == 1) {               // the unpaired last line
-                const float* l = tc + (jx * E + ORD - 1) * E;
+                const float* l = tc + jx * SX + (ORD - 1) * SY;
                 float z0 = 0.f, z1 = 0.f;
 #pragma unroll
                 for (int jz = 0; jz < ORD; ++jz) {
@@ -298,7 +362,7 @@ __device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base,
 // are kept as (even, odd) pairs that are added at the end of each x-plane.
 // Same arithmetic per term as eval_particle; the sums are grouped by parity
 // of jy.  base points at the component's first stencil node.
-template <int ORD, bool GRAD, int E>
+template <int ORD, bool GRAD, int SX, int SY>
 __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base, float tx, float ty, float tz,
                                                   float dscale, float* __restrict__ out_u,
                                                   float* __restrict__ out_grad) {
@@ -324,8 +388,8 @@ __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base
         float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-            const float* l0 = base + (jx * E + 2 * p) * E;
-            const float* l1 = l0 + E;
+            const float* l0 = base + jx * SX + 2 * p * SY;
+            const float* l1 = l0 + SY;
             float2 z0 = make_float2(0.f, 0.f), z1 = z0;
 #pragma unroll
             for (int jz = 0; jz < ORD; ++jz) {
@@ -340,7 +404,7 @@ __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base
             }
         }
         if constexpr (ORD % 2 == 1) {               // the unpaired last line
-            const float* l = base + (jx * E + ORD - 1) * E;
+            const float* l = base + jx * SX + (ORD - 1) * SY;
             float z0 = 0.f, z1 = 0.f;
 #pragma unroll
             for (int jz = 0; jz < ORD; ++jz) {
@@ -372,17 +436,17 @@ __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base
 // FP64: one thread per particle (the FP64 pipe, not shared memory, bounds it).
 template <int ORD, typename TR, bool GRAD>
 __global__ void __launch_bounds__(128)
-gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __restrict__ out_u,
+gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, double* __restrict__ out_u,
            double* __restrict__ out_grad, double dscale) {
-    constexpr int B = brick_edge(BSPLINE_F64);
-    constexpr int E = tile_edge<ORD, double>();
+    using S = Shape<double, ORD>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* tile = reinterpret_cast<double*>(smem_raw);
     const unsigned brick = blockIdx.x;
     const unsigned beg = w.offset[brick], end = w.offset[brick + 1];
     if (beg == end) return;
-    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
-    stage_tile<ORD, double>(tile, coef, N, x0, y0, z0);
+    int x0, y0, z0;
+    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
+    stage_brick<ORD, double>(tile, coef, N, x0, y0, z0);
     cp_async_wait_all();
     __syncthreads();
     for (unsigned i = beg + threadIdx.x; i < end; i += blockDim.x) {
@@ -391,14 +455,14 @@ gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
         const unsigned idx = w.s_idx[i];
-        double u[3], g[9];
-        eval_particle<ORD, double, GRAD, E>(tile + (ox * E + oy) * E + oz, (double)rc.t[0], (double)rc.t[1],
-                                             (double)rc.t[2], dscale, u, g);
+        double u[3], gr[9];
+        eval_particle<ORD, double, GRAD, S::SX, S::SY, S::TS>(tile + ox * S::SX + oy * S::SY + oz, (double)rc.t[0],
+                                                               (double)rc.t[1], (double)rc.t[2], dscale, u, gr);
 #pragma unroll
         for (int c = 0; c < 3; ++c) out_u[3 * (size_t)idx + c] = u[c];
         if (GRAD) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) out_grad[9 * (size_t)idx + k] = g[k];
+            for (int k = 0; k < 9; ++k) out_grad[9 * (size_t)idx + k] = gr[k];
         }
     }
 }
@@ -416,10 +480,10 @@ gather_f64(const double* __restrict__ coef, int N, int nbx, Ws<TR> w, double* __
 // upper bound on the number of items and surplus CTAs return at once.
 template <int ORD, typename CT, typename TR, bool GRAD>
 __global__ void __launch_bounds__(kGatherThreads)
-gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, float* __restrict__ out_u,
+gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __restrict__ out_u,
            float* __restrict__ out_grad, float dscale) {
-    constexpr int B = brick_edge(BSPLINE_F32);
-    constexpr int E = tile_edge<ORD, CT>();
+    using S = Shape<CT, ORD>;
+    const unsigned NB = bg.NB;
     constexpr int NW = kGatherThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* tile = reinterpret_cast<float*>(smem_raw);
@@ -430,8 +494,9 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
     const unsigned brick = w.item[item];
     const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * kChunk;
     const unsigned end = w.offset[brick + 1];
-    const int x0 = (brick / (nbx * nbx)) * B, y0 = ((brick / nbx) % nbx) * B, z0 = (brick % nbx) * B;
-    stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
+    int x0, y0, z0;
+    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
+    stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
         const int n = (int)min(kChunk, end - c0);
@@ -448,7 +513,7 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
                 const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(cp & 1023u) - z0;
-                const unsigned r = (unsigned)((ox * E + oy) * E + oz) & 31u;
+                const unsigned r = (unsigned)(ox * S::SX + oy * S::SY + oz) & 31u;
                 packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
             }
         }
@@ -529,8 +594,8 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(rc.cell & 1023u) - z0;
                 float u[3], g[9];
-                eval_particle_x2<ORD, GRAD, E>(tile + (ox * E + oy) * E + oz, (float)rc.t[0], (float)rc.t[1],
-                                                (float)rc.t[2], dscale, u, g);
+                eval_particle_x2<ORD, GRAD, S::SX, S::SY, S::TS>(tile + ox * S::SX + oy * S::SY + oz, (float)rc.t[0],
+                                                                  (float)rc.t[1], (float)rc.t[2], dscale, u, g);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) out_u[3 * (size_t)idx + c] = u[c];
                 if (GRAD) {
@@ -552,8 +617,9 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(rc.cell & 1023u) - z0;
                 float u, g[3];
-                eval_component_x2<ORD, GRAD, E>(tile + c * (E * E * E) + (ox * E + oy) * E + oz, (float)rc.t[0],
-                                                (float)rc.t[1], (float)rc.t[2], dscale, &u, g);
+                eval_component_x2<ORD, GRAD, S::SX, S::SY>(tile + c * S::TS + ox * S::SX + oy * S::SY + oz,
+                                                           (float)rc.t[0], (float)rc.t[1], (float)rc.t[2], dscale,
+                                                           &u, g);
                 out_u[3 * (size_t)idx + c] = u;
                 if (GRAD) {
 #pragma unroll
@@ -565,7 +631,7 @@ gather_f32(const CT* __restrict__ coef, int N, int nbx, unsigned NB, Ws<TR> w, f
 }
 
 template <typename K> int set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) {
+    if (bytes > 32 * 1024) {           // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
@@ -573,22 +639,23 @@ template <typename K> int set_smem(K kernel, size_t bytes) {
 }
 
 template <int ORD, typename CT, typename AT, typename TR>
-int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int nbx, void* out_u, void* out_grad,
+int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u, void* out_grad,
                bool grad) {
+    const unsigned NB = g.NB;
     const size_t sm = tile_bytes<ORD, CT>();
     const AT dscale = (AT)((double)p->N / p->L);
     int rc;
     if constexpr (sizeof(AT) == 8) {
         auto k = grad ? gather_f64<ORD, TR, true> : gather_f64<ORD, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const double*>(coeffs), p->N, nbx, w, (double*)out_u,
+        k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const double*>(coeffs), p->N, g, w, (double*)out_u,
                                       grad ? (double*)out_grad : nullptr, dscale);
     } else {
         auto k = grad ? gather_f32<ORD, CT, TR, true> : gather_f32<ORD, CT, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
         // work items: at most one partial chunk per brick plus P / kChunk full ones
         const long long items = (long long)NB + (w.P + kChunk - 1) / kChunk;
-        k<<<(unsigned)items, kGatherThreads, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, nbx, NB, w,
+        k<<<(unsigned)items, kGatherThreads, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, g, w,
                                                               (float*)out_u, grad ? (float*)out_grad : nullptr, dscale);
     }
     return BSPLINE_OK;
@@ -598,10 +665,10 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, unsigned NB, int
 
 #define BS_GATHER_EXTERN(ORD, CT, AT, TR)                                                                 \
     extern template int gather_impl::run_gather<ORD, CT, AT, TR>(bspline_plan_s*, const void*,               \
-                                                                  gather_impl::Ws<TR>, unsigned, int, void*, \
+                                                                  gather_impl::Ws<TR>, BrickGrid, void*,     \
                                                                   void*, bool);
 #define BS_GATHER_INSTANTIATE(ORD, CT, AT, TR)                                                          \
     template int gather_impl::run_gather<ORD, CT, AT, TR>(bspline_plan_s*, const void*, gather_impl::Ws<TR>, \
-                                                           unsigned, int, void*, void*, bool);
+                                                           BrickGrid, void*, void*, bool);
 
 }  // namespace bs
