@@ -328,6 +328,12 @@ def run_ours(args):
               "fma_per_particle_table1": from_table1, "fma_rate_tfma": fma_rate / 1e12,
               "fma_peak_tfma_at_max_clock": fma_peak / 1e12, "alu_frac_at_max_clock": fma_rate / fma_peak,
               "particles_per_s": P / (g_ms / 1e3),
+              # the bound that binds: shared-memory reads of the stencil (3 n^3 FP32 values per particle)
+              # against 128 bytes per clock per SM at the maximum clock
+              "smem_bytes_per_particle": 3 * order ** 3 * 4,
+              "smem_gbs": P * 3 * order ** 3 * 4 / (g_ms / 1e3) / 1e9,
+              "smem_peak_gbs_at_max_clock": sms * 128 * pk["sm_max_mhz"] * 1e6 / 1e9,
+              "smem_frac_at_max_clock": P * 3 * order ** 3 * 4 / (g_ms / 1e3) / (sms * 128 * pk["sm_max_mhz"] * 1e6),
               "traffic": measured_traffic("gather", "f32", N, order)}
     stages_ms = {s: {"total_ms": stages[s][0], "launches": stages[s][1],
                      "share": stages[s][0] / max(sum(v[0] for v in stages.values()), 1e-30)} for s in STAGES}
