@@ -216,12 +216,62 @@ __device__ __forceinline__ void stage_tile16(float* tile, const float* __restric
     }
 }
 
+// BF16 coefficients: 16-byte loads of 8 values (rows start at z0, a multiple
+// of 16, and N is a multiple of 8, so a chunk never straddles the wrap),
+// widened to FP32 in registers and stored as two 16-byte words.  All of a
+// lane's loads are issued before its stores.
+template <int ORD>
+__device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16* __restrict__ coef, int N, int x0,
+                                                int y0, int z0) {
+    using S = Shape<__nv_bfloat16, ORD>;
+    constexpr int CH = (S::PZ + 7) / 8;               // chunks of 8 per row (the last may overhang the pitch)
+    constexpr int PER = S::EY * CH;
+    constexpr int NI = (PER + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int goff[NI], soff[NI], nst[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int f = lane + 32 * i;
+        const int iy = f / CH, ch = f - iy * CH;
+        goff[i] = f < PER ? wrap_index(y0 + iy, N) * N + wrap_index(z0 + 8 * ch, N) : -1;
+        soff[i] = iy * S::SY + 8 * ch;
+        nst[i] = (S::PZ - 8 * ch) >= 8 ? 2 : 1;       // 16-byte stores that stay inside the row pitch
+    }
+    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
+        const int c = pl / S::EX, ix = pl - c * S::EX;
+        const __nv_bfloat16* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
+        float* dst = tile + (size_t)pl * S::SX;
+        uint4 v[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+            if (goff[i] >= 0) v[i] = __ldg(reinterpret_cast<const uint4*>(plane + goff[i]));
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            if (goff[i] < 0) continue;
+            const unsigned w4[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+            float f[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                f[2 * q] = __uint_as_float(w4[q] << 16);             // bf16 -> fp32: the high half of the word
+                f[2 * q + 1] = __uint_as_float(w4[q] & 0xffff0000u);
+            }
+            *reinterpret_cast<float4*>(dst + soff[i]) = make_float4(f[0], f[1], f[2], f[3]);
+            if (nst[i] == 2) *reinterpret_cast<float4*>(dst + soff[i] + 4) = make_float4(f[4], f[5], f[6], f[7]);
+        }
+    }
+}
+
 template <int ORD, typename CT>
 __device__ __forceinline__ void stage_brick(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                             int y0, int z0) {
     if constexpr (sizeof(CT) == 4) {
         if (N >= 16) {
             stage_tile16<ORD>(tile, coef, N, x0, y0, z0);
+            return;
+        }
+    } else if constexpr (sizeof(CT) == 2) {
+        if (N >= 16) {
+            stage_tile_bf16<ORD>(tile, coef, N, x0, y0, z0);
             return;
         }
     }
