@@ -255,6 +255,16 @@ def test_run_host_matches_device_path(B):
     go = torch.empty((4096, 3, 3), dtype=torch.float32).pin_memory()
     plan.run_host(uh, xh, uo, go)
     assert np.array_equal(uo.numpy(), u) and np.array_equal(go.numpy(), g)
+    # again on the same plan (buffers and the second stream are reused), u only, with a non-finite position
+    x2 = x.copy()
+    x2[7, 1] = np.nan
+    uo2 = torch.full((4096, 3), 5.0, dtype=torch.float32).pin_memory()
+    plan.run_host(uh, torch.from_numpy(x2).pin_memory(), uo2, None)
+    assert plan.status() == 1
+    ok = np.ones(4096, bool)
+    ok[7] = False
+    assert np.isnan(uo2.numpy()[7]).all()
+    assert np.array_equal(uo2.numpy()[ok], u[ok])
 
 
 def test_custom_domain_length(B):
