@@ -179,7 +179,14 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
 #pragma unroll
                     for (int jz = 0; jz < ORD; ++jz) {
                         const A v = GRAD ? fma(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz];
-                        atomicAdd(line + jz, v);
+                        if constexpr (sizeof(A) == 4) {   // reduction without a return value
+                            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(
+                                             (unsigned)__cvta_generic_to_shared(line + jz)),
+                                         "f"((float)v)
+                                         : "memory");
+                        } else {
+                            atomicAdd(line + jz, v);
+                        }
                     }
                 }
             }
