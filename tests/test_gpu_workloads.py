@@ -126,3 +126,25 @@ def test_full_size_512_quintic_sampled_parity(B):
     print(f"512^3 quintic: FP32 normwise u {eu32:.2e} grad {eg32:.2e}; BF16 u {eu16:.2e} grad {eg16:.2e}")
     assert eu32 < 2e-5 and eg32 < 5e-5
     assert eu16 < 2e-2 and eg16 < 5e-2
+
+
+@pytest.mark.parametrize("N", [768, 1024])
+def test_largest_grids_against_direct_sum(B, N):
+    """The largest compiled grids (768 = 3 * 256 with the radix-3 stage, and 1024), FP32, quintic: a
+    low-wavenumber field, whose interpolation error is far below FP32 rounding, against the direct
+    trigonometric sum at sampled positions."""
+    F = synth.kolmogorov_field(N, seed=31, kmax=4)
+    plan = B.Plan(N, 6, "f32")
+    uh = torch.zeros((3, N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+    idx = torch.from_numpy(F.idx).cuda()
+    uh[:, idx[:, 0], idx[:, 1], idx[:, 2]] = torch.from_numpy(F.val).to(torch.complex64).cuda()
+    coef = plan.coeffs(uh)
+    x = synth.uniform_particles(4096, seed=32)
+    u, g = plan.interp(coef, torch.from_numpy(x).cuda())
+    assert plan.status() == 0
+    ru, rg = O.direct_sum_modes(N, F.idx, F.val.astype(np.complex64).astype(np.complex128), x)
+    assert normwise(u.cpu().numpy(), ru) < 2e-5
+    assert normwise(g.cpu().numpy(), rg) < 5e-5
+    del uh, coef, u, g
+    plan.close()
+    torch.cuda.empty_cache()
