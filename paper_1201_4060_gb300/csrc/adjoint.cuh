@@ -244,10 +244,50 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
     stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+    __shared__ unsigned s_bucket[32];
+    __shared__ unsigned short s_order[kChunk];
+    const unsigned n = end - beg;
+    if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
+    __syncthreads();                                    // the tile copies stay in flight while bucketing
+    // FP32 tiles: particles ordered rank-major, bank-minor by the bank of their stencil origin, as in
+    // the gather, so a warp's tile loads hit distinct banks
+    constexpr bool kBucket = sizeof(A) == 4;
+    if constexpr (kBucket) {
+        constexpr int KT = (kChunk + kAdjThreads - 1) / kAdjThreads;
+        unsigned packed[KT];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const unsigned i = threadIdx.x + k * kAdjThreads;
+            if (i < n) {
+                const unsigned cp = w.s_rec[beg + i].cell;
+                const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
+                const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
+                const int oz = (int)(cp & 1023u) - z0;
+                const unsigned r = (unsigned)(ox * S::SX + oy * S::SY + oz) & 31u;
+                packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const unsigned i = threadIdx.x + k * kAdjThreads;
+            if (i < n) {
+                const unsigned r = packed[k] & 31u, rk = packed[k] >> 5;
+                unsigned pos = 0;
+#pragma unroll 8
+                for (unsigned q = 0; q < 32; ++q) {
+                    const unsigned bq = s_bucket[q];
+                    pos += min(bq, rk) + ((q < r && bq > rk) ? 1u : 0u);
+                }
+                s_order[pos] = (unsigned short)i;
+            }
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
     const A s2 = dscale * dscale;
-    for (unsigned i = beg + threadIdx.x; i < end; i += kAdjThreads) {
+    for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
+        const unsigned i = beg + (kBucket ? (unsigned)s_order[q] : q);
         const Rec<TR> rc = w.s_rec[i];
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
