@@ -115,6 +115,16 @@ int bspline_coeffs(bspline_plan_t plan, const void* u_hat, void* coeffs);
 int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
                    void* out_u, void* out_grad, int flags);
 
+/* Steps 1-3 in one call on device buffers: bspline_coeffs(u_hat -> coeffs)
+ * then bspline_interp(coeffs, x -> out_u, out_grad), arguments and checks as
+ * those two.  The particle sort needs only x, so it runs on a second stream
+ * of the plan, concurrently with the coefficient transform, and the
+ * evaluation starts once both are done; the call returns after queueing and
+ * everything it queued is ordered after earlier work on the plan's stream
+ * and before later work on it.  Same results as the two calls. */
+int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const double* x, int64_t P,
+                 void* out_u, void* out_grad, int flags);
+
 /* Adjoint (reverse-mode derivative) of bspline_coeffs + bspline_interp for
  * the loss  sum_p g_u[p] . u(x_p) + sum_p g_grad[p] : grad u(x_p).  The paper
  * has no adjoint; this is the transpose of the maps of Sections 3-4 and 7.

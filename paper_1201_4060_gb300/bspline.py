@@ -60,6 +60,7 @@ def _load() -> ctypes.CDLL:
         "bspline_uhat_bytes": (i32, [vp, ctypes.POINTER(sz)]),
         "bspline_coeffs": (i32, [vp, vp, vp]),
         "bspline_interp": (i32, [vp, vp, vp, i64, vp, vp, i32]),
+        "bspline_eval": (i32, [vp, vp, vp, vp, i64, vp, vp, i32]),
         "bspline_spread_adjoint": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
         "bspline_workspace_bytes": (i32, [vp, i64, ctypes.POINTER(sz)]),
         "bspline_status": (i32, [vp, ctypes.POINTER(i64)]),
@@ -129,6 +130,11 @@ def bspline_coeffs(plan: int, u_hat_ptr: int, coeffs_ptr: int) -> int:
 
 def bspline_interp(plan: int, coeffs_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int, flags: int) -> int:
     return _load().bspline_interp(plan, coeffs_ptr, x_ptr, P, u_ptr, grad_ptr, flags)
+
+
+def bspline_eval(plan: int, u_hat_ptr: int, coeffs_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int,
+                 flags: int) -> int:
+    return _load().bspline_eval(plan, u_hat_ptr, coeffs_ptr, x_ptr, P, u_ptr, grad_ptr, flags)
 
 
 def bspline_spread_adjoint(plan, coeffs_ptr, x_ptr, P, gu_ptr, ggrad_ptr, gcoef_ptr, guhat_ptr, gx_ptr) -> int:
@@ -284,6 +290,33 @@ class Plan:
                             out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
         _check(rc, "bspline_interp")
         return (out_u, out_grad) if grad else out_u
+
+    def eval(self, u_hat, x, coef=None, out_u=None, out_grad=None, grad: bool = True, stream=None):
+        """coeffs(u_hat) then interp at x in one call, the particle sort overlapping the transform.
+
+        Returns (coef, u, grad_u), or (coef, u) with grad=False.
+        """
+        import torch
+        N = self.N
+        if u_hat.shape != (3, N, N, N // 2 + 1) or u_hat.dtype != self.uhat_dtype or not u_hat.is_cuda \
+                or not u_hat.is_contiguous():
+            raise ValueError(f"u_hat must be contiguous CUDA {self.uhat_dtype} of shape {(3, N, N, N // 2 + 1)}")
+        if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
+        if coef is None:
+            coef = self.empty_coeffs()
+        if coef.shape != (3, N, N, N) or coef.dtype != self.coef_dtype or not coef.is_contiguous():
+            raise ValueError("bad coefficient buffer")
+        P = x.shape[0]
+        if out_u is None:
+            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=x.device)
+        if grad and out_grad is None:
+            out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=x.device)
+        self._stream(stream)
+        rc = bspline_eval(self.handle, u_hat.data_ptr(), coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
+                          out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
+        _check(rc, "bspline_eval")
+        return (coef, out_u, out_grad) if grad else (coef, out_u)
 
     def spread_adjoint(self, x, g_u=None, g_grad=None, coef=None, g_coef=None, u_hat_grad: bool = True,
                        stream=None):

@@ -234,6 +234,15 @@ void free_plan(bspline_plan_s* p) {
     delete p;
 }
 
+// The plan's second stream and its two events, created on first use.
+int ensure_aux(bspline_plan_s* plan) {
+    cudaError_t e = cudaSuccess;
+    if (!plan->aux_stream) e = cudaStreamCreateWithFlags(&plan->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !plan->ev_start) e = cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess && !plan->ev_sorted) e = cudaEventCreateWithFlags(&plan->ev_sorted, cudaEventDisableTiming);
+    return set_cuda_error(e);
+}
+
 }  // namespace
 }  // namespace bs
 
@@ -338,6 +347,35 @@ int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int
     return launch_interp(plan, coeffs, x, P, out_u, out_grad, flags);
 }
 
+int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const double* x, int64_t P, void* out_u,
+                 void* out_grad, int flags) {
+    if (!valid_plan(plan) || !u_hat || !coeffs) return BSPLINE_ERR_INVALID_ARG;
+    if (!aligned(u_hat, 16) || !aligned(coeffs, 16)) return BSPLINE_ERR_INVALID_ARG;
+    const char* a = (const char*)u_hat;
+    const char* b = (const char*)coeffs;
+    if (a < b + coef_bytes_of(plan) && b < a + uhat_bytes_of(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (flags & ~BSPLINE_INTERP_NO_GRAD) return BSPLINE_ERR_INVALID_ARG;
+    if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
+    if (P > 0) {
+        if (!x || !out_u) return BSPLINE_ERR_INVALID_ARG;
+        if (!(flags & BSPLINE_INTERP_NO_GRAD) && !out_grad) return BSPLINE_ERR_INVALID_ARG;
+        const size_t ob = out_bytes(plan->dtype);
+        if (!aligned(x, 8) || !aligned(out_u, ob) || (out_grad && !aligned(out_grad, ob)))
+            return BSPLINE_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    int rc;
+    if (P == 0) return launch_coeffs(plan, u_hat, coeffs);
+    if ((rc = ensure_aux(plan))) return rc;
+    // the second stream starts after everything already queued on the plan's stream
+    cudaError_t e = cudaEventRecord(plan->ev_start, plan->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->aux_stream, plan->ev_start, 0);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if ((rc = launch_coeffs(plan, u_hat, coeffs))) return rc;
+    return launch_interp_split(plan, coeffs, x, P, out_u, out_grad, flags, plan->aux_stream, plan->ev_sorted);
+}
+
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, const void* g_u,
                            const void* g_grad, void* g_coeffs, void* g_u_hat, double* g_x) {
     if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
@@ -405,14 +443,10 @@ int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* 
     if ((rc = plan->host_x.grow(sizeof(double) * 3 * (size_t)(P ? P : 1)))) return rc;
     if ((rc = plan->host_u.grow(ob * 3 * (size_t)(P ? P : 1)))) return rc;
     if ((rc = plan->host_grad.grow(ob * 9 * (size_t)(P ? P : 1)))) return rc;
-    cudaError_t e = cudaSuccess;
-    if (!plan->aux_stream) e = cudaStreamCreateWithFlags(&plan->aux_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !plan->ev_start) e = cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming);
-    if (e == cudaSuccess && !plan->ev_sorted) e = cudaEventCreateWithFlags(&plan->ev_sorted, cudaEventDisableTiming);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    if ((rc = ensure_aux(plan))) return rc;
     cudaStream_t st = plan->stream, aux = plan->aux_stream;
     // the second stream starts after everything already queued on the plan's stream
-    e = cudaEventRecord(plan->ev_start, st);
+    cudaError_t e = cudaEventRecord(plan->ev_start, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, plan->ev_start, 0);
     if (e == cudaSuccess && P)
         e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, aux);

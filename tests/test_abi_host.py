@@ -55,6 +55,7 @@ def test_null_plan_is_rejected_everywhere():
     assert B.bspline_destroy(0) == B.OK
     assert B.bspline_coeffs(0, 16, 32) == B.ERR_INVALID_ARG
     assert B.bspline_interp(0, 16, 16, 10, 16, 16, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_eval(0, 16, 32, 16, 10, 16, 16, 0) == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_stream(0, 0) == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_length(0, 1.0) == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_prefilter(0, 0) == B.ERR_INVALID_ARG

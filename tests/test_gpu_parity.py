@@ -267,6 +267,56 @@ def test_run_host_matches_device_path(B):
     assert np.array_equal(uo2.numpy()[ok], u[ok])
 
 
+@pytest.mark.parametrize("dtype,N,order", [("f32", 48, 6), ("f64", 32, 5), ("bf16", 64, 4)])
+def test_eval_matches_coeffs_then_interp(B, dtype, N, order):
+    """bspline_eval (sort on the second stream, overlapping the transform) gives the
+    two-call results bit for bit, call after call on one plan, also u only and with
+    a non-finite position; the FP64 case is held to the oracle too."""
+    half = synth.kolmogorov_field(N, seed=21).dense()
+    x = synth.clustered_particles(20000, seed=21)
+    c_ref, u_ref, g_ref, _ = gpu_path(B, half, x, N, order, dtype)
+    plan = B.Plan(N, order, dtype)
+    uh = torch.from_numpy(half).to(plan.uhat_dtype).cuda()
+    xt = torch.from_numpy(x).cuda()
+    for _ in range(3):
+        coef, u, g = plan.eval(uh, xt)
+        assert plan.status() == 0
+        c = coef.float().cpu().numpy() if dtype == "bf16" else coef.cpu().numpy()
+        assert np.array_equal(c, c_ref)
+        assert np.array_equal(u.cpu().numpy(), u_ref) and np.array_equal(g.cpu().numpy(), g_ref)
+    if dtype == "f64":
+        ru, rg = O.interpolate(half, x, order)
+        assert normwise(u_ref, ru) < TOL64 and normwise(g_ref, rg) < TOL64
+    x2 = x.copy()
+    x2[11, 2] = np.inf
+    coef2, u2 = plan.eval(uh, torch.from_numpy(x2).cuda(), coef=coef, grad=False)
+    assert plan.status() == 1
+    ok = np.ones(len(x), bool)
+    ok[11] = False
+    u2 = u2.cpu().numpy()
+    assert np.isnan(u2[11]).all() and np.array_equal(u2[ok], u_ref[ok])
+    # no particles: only the transform runs
+    coef3, u3, g3 = plan.eval(uh, torch.empty((0, 3), dtype=torch.float64, device="cuda"))
+    assert u3.shape == (0, 3) and g3.shape == (0, 3, 3)
+    c3 = coef3.float().cpu().numpy() if dtype == "bf16" else coef3.cpu().numpy()
+    assert np.array_equal(c3, c_ref)
+
+
+def test_eval_rejects_bad_arguments(B):
+    plan = B.Plan(16, 4, "f32")
+    h = plan.handle
+    buf = torch.empty(1 << 18, dtype=torch.float64, device="cuda")
+    p = buf.data_ptr()
+    q = p + (1 << 20)
+    assert B.bspline_eval(h, p, p, q, 10, q, q, 0) == B.ERR_INVALID_ARG          # coeffs alias u_hat
+    assert B.bspline_eval(h, p + 8, q, q, 10, q, q, 0) == B.ERR_INVALID_ARG      # misaligned u_hat
+    assert B.bspline_eval(h, p, q, q + 4, 10, q, q, 0) == B.ERR_INVALID_ARG      # misaligned x
+    assert B.bspline_eval(h, p, q, 0, 10, q, q, 0) == B.ERR_INVALID_ARG          # x NULL with P > 0
+    assert B.bspline_eval(h, p, q, q, 10, q, 0, 0) == B.ERR_INVALID_ARG          # grad NULL without flag
+    assert B.bspline_eval(h, p, q, q, -1, q, q, 0) == B.ERR_INVALID_ARG
+    assert B.bspline_eval(h, p, q, q, 10, q, q, 0x80) == B.ERR_INVALID_ARG       # unknown flag
+
+
 def test_custom_domain_length(B):
     N, order, Lc = 16, 4, 3.0
     half = synth.kolmogorov_field(N, seed=12).dense()
