@@ -100,7 +100,8 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // its ring slot have read it.  Every dependency points to an earlier item,
 // taken by a CTA that is already running, so the waits end; each wait is
 // still bounded (about a second) and, if it runs out, sets the error word and
-// the kernel returns.
+// the CTA returns; every later wait of the launch sees the error word and
+// returns at once, so the launch ends.
 //
 // c2r along kz: with M = N/2 and X[M + k] = conj(X[M - k]) (X[M] itself for
 // k = 0), E[k] = X[k] + X[M + k] and O[k] = (X[k] - X[M + k]) exp(2 pi i k / N)
@@ -151,6 +152,12 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
+// Count one finished item: a release reduction, so everything the CTA wrote or
+// read before its last barrier happens before any acquire load that sees the count.
+__device__ __forceinline__ void signal_release(unsigned* p) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+
 // Thread 0 waits until *flag >= target (bounded); returns false for the whole CTA on error.
 __device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, unsigned* error, unsigned* s_ok) {
     if (threadIdx.x == 0) {
@@ -171,10 +178,13 @@ __device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, 
     return *s_ok != 0u;
 }
 
-// Z rows per item: NL (FP32), 2 NL (FP64); fewer rows keep the shared memory
-// of a CTA small enough for four CTAs per SM in FP32.
+// Z rows per item: 2 NL (16 FP32 rows, 8 FP64 rows; all of them for small N).
+// The rows are transformed in place (the staged ring rows and the transform
+// buffer share memory), which keeps a CTA's shared memory small enough for
+// four CTAs per SM in FP32 while halving the number of Z items and the fixed
+// cost each one carries (its wait, its barriers, its signal).
 template <typename R, int N, int NL> constexpr int z_rows() {
-    return ((sizeof(R) == 4 ? 1 : 2) * NL < N) ? (sizeof(R) == 4 ? 1 : 2) * NL : N;
+    return (2 * NL < N) ? 2 * NL : N;
 }
 
 // Row pitch of the staged ring rows of a Z item: HP plus 16 bytes of skew, so
@@ -189,7 +199,8 @@ constexpr size_t yz_smem_elems() {
     using V = typename Cx<R>::T;
     constexpr int NR = z_rows<R, N, TL>();
     constexpr size_t y = (size_t)N * NLY;
-    constexpr size_t z = (size_t)NR * z_row_pitch<V, N>() + (size_t)(N / 2) * (NR + 1);
+    constexpr size_t zr = (size_t)NR * z_row_pitch<V, N>(), zt = (size_t)(N / 2) * (NR + 1);
+    constexpr size_t z = zr > zt ? zr : zt;
     return N + (y > z ? y : z);
 }
 
@@ -219,7 +230,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* buf = tws + N;                                   // Y: [N][QY] tile of NLY columns
     V* raw = buf;                                       // Z: NR ring rows, pitch RP
-    V* trans = buf + NR * RP;                           // Z: [M][QZ] transform buffer
+    V* trans = buf;                                     // Z: [M][QZ] transform buffer over them (in place)
     __shared__ unsigned s_item[2], s_ok;
     unsigned* next = ctr;
     unsigned* done_y = ctr + 1;
@@ -232,7 +243,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     for (unsigned it = 0;; ++it) {
         // alternate slots: the slot written now was last read two items ago, before this item's barriers
         if (t == 0) {
-            s_item[it & 1u] = (ld_acquire(error) != 0u) ? 0xffffffffu : claimed;
+            s_item[it & 1u] = claimed;
             claimed = atomicAdd(next, 1u);
         }
         __syncthreads();
@@ -267,8 +278,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             }
             __syncthreads();
             if (t == 0 && !drop_signals) {
-                __threadfence();
-                atomicAdd(&done_y[lp], 1u);
+                signal_release(&done_y[lp]);
             }
         } else {
             // ---- Z item: rows y0..y0+NR-1 of the plane, c2r along kz
@@ -283,8 +293,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             cp_async_wait_all();
             __syncthreads();                            // the slot's rows are read: release it
             if (t == 0) {
-                __threadfence();
-                atomicAdd(&done_z[lp], 1u);
+                signal_release(&done_z[lp]);
             }
             auto ld = [&](int k, int b) -> V {          // even/odd split of the half spectrum
                 const V* row = raw + b * RP;
@@ -300,7 +309,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             if constexpr (radix_for(M) == M) {
                 stage_single<V, M, NR, T>(ld, st);
             } else {
-                stage_first<V, M, NR, T, QZ>(trans, ld);
+                stage_first<V, M, NR, T, QZ, true>(trans, ld);
                 stages_mid<V, M, NR, T, QZ, radix_for(M)>(trans, tws, 2);
                 stage_last<V, M, NR, T, QZ, true>(trans, tws, 2, st);
             }

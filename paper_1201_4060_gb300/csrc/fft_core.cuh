@@ -143,7 +143,9 @@ constexpr int ns_last(int L) {
 
 // First stage (NS = 1): butterfly j of line b takes positions j + r L/R from
 // ld(position, line) and writes s[(j R + r) QS + b].  Ends with a barrier.
-template <typename V, int L, int NLINES, int T, int QS, typename Ld>
+// IN_PLACE: ld reads the same shared memory, so a barrier separates every
+// thread's reads from the first write.
+template <typename V, int L, int NLINES, int T, int QS, bool IN_PLACE = false, typename Ld>
 __device__ __forceinline__ void stage_first(V* s, Ld ld) {
     constexpr int RADIX = radix_for(L);
     constexpr int NB = (L / RADIX) * NLINES;
@@ -159,6 +161,7 @@ __device__ __forceinline__ void stage_first(V* s, Ld ld) {
             for (int r = 0; r < RADIX; ++r) v[i][r] = ld(j + r * (L / RADIX), b);
         }
     }
+    if constexpr (IN_PLACE) __syncthreads();
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int u = t + i * T;
