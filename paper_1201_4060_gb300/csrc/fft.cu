@@ -97,11 +97,14 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // counter: per plane, ceil(H / NL) "Y" items (NL kz columns, all ky) then
 // N / NR "Z" items (NR rows y, all kz).  A Z item waits until all Y items of
 // its plane have been stored; a Y item waits until the Z items that last used
-// its ring slot have read it.  Every dependency points to an earlier item,
-// taken by a CTA that is already running, so the waits end; each wait is
-// still bounded (about a second) and, if it runs out, sets the error word and
-// the CTA returns; every later wait of the launch sees the error word and
-// returns at once, so the launch ends.
+// its ring slot have read it.  Thread 0 checks an item's flag when it hands
+// the item to its CTA: while the previous item runs it has already read that
+// flag (relaxed), and if the read shows the dependency done an acquire fence
+// is all the check costs; otherwise it waits on the flag with acquire loads.
+// Every dependency points to an earlier item, taken by a CTA that is already
+// running, so the waits end; each wait is still bounded (about a second) and,
+// if it runs out, sets the error word and the CTA returns; every later wait
+// of the launch sees the error word and returns at once, so the launch ends.
 //
 // c2r along kz: with M = N/2 and X[M + k] = conj(X[M - k]) (X[M] itself for
 // k = 0), E[k] = X[k] + X[M + k] and O[k] = (X[k] - X[M + k]) exp(2 pi i k / N)
@@ -158,24 +161,27 @@ __device__ __forceinline__ void signal_release(unsigned* p) {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
 }
 
-// Thread 0 waits until *flag >= target (bounded); returns false for the whole CTA on error.
-__device__ __forceinline__ bool cta_wait(const unsigned* flag, unsigned target, unsigned* error, unsigned* s_ok) {
-    if (threadIdx.x == 0) {
-        unsigned ok = 1;
-        long long it = 0;
-        while (ld_acquire(flag) < target) {
-            if (ld_acquire(error) != 0u) { ok = 0; break; }
-            if (++it > kWaitLimit) {
-                atomicExch(error, 1u);
-                ok = 0;
-                break;
-            }
-            __nanosleep(200);
+// Relaxed load at GPU scope: no ordering of its own; with fence_acq_rel after
+// it (once it has seen a released count) it acts as an acquire.
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Thread 0 only: bounded acquire wait for *flag >= target; false (error word set) if it runs out.
+__device__ __forceinline__ bool spin_acquire(const unsigned* flag, unsigned target, unsigned* error) {
+    long long it = 0;
+    while (ld_acquire(flag) < target) {
+        if (ld_acquire(error) != 0u) return false;
+        if (++it > kWaitLimit) {
+            atomicExch(error, 1u);
+            return false;
         }
-        *s_ok = ok;
+        __nanosleep(200);
     }
-    __syncthreads();
-    return *s_ok != 0u;
+    return true;
 }
 
 // Z rows per item: 2 NL (16 FP32 rows, 8 FP64 rows; all of them for small N).
@@ -231,7 +237,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     V* buf = tws + N;                                   // Y: [N][QY] tile of NLY columns
     V* raw = buf;                                       // Z: NR ring rows, pitch RP
     V* trans = buf;                                     // Z: [M][QZ] transform buffer over them (in place)
-    __shared__ unsigned s_item[2], s_ok;
+    __shared__ unsigned s_item[2];
     unsigned* next = ctr;
     unsigned* done_y = ctr + 1;
     unsigned* done_z = ctr + 1 + planes;
@@ -240,15 +246,51 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     // thread 0 claims the following item while this one runs (its counter round trip overlaps the work);
     // a claimed item depends only on earlier items, so the smallest running item can always proceed
     unsigned claimed = (t == 0) ? atomicAdd(next, 1u) : 0u;
+    const unsigned total = (unsigned)(planes * IPP);
+    unsigned pre_item = 0xffffffffu, pre_val = 0;       // thread 0: relaxed read of the next item's flag
+    // the flag an item waits for: a Z item its plane's Y items, a Y item its ring slot
+    auto flag_of = [&](unsigned item, const unsigned** f, unsigned* target) {
+        long long lp;
+        int r;
+        item_to_plane<TPZ, ZPP>(item, planes, lag, &lp, &r);
+        *f = nullptr;
+        if (r >= TPZ) {
+            *f = &done_y[lp];
+            *target = (unsigned)TPZ;
+        } else if (lp >= ring_slots) {
+            *f = &done_z[lp - ring_slots];
+            *target = (unsigned)ZPP;
+        }
+    };
+    auto prefetch_flag = [&]() {                        // thread 0, once the next claim has returned
+        pre_item = claimed;
+        const unsigned* f;
+        unsigned target;
+        if (pre_item < total) {
+            flag_of(pre_item, &f, &target);
+            pre_val = f ? ld_relaxed(f) : 0u;
+        }
+    };
     for (unsigned it = 0;; ++it) {
         // alternate slots: the slot written now was last read two items ago, before this item's barriers
         if (t == 0) {
-            s_item[it & 1u] = claimed;
+            const unsigned item = claimed;
             claimed = atomicAdd(next, 1u);
+            unsigned ok = 1;
+            if (item < total) {
+                const unsigned* f;
+                unsigned target;
+                flag_of(item, &f, &target);
+                if (f) {
+                    if (pre_item == item && pre_val >= target) { fence_acq_rel(); }
+                    else ok = spin_acquire(f, target, error) ? 1u : 0u;
+                }
+            }
+            s_item[it & 1u] = ok ? item : 0xfffffffeu;
         }
         __syncthreads();
         const unsigned item = s_item[it & 1u];
-        if (item >= (unsigned)(planes * IPP)) return;
+        if (item >= total) return;
         long long lp;                                   // plane within this launch; pl = plane0 + lp
         int r;
         item_to_plane<TPZ, ZPP>(item, planes, lag, &lp, &r);
@@ -267,13 +309,12 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
                 if (b < valid) dst[(long long)q * HP + b] = v;
             };
             if constexpr (radix_for(N) == N) {
-                if (lp >= ring_slots && !cta_wait(&done_z[lp - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
+                if (t == 0) prefetch_flag();
                 stage_single<V, N, NLY, T>(ld, st);
             } else {
                 stage_first<V, N, NLY, T, QY>(buf, ld);
+                if (t == 0) prefetch_flag();
                 stages_mid<V, N, NLY, T, QY, radix_for(N)>(buf, tws, 1);
-                // the slot is free once the Z items of the plane that used it before have read it
-                if (lp >= ring_slots && !cta_wait(&done_z[lp - ring_slots], (unsigned)ZPP, error, &s_ok)) return;
                 stage_last<V, N, NLY, T, QY, false>(buf, tws, 1, st);
             }
             __syncthreads();
@@ -282,7 +323,6 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             }
         } else {
             // ---- Z item: rows y0..y0+NR-1 of the plane, c2r along kz
-            if (!cta_wait(&done_y[lp], (unsigned)TPZ, error, &s_ok)) return;
             const int y0 = (r - TPZ) * NR;
             const unsigned char* src = reinterpret_cast<const unsigned char*>(slot + (long long)y0 * HP);
             unsigned char* dstb = reinterpret_cast<unsigned char*>(raw);
@@ -294,6 +334,7 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             __syncthreads();                            // the slot's rows are read: release it
             if (t == 0) {
                 signal_release(&done_z[lp]);
+                prefetch_flag();
             }
             auto ld = [&](int k, int b) -> V {          // even/odd split of the half spectrum
                 const V* row = raw + b * RP;
