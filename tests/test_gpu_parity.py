@@ -175,6 +175,54 @@ def test_edge_cases_f64(B):
     assert normwise(g, rg) < TOL64
 
 
+@pytest.mark.parametrize("order", [4, 5])
+def test_edge_cases_f32(B, order):
+    """FP32 plans locate particles from an integer product of the significands of x and N/L
+    (no FP64 multiply); positions on nodes, on the seam, far outside, tiny and negative."""
+    N = 16
+    half = synth.kolmogorov_field(N, seed=4).dense().astype(np.complex64).astype(np.complex128)
+    h = L / N
+    pts = [
+        [0.0, 0.0, 0.0],
+        [h, 2 * h, 3 * h],
+        [L, L, L],
+        [-1e-13, 1e-13, L - 1e-13],
+        [-7.5 * L, 3.25 * L, 1e3],
+        [0.5 * h, 0.5 * h, 0.5 * h],
+        [1e-30, 5e-324, 2.0 ** -70],
+        [np.nextafter(h, 0.0), np.nextafter(h, 1.0), 7 * h],
+        [1e6, -1e6, 123.456],
+    ]
+    rng = np.random.default_rng(1)
+    pts += rng.uniform(-3 * L, 4 * L, (500, 3)).tolist()
+    x = np.array(pts)
+    _, u, g, nf = gpu_path(B, half, x, N, order, "f32")
+    ru, rg = O.interpolate(half, x, order)
+    assert nf == 0
+    assert normwise(u, ru) < TOL32["u"]
+    assert normwise(g, rg) < TOL32["grad"]
+
+
+def test_nonfinite_positions_f32(B):
+    N, order = 16, 6
+    half = synth.kolmogorov_field(N, seed=4).dense().astype(np.complex64).astype(np.complex128)
+    x = synth.uniform_particles(100, seed=3)
+    x[5, 0] = np.nan
+    x[17, 2] = np.inf
+    x[42, 1] = -np.inf
+    x[60, 1] = 1e300
+    x[61, 0] = -1e300
+    x[62, 2] = 2.0 ** 60                      # no fraction bits left at FP64 precision
+    _, u, g, nf = gpu_path(B, half, x, N, order, "f32")
+    bad = [5, 17, 42, 60, 61, 62]
+    assert nf == len(bad)
+    assert np.all(np.isnan(u[bad])) and np.all(np.isnan(g[bad]))
+    good = np.setdiff1d(np.arange(100), bad)
+    ru, rg = O.interpolate(half, x[good], order)
+    assert normwise(u[good], ru) < TOL32["u"]
+    assert normwise(g[good], rg) < TOL32["grad"]
+
+
 def test_nonfinite_positions_give_nan_and_status(B):
     N, order = 16, 4
     half = synth.kolmogorov_field(N, seed=4).dense()
