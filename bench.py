@@ -133,7 +133,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- algorithmic bytes
 
-def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
+def algorithmic_bytes(stage: str, N: int, P: int, dtype: str, order: int = 6) -> float:
     """Bytes a kernel must move at minimum (each input read once, each output written once)."""
     H = N // 2 + 1
     cplx = 16 if dtype == "f64" else 8
@@ -142,15 +142,16 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str) -> float:
     tb = 8 if dtype == "f64" else 4
     spec = 3 * N * N * H * cplx
     coef = 3 * N ** 3 * elem
-    brick = 8 if dtype == "f64" else 16
-    nb = max(1, N // brick) ** 3
-    rec = 16 if tb == 4 else 32                  # packed record: first node + t per axis
+    bx = 8 if dtype == "f64" else 16             # brick extents (x = z); y is 12 up to order 6 in FP32
+    by = 8 if (dtype == "f64" or order > 6) else 12
+    nb = (-(-N // bx)) ** 2 * (-(-N // by))
+    rec = 16 if tb == 4 else 32                  # first node + t per axis (the stored record adds padding)
     return {
         "fft_x": 2 * spec,                       # read u_hat, write the x-transformed spectrum
         "fft_yz": spec + coef,                   # read that spectrum, write coefficients (ring stays in L2)
         "bin": P * 24,                           # positions in (per-brick counts stay in L2)
         "scan": 4 * 4 * (nb + 1),
-        "scatter": P * 24 + P * (rec + 4),       # positions in again; sorted record and index out
+        "scatter": P * 24 + P * (rec + 4),       # positions in again; sorted record and original index out
         "gather": coef + P * (rec + 4) + P * 12 * outb,    # coefficients once, sorted records, u and grad out
     }[stage]
 
@@ -310,7 +311,7 @@ def run_ours(args):
     pk = peaks()
     dom = max(STAGES, key=lambda s: stages[s][0])
     dom_ms = stages[dom][0] / max(stages[dom][1], 1)
-    abytes = algorithmic_bytes(dom, N, P, "f32")
+    abytes = algorithmic_bytes(dom, N, P, "f32", order)
     achieved = abytes / (dom_ms / 1e3) / 1e9
     traffic = measured_traffic(dom, "f32", N, order)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -322,7 +323,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     fma_peak = sms * 128 * pk["sm_max_mhz"] * 1e6
     fma_rate = P * from_table1 / (g_ms / 1e3)
-    g_bytes = algorithmic_bytes("gather", N, P, "f32")
+    g_bytes = algorithmic_bytes("gather", N, P, "f32", order)
     gather = {"avg_launch_ms": g_ms, "achieved_gbs": g_bytes / (g_ms / 1e3) / 1e9,
               "hbm_frac": g_bytes / (g_ms / 1e3) / 1e9 / pk["hbm_gbs"],
               "fma_per_particle_table1": from_table1, "fma_rate_tfma": fma_rate / 1e12,
@@ -356,7 +357,7 @@ def run_ours(args):
         ms_bf, st_bf, _ = run_form(B, wl, F, x, "bf16", ks, 2, device)
         gb = st_bf["gather"][0] / max(st_bf["gather"][1], 1)
         forms["bf16"] = {"particles_per_s": P / (ms_bf / 1e3), "ms_per_step": ms_bf, "gather_ms": gb,
-                         "gather_hbm_frac": algorithmic_bytes("gather", N, P, "bf16") / (gb / 1e3) / 1e9 /
+                         "gather_hbm_frac": algorithmic_bytes("gather", N, P, "bf16", order) / (gb / 1e3) / 1e9 /
                          pk["hbm_gbs"]}
         ms_64, st_64, _ = run_form(B, wl, F, x, "f64", 2, 1, device)
         g64 = st_64["gather"][0] / max(st_64["gather"][1], 1)

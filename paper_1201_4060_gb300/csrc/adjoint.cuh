@@ -151,7 +151,7 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
-        const size_t idx = w.s_idx[i];
+        const size_t idx = rc.idx;
         A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
         bspline_weights<ORD, A>((A)rc.t[0], wx, dwx);
         bspline_weights<ORD, A>((A)rc.t[1], wy, dwy);
@@ -292,7 +292,7 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
-        const size_t idx = w.s_idx[i];
+        const size_t idx = rc.idx;
         A wx[ORD], dwx[ORD], d2wx[ORD], wy[ORD], dwy[ORD], d2wy[ORD], wz[ORD], dwz[ORD], d2wz[ORD];
         bspline_weights2<ORD, A>((A)rc.t[0], wx, dwx, d2wx);
         bspline_weights2<ORD, A>((A)rc.t[1], wy, dwy, d2wy);

@@ -278,8 +278,9 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
             d = atomicAdd(&w.cursor[k], 1u);
         }
         if (place) {
-            w.s_rec[d] = r;
-            w.s_idx[d] = (unsigned)p;
+            r.idx = (unsigned)p;
+            if constexpr (sizeof(TR) == 4) r.pad[0] = r.pad[1] = r.pad[2] = 0u;
+            w.s_rec[d] = r;                             // one whole 32-byte sector
         }
     }
 }

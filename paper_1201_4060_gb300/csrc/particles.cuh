@@ -11,12 +11,23 @@ namespace gather_impl {
 constexpr int kAnchorBits = 10;          // N <= 1024
 
 // One particle's located record: packed first stencil node
-// (ax << 20 | ay << 10 | az) and the local variable t per axis.  16 bytes
-// for FP32 t, 32 bytes for FP64 t, so that it moves in one vector access.
-template <typename TR> struct __align__(16) Rec {
+// (ax << 20 | ay << 10 | az), the local variable t per axis and the
+// particle's original index.  Exactly one 32-byte sector: the placement pass
+// writes records to scattered slots, and a record that filled only part of a
+// sector would cost a read-modify-write of it in DRAM.
+template <typename TR> struct Rec;
+template <> struct __align__(32) Rec<float> {
     unsigned cell;
-    TR t[3];
+    float t[3];
+    unsigned idx;
+    unsigned pad[3];    // written as zeros, so that every store covers the whole sector
 };
+template <> struct __align__(32) Rec<double> {
+    unsigned cell;
+    unsigned idx;
+    double t[3];
+};
+static_assert(sizeof(Rec<float>) == 32 && sizeof(Rec<double>) == 32, "one sector per record");
 
 // Particles per gather work item: a brick with more particles is split into
 // several items, each staging the brick's tile, so no CTA serialises a clump.
@@ -30,7 +41,6 @@ template <typename TR> struct Ws {
     unsigned* item;     // [NB + ceil(P / kChunk)]  brick of each work item (the first chunk[NB] are set)
     long long P;        // particles
     Rec<TR>* s_rec;     // [P]       located records sorted by brick
-    unsigned* s_idx;    // [P]       original particle index of each sorted record
 };
 
 inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -49,7 +59,6 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     w->chunk = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->item = (unsigned*)take(sizeof(unsigned) * (NB + (P + kChunk - 1) / kChunk));
     w->s_rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
-    w->s_idx = (unsigned*)take(sizeof(unsigned) * P);
     return off;
 }
 
@@ -504,7 +513,7 @@ gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, doubl
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
-        const unsigned idx = w.s_idx[i];
+        const unsigned idx = rc.idx;
         double u[3], gr[9];
         eval_particle<ORD, double, GRAD, S::SX, S::SY, S::TS>(tile + ox * S::SX + oy * S::SY + oz, (double)rc.t[0],
                                                                (double)rc.t[1], (double)rc.t[2], dscale, u, gr);
@@ -611,9 +620,8 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
                 *hi = min((unsigned)n, *lo + 32u);
             }
         };
-        // the next job's record and index are loaded while the current one is evaluated
+        // the next job's record is loaded while the current one is evaluated
         Rec<TR> rc_n;
-        unsigned idx_n = 0;
         bool v_n = false;
         auto fetch = [&](unsigned j) {
             unsigned lo, hi;
@@ -623,7 +631,6 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             if (v_n) {
                 const unsigned i = c0 + s_order[pos];
                 rc_n = w.s_rec[i];
-                idx_n = w.s_idx[i];
             }
         };
         // Jobs are dealt to the NW warps in rounds.  A last, partly filled round
@@ -635,7 +642,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
         if ((unsigned)warp < jfull) fetch(warp);
         for (unsigned j = warp; j < jfull; j += NW) {
             const Rec<TR> rc = rc_n;
-            const unsigned idx = idx_n;
+            const unsigned idx = rc.idx;
             const bool v = v_n;
             v_n = false;
             if (j + NW < jfull) fetch(j + NW);
@@ -662,7 +669,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             if (pos < hi) {
                 const unsigned i = c0 + s_order[pos];
                 const Rec<TR> rc = w.s_rec[i];
-                const unsigned idx = w.s_idx[i];
+                const unsigned idx = rc.idx;
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(rc.cell & 1023u) - z0;
