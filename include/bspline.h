@@ -170,6 +170,21 @@ int bspline_status(bspline_plan_t plan, int64_t* nonfinite);
 int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P,
                      void* u_host, void* grad_host);
 
+/* bspline_run_host without its final synchronisation: returns once the
+ * copies and kernels are queued on the plan's streams.  The host buffers
+ * must stay valid, the inputs unchanged and the outputs unread until
+ * bspline_wait(plan) returns; errors of the queued work are reported there.
+ * Calls on one plan run in order (each starts after everything the previous
+ * one queued); calls on plans with different streams overlap, so a caller
+ * that alternates two plans streams steps with one step's result copy to the
+ * host running while the next step's inputs are copied in. */
+int bspline_run_host_async(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P,
+                           void* u_host, void* grad_host);
+
+/* Wait for all work queued on the plan (all of its streams); the first CUDA
+ * error of that work, else BSPLINE_OK. */
+int bspline_wait(bspline_plan_t plan);
+
 /* Free the plan, its tables and workspace.  NULL is accepted. */
 int bspline_destroy(bspline_plan_t plan);
 

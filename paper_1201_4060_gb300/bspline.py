@@ -65,6 +65,8 @@ def _load() -> ctypes.CDLL:
         "bspline_workspace_bytes": (i32, [vp, i64, ctypes.POINTER(sz)]),
         "bspline_status": (i32, [vp, ctypes.POINTER(i64)]),
         "bspline_run_host": (i32, [vp, vp, vp, i64, vp, vp]),
+        "bspline_run_host_async": (i32, [vp, vp, vp, i64, vp, vp]),
+        "bspline_wait": (i32, [vp]),
         "bspline_destroy": (i32, [vp]),
         "bspline_status_string": (ctypes.c_char_p, [i32]),
         "bspline_version": (ctypes.c_char_p, []),
@@ -130,6 +132,14 @@ def bspline_coeffs(plan: int, u_hat_ptr: int, coeffs_ptr: int) -> int:
 
 def bspline_interp(plan: int, coeffs_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int, flags: int) -> int:
     return _load().bspline_interp(plan, coeffs_ptr, x_ptr, P, u_ptr, grad_ptr, flags)
+
+
+def bspline_run_host_async(plan: int, u_hat_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int) -> int:
+    return _load().bspline_run_host_async(plan, u_hat_ptr, x_ptr, P, u_ptr, grad_ptr)
+
+
+def bspline_wait(plan: int) -> int:
+    return _load().bspline_wait(plan)
 
 
 def bspline_eval(plan: int, u_hat_ptr: int, coeffs_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int,
@@ -374,12 +384,21 @@ class Plan:
         _check(rc, "bspline_workspace_bytes")
         return b
 
-    def run_host(self, u_hat_host, x_host, u_host, grad_host=None, stream=None):
-        """Whole path on host (ideally pinned) tensors; copies happen inside the library call."""
+    def run_host(self, u_hat_host, x_host, u_host, grad_host=None, stream=None, wait: bool = True):
+        """Whole path on host (ideally pinned) tensors; copies happen inside the library call.
+
+        wait=False queues the work and returns (bspline_run_host_async): the tensors must be left
+        alone until wait() returns.
+        """
         self._stream(stream)
-        rc = bspline_run_host(self.handle, u_hat_host.data_ptr(), x_host.data_ptr(), x_host.shape[0],
-                              u_host.data_ptr(), grad_host.data_ptr() if grad_host is not None else 0)
-        _check(rc, "bspline_run_host")
+        fn = bspline_run_host if wait else bspline_run_host_async
+        rc = fn(self.handle, u_hat_host.data_ptr(), x_host.data_ptr(), x_host.shape[0],
+                u_host.data_ptr(), grad_host.data_ptr() if grad_host is not None else 0)
+        _check(rc, "bspline_run_host" if wait else "bspline_run_host_async")
+
+    def wait(self):
+        """Wait for everything queued on the plan (bspline_wait)."""
+        _check(bspline_wait(self.handle), "bspline_wait")
 
 
 # ---- batches of independent fields (one CUDA graph launch) -------------------------

@@ -223,8 +223,11 @@ void free_plan(bspline_plan_s* p) {
     p->work.release();
     p->pws.release();
     if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->ev_sorted) cudaEventDestroy(p->ev_sorted);
+    for (cudaEvent_t ev : p->ev_copied)
+        if (ev) cudaEventDestroy(ev);
     p->host_uhat.release();
     p->host_coef.release();
     p->host_x.release();
@@ -240,6 +243,15 @@ int ensure_aux(bspline_plan_s* plan) {
     if (!plan->aux_stream) e = cudaStreamCreateWithFlags(&plan->aux_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !plan->ev_start) e = cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess && !plan->ev_sorted) e = cudaEventCreateWithFlags(&plan->ev_sorted, cudaEventDisableTiming);
+    return set_cuda_error(e);
+}
+
+// The copy stream and its events, created on first use.
+int ensure_copy(bspline_plan_s* plan) {
+    cudaError_t e = cudaSuccess;
+    if (!plan->copy_stream) e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t& ev : plan->ev_copied)
+        if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     return set_cuda_error(e);
 }
 
@@ -425,13 +437,15 @@ int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {
     return BSPLINE_OK;
 }
 
-// Copies and compute overlap on two streams: the positions go first on the
-// second stream and are sorted there while u_hat is copied component by
-// component on the plan's stream, each component transformed as soon as it
-// has arrived; the gather waits for the sort and the last component, then the
-// results are copied back.
-int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P, void* u_host,
-                     void* grad_host) {
+// Copies and compute overlap on three streams: the copy stream brings the
+// positions and then the three u_hat components in back to back, so the
+// host-to-device link never waits for a kernel; the second stream sorts the
+// positions as soon as they have arrived, and the plan's stream transforms
+// each component as soon as it has arrived; the gather waits for the sort
+// and the last component, then the results are copied back on the plan's
+// stream.  Returns once all of it is queued.
+int bspline_run_host_async(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P,
+                           void* u_host, void* grad_host) {
     if (!valid_plan(plan) || !u_hat_host || !u_host || (P > 0 && !x_host)) return BSPLINE_ERR_INVALID_ARG;
     if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
@@ -443,19 +457,26 @@ int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* 
     if ((rc = plan->host_x.grow(sizeof(double) * 3 * (size_t)(P ? P : 1)))) return rc;
     if ((rc = plan->host_u.grow(ob * 3 * (size_t)(P ? P : 1)))) return rc;
     if ((rc = plan->host_grad.grow(ob * 9 * (size_t)(P ? P : 1)))) return rc;
-    if ((rc = ensure_aux(plan))) return rc;
-    cudaStream_t st = plan->stream, aux = plan->aux_stream;
-    // the second stream starts after everything already queued on the plan's stream
+    if ((rc = ensure_aux(plan)) || (rc = ensure_copy(plan))) return rc;
+    cudaStream_t st = plan->stream, aux = plan->aux_stream, cp = plan->copy_stream;
+    // the other streams start after everything already queued on the plan's stream (which ends
+    // with the previous call's result copies, after every reader of the device buffers)
     cudaError_t e = cudaEventRecord(plan->ev_start, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, plan->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cp, plan->ev_start, 0);
     if (e == cudaSuccess && P)
-        e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, aux);
-    if (e != cudaSuccess) return set_cuda_error(e);
+        e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, cp);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_copied[0], cp);
     const size_t comp = uhat_bytes_of(plan) / 3;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
         e = cudaMemcpyAsync((char*)plan->host_uhat.ptr + c * comp, (const char*)u_hat_host + c * comp, comp,
-                            cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return set_cuda_error(e);
+                            cudaMemcpyHostToDevice, cp);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->ev_copied[1 + c], cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, plan->ev_copied[0], 0);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    for (int c = 0; c < 3; ++c) {
+        if ((e = cudaStreamWaitEvent(st, plan->ev_copied[1 + c], 0)) != cudaSuccess) return set_cuda_error(e);
         if ((rc = launch_coeffs_range(plan, plan->host_uhat.ptr, plan->host_coef.ptr, c, c + 1))) return rc;
     }
     if (P) {
@@ -468,9 +489,27 @@ int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* 
             e = cudaMemcpyAsync(grad_host, plan->host_grad.ptr, ob * 9 * P, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
-    e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(aux);
+    return BSPLINE_OK;
+}
+
+int bspline_wait(bspline_plan_t plan) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e == cudaSuccess && plan->aux_stream) e = cudaStreamSynchronize(plan->aux_stream);
+    if (e == cudaSuccess && plan->copy_stream) e = cudaStreamSynchronize(plan->copy_stream);
     return set_cuda_error(e);
+}
+
+int bspline_run_host(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P, void* u_host,
+                     void* grad_host) {
+    int rc = bspline_run_host_async(plan, u_hat_host, x_host, P, u_host, grad_host);
+    if (rc != BSPLINE_OK) {
+        if (valid_plan(plan)) bspline_wait(plan);       // let whatever was queued finish before reporting
+        return rc;
+    }
+    return bspline_wait(plan);
 }
 
 int bspline_destroy(bspline_plan_t plan) {

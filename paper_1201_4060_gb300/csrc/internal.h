@@ -89,10 +89,13 @@ struct bspline_plan_s {
     unsigned long long* d_status = nullptr;
     int sms = 1;            // streaming multiprocessors of the plan's device
     int test_hooks = 0;     // BSPLINE_TEST_* flags
-    // Buffers, second stream and events of bspline_run_host.
+    // Buffers, second stream and events of bspline_run_host (and the second
+    // stream of bspline_eval); the copy stream and its events feed the
+    // host-to-device copies of bspline_run_host.
     bs::DeviceBuffer host_uhat, host_coef, host_x, host_u, host_grad;
-    cudaStream_t aux_stream = nullptr;
+    cudaStream_t aux_stream = nullptr, copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_sorted = nullptr;
+    cudaEvent_t ev_copied[4] = {};      // positions, then the three u_hat components, arrived
     // Per-kernel timing (bspline_plan_set_timing): event pairs recorded on the
     // plan's stream around each launch, resolved by bspline_stage_times.
     bool timing = false;

@@ -64,6 +64,8 @@ def test_null_plan_is_rejected_everywhere():
     assert B.bspline_uhat_bytes(0)[0] == B.ERR_INVALID_ARG
     assert B.bspline_status(0)[0] == B.ERR_INVALID_ARG
     assert B.bspline_run_host(0, 16, 16, 1, 16, 16) == B.ERR_INVALID_ARG
+    assert B.bspline_run_host_async(0, 16, 16, 1, 16, 16) == B.ERR_INVALID_ARG
+    assert B.bspline_wait(0) == B.ERR_INVALID_ARG
     assert B.bspline_spread_adjoint(0, 0, 0, 0, 0, 0, 0, 0, 0) == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_timing(0, 1) == B.ERR_INVALID_ARG
     assert B.bspline_stage_times(0)[0] == B.ERR_INVALID_ARG

@@ -315,6 +315,33 @@ def test_run_host_matches_device_path(B):
     assert np.array_equal(uo2.numpy()[ok], u[ok])
 
 
+def test_run_host_async_on_alternating_plans(B):
+    """Steps queued with bspline_run_host_async on two plans (two streams) and collected with
+    bspline_wait give the synchronous results; a plan that has run nothing waits at once."""
+    N, order, P = 32, 6, 5000
+    fields = [synth.kolmogorov_field(N, seed=30 + k).dense().astype(np.complex64) for k in range(4)]
+    xs = [synth.clustered_particles(P, seed=40 + k) for k in range(4)]
+    ref = []
+    for k in range(4):
+        _, u, g, _ = gpu_path(B, fields[k], xs[k], N, order, "f32")
+        ref.append((u, g))
+    plans = [B.Plan(N, order, "f32") for _ in range(2)]
+    plans[1].wait()
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    uh = [torch.from_numpy(f).pin_memory() for f in fields]
+    xh = [torch.from_numpy(x).pin_memory() for x in xs]
+    outs = [(torch.full((P, 3), np.nan, dtype=torch.float32).pin_memory(),
+             torch.full((P, 3, 3), np.nan, dtype=torch.float32).pin_memory()) for _ in range(4)]
+    for k in range(4):
+        i = k % 2
+        plans[i].wait()
+        plans[i].run_host(uh[k], xh[k], *outs[k], stream=streams[i], wait=False)
+    for p in plans:
+        p.wait()
+    for k in range(4):
+        assert np.array_equal(outs[k][0].numpy(), ref[k][0]) and np.array_equal(outs[k][1].numpy(), ref[k][1])
+
+
 @pytest.mark.parametrize("dtype,N,order", [("f32", 48, 6), ("f64", 32, 5), ("bf16", 64, 4)])
 def test_eval_matches_coeffs_then_interp(B, dtype, N, order):
     """bspline_eval (sort on the second stream, overlapping the transform) gives the
