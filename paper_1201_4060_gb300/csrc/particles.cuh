@@ -537,8 +537,10 @@ gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, doubl
 // One CTA per work item: item i is chunk i - chunk[b] of the brick b with
 // chunk[b] <= i < chunk[b + 1] (at most kChunk particles); the grid is an
 // upper bound on the number of items and surplus CTAs return at once.
+// Two CTAs per SM (80 registers): orders 7 and 8 would otherwise take 84 and
+// 102 registers and run one CTA per SM, 22 % and 16 % slower at 256^3.
 template <int ORD, typename CT, typename TR, bool GRAD>
-__global__ void __launch_bounds__(kGatherThreads)
+__global__ void __launch_bounds__(kGatherThreads, 2)
 gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __restrict__ out_u,
            float* __restrict__ out_grad, float dscale) {
     using S = Shape<CT, ORD>;
