@@ -51,6 +51,29 @@ def peaks() -> dict:
 _OVERRIDE = {}
 
 
+# ----------------------------------------------------------------------------- ranks (N > 1)
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: the job is done when every replica is (all_reduce MAX)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, P: int, steps: int, ms_total: float) -> float:
+    """Whole-job particles/s: every rank evaluates its own P particles per step (weak scaling)."""
+    return world * P * steps / (ms_total / 1e3)
+
+
+def rank_particle_seed(wl: dict, rank: int) -> int:
+    """Each rank draws its own particle shard from the same recipe."""
+    return wl["particle_seed"] + rank
+
+
 def workload():
     """The benchmark workload; --N/--P shrink it for profiling captures only (not bench values)."""
     from paper_1201_4060_gb300 import synth
@@ -253,7 +276,7 @@ def run_ours(args):
     wl = workload()
     N, order, P = wl["N"], wl["order"], wl["P"]
     F = synth.kolmogorov_field(N, seed=wl["field_seed"])
-    xs = synth.clustered_particles(P, seed=wl["particle_seed"] + rank)
+    xs = synth.clustered_particles(P, seed=rank_particle_seed(wl, rank))
     x = torch.from_numpy(xs).to(device)
 
     # ---- headline: FP32 coefficients, whole path, timed region of exactly K steps
@@ -300,11 +323,8 @@ def run_ours(args):
     stages = plan.stage_times()
     nonfinite = plan.status()
     plan.set_timing(False)
-    t_max = torch.tensor([ms_total], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_total = float(t_max.item())
-    value = world * P * args.steps / (ms_total / 1e3)
+    ms_total = max_over_ranks(ms_total, world, device)
+    value = job_throughput(world, P, args.steps, ms_total)
     launches = sum(n for (_, n) in stages.values())
 
     # ---- roofline of the dominant kernel (largest share of the timed region)
