@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particles/s for u+grad-u (quintic B-spline, 512^3), FP32 vs FP64 form, % HBM peak"
 UNIT = "particles/s"
 WORKLOAD_NAME = "throughput512"
-STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather"]
+STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "gather_direct"]
 
 
 def peaks() -> dict:
@@ -176,11 +176,13 @@ def algorithmic_bytes(stage: str, N: int, P: int, dtype: str, order: int = 6) ->
         "scan": 4 * 4 * (nb + 1),
         "scatter": P * 24 + P * (rec + 4),       # positions in again; sorted record and original index out
         "gather": coef + P * (rec + 4) + P * 12 * outb,    # coefficients once, sorted records, u and grad out
+        "gather_direct": 4 * nb,                 # per-brick counts (its particles are counted in "gather")
     }[stage]
 
 
 def kernel_source_sha(stage: str) -> str:
-    files = {"gather": ["particles.cuh"], "bin": ["particles.cu"], "scan": ["particles.cu"],
+    files = {"gather": ["particles.cuh"], "gather_direct": ["particles.cuh"], "bin": ["particles.cu"],
+             "scan": ["particles.cu"],
              "scatter": ["particles.cu"], "fft_x": ["fft.cu", "fft_core.cuh"],
              "fft_yz": ["fft.cu", "fft_core.cuh"]}[stage]
     h = hashlib.sha256()

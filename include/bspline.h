@@ -92,6 +92,33 @@ int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind);
 /* Bind the plan to a cudaStream_t (passed as void*; NULL = legacy stream). */
 int bspline_plan_set_stream(bspline_plan_t plan, void* stream);
 
+/* Gather split.  Particles are sorted by brick; a brick holding fewer than
+ * direct_below particles is evaluated by the direct gather (each particle's
+ * stencil read from global memory, a warp per brick), the others by the
+ * staged gather (the brick's coefficient tile staged in shared memory, a CTA
+ * per up to 2048 of its particles).  Both give the same results bit for bit;
+ * only the time differs: a staged brick carries a fixed cost of a few
+ * microseconds of dependent latency, which a handful of particles does not
+ * repay.  0 stages every brick.  FP32 and BF16 plans (FP64 plans always
+ * stage).  BSPLINE_GATHER_SPLIT_AUTO (the default) takes 32 for a call with
+ * fewer than 64 particles per brick on average and 0 otherwise;
+ * bspline_plan_autotune picks the split by timing. */
+#define BSPLINE_GATHER_SPLIT_AUTO 0xfffffffeu
+int bspline_plan_set_gather_split(bspline_plan_t plan, unsigned direct_below);
+
+/* Autotuner of the gather split: times bspline_interp of these P particles
+ * (device buffers as for bspline_interp, out_grad NULL for u only) with the
+ * split at 0, 8, 32, 128, 512 and "every brick direct", sets the fastest on
+ * the plan and returns it in *split_out and its time per call in *ms_out
+ * (either may be NULL).  out_u and out_grad are scratch: on return they
+ * hold the result of the last timed call.  If the environment variable
+ * BSPLINE_AUTOTUNE_CACHE names a file, a choice recorded there for the same
+ * (GPU name, N, order, dtype, ceil(log2 P)) is applied without timing
+ * (*ms_out = 0), and a new choice is appended to it as one JSON line.
+ * Synchronises the plan's stream. */
+int bspline_plan_autotune(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, void* out_u,
+                          void* out_grad, unsigned* split_out, double* ms_out);
+
 /* Size in bytes of the coefficient buffer (3 N^3 elements of the dtype). */
 int bspline_coeffs_bytes(bspline_plan_t plan, size_t* bytes);
 
@@ -211,7 +238,8 @@ enum {
     BSPLINE_STAGE_SPREAD = 6,   /* adjoint: cotangents spread onto coefficients */
     BSPLINE_STAGE_GRAD_X = 7,   /* adjoint: position gradients */
     BSPLINE_STAGE_ADJ_FFT = 8,  /* adjoint: forward real transform + prefilter */
-    BSPLINE_NSTAGES = 9
+    BSPLINE_STAGE_GATHER_DIRECT = 9,   /* gather of the sparse bricks from global memory */
+    BSPLINE_NSTAGES = 10
 };
 int bspline_plan_set_timing(bspline_plan_t plan, int enable);
 int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);

@@ -30,6 +30,7 @@ NOALLOC_MAX_PARTICLES = 131072
 F64, F32, BF16 = 0, 1, 2
 PREFILTER_INTERP, PREFILTER_L2 = 0, 1
 INTERP_NO_GRAD = 0x1
+GATHER_SPLIT_AUTO = 0xFFFFFFFE
 
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 
@@ -72,6 +73,9 @@ def _load() -> ctypes.CDLL:
         "bspline_version": (ctypes.c_char_p, []),
         "bspline_plan_set_timing": (i32, [vp, i32]),
         "bspline_plan_set_test_hooks": (i32, [vp, i32]),
+        "bspline_plan_set_gather_split": (i32, [vp, ctypes.c_uint]),
+        "bspline_plan_autotune": (i32, [vp, vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_uint),
+                                        ctypes.POINTER(ctypes.c_double)]),
         "bspline_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
         "bspline_interp_noalloc": (i32, [vp, i32, i32, i32, ctypes.c_double, vp, i64, vp, vp, i32, vp]),
         "bspline_batch_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]),
@@ -187,8 +191,8 @@ def bspline_status_string(code: int) -> str:
     return status_string(code)
 
 
-NSTAGES = 9
-STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "spread", "grad_x", "adj_fft"]
+NSTAGES = 10
+STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "spread", "grad_x", "adj_fft", "gather_direct"]
 TEST_DROP_TRANSFORM_SIGNALS = 0x1
 
 
@@ -366,6 +370,28 @@ class Plan:
         if rc not in (OK, ERR_NONFINITE_INPUT):
             raise BSplineError(rc, "bspline_status")
         return n
+
+    def set_gather_split(self, direct_below: int) -> None:
+        """Bricks with fewer particles than this use the direct gather (bspline_plan_set_gather_split)."""
+        _check(_load().bspline_plan_set_gather_split(self.handle, int(direct_below)), "bspline_plan_set_gather_split")
+
+    def autotune(self, coef, x, out_u=None, out_grad=None, grad: bool = True):
+        """Pick the gather split for these particles by timing (bspline_plan_autotune); returns (split, ms)."""
+        import torch
+        if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
+        P = x.shape[0]
+        if out_u is None:
+            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=x.device)
+        if grad and out_grad is None:
+            out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=x.device)
+        self._stream(None)
+        split = ctypes.c_uint()
+        ms = ctypes.c_double()
+        rc = _load().bspline_plan_autotune(self.handle, coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
+                                          out_grad.data_ptr() if grad else 0, ctypes.byref(split), ctypes.byref(ms))
+        _check(rc, "bspline_plan_autotune")
+        return split.value, ms.value
 
     def set_test_hooks(self, hooks: int) -> None:
         _check(bspline_plan_set_test_hooks(self.handle, hooks), "bspline_plan_set_test_hooks")

@@ -12,6 +12,7 @@
 // The FP64 values are rounded to FP32 once for the FP32/BF16 plans.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -429,6 +430,91 @@ int bspline_status(bspline_plan_t plan, int64_t* nonfinite) {
     if (nonfinite) *nonfinite = (int64_t)h[0];
     if (h[1]) return BSPLINE_ERR_TIMEOUT;
     return h[0] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
+}
+
+int bspline_plan_set_gather_split(bspline_plan_t plan, unsigned direct_below) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    plan->direct_below = direct_below;
+    return BSPLINE_OK;
+}
+
+int bspline_plan_autotune(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, void* out_u,
+                          void* out_grad, unsigned* split_out, double* ms_out) {
+    if (!valid_plan(plan) || P <= 0 || P > 0x7fffffffLL || !coeffs || !x || !out_u) return BSPLINE_ERR_INVALID_ARG;
+    const size_t ob = out_bytes(plan->dtype);
+    if (!aligned(coeffs, 16) || !aligned(x, 8) || !aligned(out_u, ob) || (out_grad && !aligned(out_grad, ob)))
+        return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    const int flags = out_grad ? 0 : BSPLINE_INTERP_NO_GRAD;
+    // cache key: GPU name, grid, order, dtype, particle count rounded up to a power of two
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, plan->device);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    int plog2 = 0;
+    while (plog2 < 62 && (1LL << plog2) < (long long)P) ++plog2;
+    static const char* kDtype[] = {"f64", "f32", "bf16"};
+    char key[384];
+    std::snprintf(key, sizeof key, "%s|N%d|o%d|%s|p2^%d", prop.name, plan->N, plan->order, kDtype[plan->dtype], plog2);
+    const char* path = std::getenv("BSPLINE_AUTOTUNE_CACHE");
+    if (path && *path) {
+        if (FILE* f = std::fopen(path, "r")) {
+            char line[1024];
+            char want[448];
+            std::snprintf(want, sizeof want, "\"key\": \"%s\"", key);
+            bool found = false;
+            unsigned split = 0;
+            while (std::fgets(line, sizeof line, f)) {
+                const char* k = std::strstr(line, want);
+                const char* s = std::strstr(line, "\"direct_below\": ");
+                if (k && s && std::sscanf(s + 16, "%u", &split) == 1) found = true;   // the last match wins
+            }
+            std::fclose(f);
+            if (found) {
+                plan->direct_below = split;
+                if (split_out) *split_out = split;
+                if (ms_out) *ms_out = 0.0;
+                return BSPLINE_OK;
+            }
+        }
+    }
+    static const unsigned kSplits[] = {0u, 8u, 32u, 128u, 512u, 0xffffffffu};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int rc = set_cuda_error(e);
+    unsigned best = plan->direct_below;
+    float best_ms = -1.f;
+    for (unsigned split : kSplits) {
+        if (rc) break;
+        plan->direct_below = split;
+        if ((rc = launch_interp(plan, coeffs, x, P, out_u, out_grad, flags))) break;     // warm-up
+        if ((e = cudaEventRecord(e0, plan->stream)) != cudaSuccess) { rc = set_cuda_error(e); break; }
+        for (int r = 0; r < 3 && rc == BSPLINE_OK; ++r) rc = launch_interp(plan, coeffs, x, P, out_u, out_grad, flags);
+        if (rc) break;
+        float ms = 0.f;
+        e = cudaEventRecord(e1, plan->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if ((rc = set_cuda_error(e))) break;
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = split;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    plan->direct_below = best;
+    if (rc) return rc;
+    if (split_out) *split_out = best;
+    if (ms_out) *ms_out = best_ms / 3.0;
+    if (path && *path) {
+        if (FILE* f = std::fopen(path, "a")) {
+            std::fprintf(f, "{\"key\": \"%s\", \"direct_below\": %u, \"ms\": %.4f}\n", key, best, best_ms / 3.0);
+            std::fclose(f);
+        }
+    }
+    return BSPLINE_OK;
 }
 
 int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {

@@ -89,6 +89,7 @@ struct bspline_plan_s {
     unsigned long long* d_status = nullptr;
     int sms = 1;            // streaming multiprocessors of the plan's device
     int test_hooks = 0;     // BSPLINE_TEST_* flags
+    unsigned direct_below = BSPLINE_GATHER_SPLIT_AUTO;   // gather split (bspline_plan_set_gather_split)
     // Buffers, second stream and events of bspline_run_host (and the second
     // stream of bspline_eval); the copy stream and its events feed the
     // host-to-device copies of bspline_run_host.

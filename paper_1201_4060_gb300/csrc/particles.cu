@@ -184,7 +184,7 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
 // item back to its brick.
 __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
                                                     unsigned* __restrict__ cursor, unsigned* __restrict__ chunk,
-                                                    unsigned* __restrict__ item, unsigned NB) {
+                                                    unsigned* __restrict__ item, unsigned NB, unsigned below) {
     __shared__ unsigned ws[32], wc[32];
     const unsigned n = NB + 1;
     const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
     for (unsigned b0 = 0; b0 < n; b0 += 1024) {
         const unsigned i = b0 + t;
         const unsigned ci = i < n ? count[i] : 0u;
-        const unsigned nc = i < NB ? (ci + kChunk - 1) / kChunk : 0u;
+        const unsigned nc = (i < NB && ci >= below) ? (ci + kChunk - 1) / kChunk : 0u;   // below: direct gather
         unsigned v = ci, vc = nc;
 #pragma unroll
         for (unsigned d = 1; d < 32; d <<= 1) {
@@ -300,6 +300,21 @@ int dispatch_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g,
     return BSPLINE_ERR_UNSUPPORTED_ORDER;
 }
 
+template <typename CT, typename AT, typename TR>
+int dispatch_direct(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u, void* out_grad,
+                    bool grad, unsigned below) {
+    switch (p->order) {
+        case 2: return run_gather_direct<2, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+        case 3: return run_gather_direct<3, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+        case 4: return run_gather_direct<4, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+        case 5: return run_gather_direct<5, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+        case 6: return run_gather_direct<6, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+        case 7: return run_gather_direct<7, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+        case 8: return run_gather_direct<8, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
+    }
+    return BSPLINE_ERR_UNSUPPORTED_ORDER;
+}
+
 inline unsigned grid_for(long long P, int threads) {
     long long g = (P + threads - 1) / threads;
     if (g > (1LL << 30)) g = 1LL << 30;
@@ -330,13 +345,17 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
+    // bricks with fewer particles than this go to the direct gather (FP32 accumulation only)
+    unsigned below = p->direct_below;
+    if (below == BSPLINE_GATHER_SPLIT_AUTO) below = P < 64LL * NB ? 32u : 0u;
+    if (sizeof(AT) == 8) below = 0u;
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
         bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, below);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
@@ -351,6 +370,11 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     {
         StageTimer tm(p, BSPLINE_STAGE_GATHER);
         rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+    }
+    if (rc) return rc;
+    if (below > 0) {
+        StageTimer tm(p, BSPLINE_STAGE_GATHER_DIRECT);
+        rc = dispatch_direct<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, below);
     }
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
@@ -371,7 +395,7 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status, NB < kAggregateBricks);
-    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
+    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
                                                              NB < kAggregateBricks);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
@@ -418,7 +442,7 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB);
+        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);

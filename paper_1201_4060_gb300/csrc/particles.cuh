@@ -335,154 +335,99 @@ __device__ __forceinline__ void eval_particle(const A* __restrict__ base, A tx, 
     }
 }
 
-// FP32 version of eval_particle with packed two-way FMAs (fma.rn.f32x2):
+// Packed two-way FP32 contraction (fma.rn.f32x2) of one component:
 // adjacent y-lines jy, jy + 1 are contracted along z together (their loads
 // form the pair, the z weight is duplicated), and their y-sums are kept as
 // (even, odd) pairs that are added at the end of each x-plane.  Same
 // arithmetic per term as eval_particle; the sums are grouped by parity of jy.
-template <int ORD, bool GRAD, int SX, int SY, int TS>
-__device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base, float tx, float ty, float tz,
-                                                 float dscale, float* __restrict__ out_u,
-                                                 float* __restrict__ out_grad) {
-    constexpr int NP = ORD / 2;                       // pairs of y-lines
-    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
-    bspline_weights<ORD, float>(tx, wx, dwx);
-    bspline_weights<ORD, float>(ty, wy, dwy);
-    bspline_weights<ORD, float>(tz, wz, dwz);
+// ld(jx, jy, jz) gives the coefficient at stencil node (jx, jy, jz): the
+// staged gather reads its shared-memory tile, the direct gather global
+// memory, with the same arithmetic in the same order, so the two agree bit
+// for bit.
+template <int ORD> struct PairWeights {
+    static constexpr int NP = ORD / 2;                // pairs of y-lines
     float2 wz2[ORD], dwz2[ORD], wyp[NP > 0 ? NP : 1], dwyp[NP > 0 ? NP : 1];
+    __device__ __forceinline__ PairWeights(const float (&wz)[ORD], const float (&dwz)[ORD], const float (&wy)[ORD],
+                                           const float (&dwy)[ORD]) {
 #pragma unroll
-    for (int j = 0; j < ORD; ++j) {
-        wz2[j] = make_float2(wz[j], wz[j]);
-        dwz2[j] = make_float2(dwz[j], dwz[j]);
+        for (int j = 0; j < ORD; ++j) {
+            wz2[j] = make_float2(wz[j], wz[j]);
+            dwz2[j] = make_float2(dwz[j], dwz[j]);
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            wyp[p] = make_float2(wy[2 * p], wy[2 * p + 1]);
+            dwyp[p] = make_float2(dwy[2 * p], dwy[2 * p + 1]);
+        }
     }
+};
+
+// One x-row of the contraction: ldr(jy, jz) gives the coefficient at
+// (jy, jz) of the row; returns the row's sums s00 = sum_y wy sum_z wz c, s10
+// with dwy, s01 with dwz.
+template <int ORD, bool GRAD, typename LDR>
+__device__ __forceinline__ void row_x2(LDR ldr, const PairWeights<ORD>& pw, const float (&wy)[ORD],
+                                       const float (&dwy)[ORD], const float (&wz)[ORD], const float (&dwz)[ORD],
+                                       float* s00, float* s10, float* s01) {
+    constexpr int NP = ORD / 2;
+    float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        wyp[p] = make_float2(wy[2 * p], wy[2 * p + 1]);
-        dwyp[p] = make_float2(dwy[2 * p], dwy[2 * p + 1]);
-    }
+        float2 z0 = make_float2(0.f, 0.f), z1 = z0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float* tc = base + c * TS;
-        float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-        for (int jx = 0; jx < ORD; ++jx) {
-            float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const float* l0 = tc + jx * SX + 2 * p * SY;
-                const float* l1 = l0 + SY;
-                float2 z0 = make_float2(0.f, 0.f), z1 = z0;
-#pragma unroll
-                for (int jz = 0; jz < ORD; ++jz) {
-                    const float2 a = make_float2(l0[jz], l1[jz]);
-                    z0 = __ffma2_rn(wz2[jz], a, z0);
-                    if (GRAD) z1 = __ffma2_rn(dwz2[jz], a, z1);
-                }
-                y00 = __ffma2_rn(wyp[p], z0, y00);
-                if (GRAD) {
-                    y10 = __ffma2_rn(dwyp[p], z0, y10);
-                    y01 = __ffma2_rn(wyp[p], z1, y01);
-                }
-            }
-            if constexpr (ORD % 2 == 1) {               // the unpaired last line
-                const float* l = tc + jx * SX + (ORD - 1) * SY;
-                float z0 = 0.f, z1 = 0.f;
-#pragma unroll
-                for (int jz = 0; jz < ORD; ++jz) {
-                    z0 = fmaf(wz[jz], l[jz], z0);
-                    if (GRAD) z1 = fmaf(dwz[jz], l[jz], z1);
-                }
-                y00.x = fmaf(wy[ORD - 1], z0, y00.x);
-                if (GRAD) {
-                    y10.x = fmaf(dwy[ORD - 1], z0, y10.x);
-                    y01.x = fmaf(wy[ORD - 1], z1, y01.x);
-                }
-            }
-            const float s00 = y00.x + y00.y;
-            u = fmaf(wx[jx], s00, u);
-            if (GRAD) {
-                gx = fmaf(dwx[jx], s00, gx);
-                gy = fmaf(wx[jx], y10.x + y10.y, gy);
-                gz = fmaf(wx[jx], y01.x + y01.y, gz);
-            }
+        for (int jz = 0; jz < ORD; ++jz) {
+            const float2 a = make_float2(ldr(2 * p, jz), ldr(2 * p + 1, jz));
+            z0 = __ffma2_rn(pw.wz2[jz], a, z0);
+            if (GRAD) z1 = __ffma2_rn(pw.dwz2[jz], a, z1);
         }
-        out_u[c] = u;
+        y00 = __ffma2_rn(pw.wyp[p], z0, y00);
         if (GRAD) {
-            out_grad[3 * c + 0] = gx * dscale;
-            out_grad[3 * c + 1] = gy * dscale;
-            out_grad[3 * c + 2] = gz * dscale;
+            y10 = __ffma2_rn(pw.dwyp[p], z0, y10);
+            y01 = __ffma2_rn(pw.wyp[p], z1, y01);
         }
+    }
+    if constexpr (ORD % 2 == 1) {                   // the unpaired last line
+        float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+        for (int jz = 0; jz < ORD; ++jz) {
+            const float a = ldr(ORD - 1, jz);
+            z0 = fmaf(wz[jz], a, z0);
+            if (GRAD) z1 = fmaf(dwz[jz], a, z1);
+        }
+        y00.x = fmaf(wy[ORD - 1], z0, y00.x);
+        if (GRAD) {
+            y10.x = fmaf(dwy[ORD - 1], z0, y10.x);
+            y01.x = fmaf(wy[ORD - 1], z1, y01.x);
+        }
+    }
+    *s00 = y00.x + y00.y;
+    *s10 = y10.x + y10.y;
+    *s01 = y01.x + y01.y;
+}
+
+// Accumulation of one x-row's sums into u and the gradient.
+template <bool GRAD>
+__device__ __forceinline__ void add_row(float wxj, float dwxj, float s00, float s10, float s01, float* u, float* gx,
+                                        float* gy, float* gz) {
+    *u = fmaf(wxj, s00, *u);
+    if (GRAD) {
+        *gx = fmaf(dwxj, s00, *gx);
+        *gy = fmaf(wxj, s10, *gy);
+        *gz = fmaf(wxj, s01, *gz);
     }
 }
 
-// One component of eval_particle in FP32 with packed two-way FMAs
-// (fma.rn.f32x2): adjacent y-lines jy, jy + 1 are contracted along z together
-// (their loads form the pair, the z weight is duplicated), and their y-sums
-// are kept as (even, odd) pairs that are added at the end of each x-plane.
-// Same arithmetic per term as eval_particle; the sums are grouped by parity
-// of jy.  base points at the component's first stencil node.
-template <int ORD, bool GRAD, int SX, int SY>
-__device__ __forceinline__ void eval_component_x2(const float* __restrict__ base, float tx, float ty, float tz,
-                                                  float dscale, float* __restrict__ out_u,
-                                                  float* __restrict__ out_grad) {
-    constexpr int NP = ORD / 2;                       // pairs of y-lines
-    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
-    bspline_weights<ORD, float>(tx, wx, dwx);
-    bspline_weights<ORD, float>(ty, wy, dwy);
-    bspline_weights<ORD, float>(tz, wz, dwz);
-    float2 wz2[ORD], dwz2[ORD], wyp[NP > 0 ? NP : 1], dwyp[NP > 0 ? NP : 1];
-#pragma unroll
-    for (int j = 0; j < ORD; ++j) {
-        wz2[j] = make_float2(wz[j], wz[j]);
-        dwz2[j] = make_float2(dwz[j], dwz[j]);
-    }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        wyp[p] = make_float2(wy[2 * p], wy[2 * p + 1]);
-        dwyp[p] = make_float2(dwy[2 * p], dwy[2 * p + 1]);
-    }
+template <int ORD, bool GRAD, typename LD>
+__device__ __forceinline__ void contract_x2(LD ld, const PairWeights<ORD>& pw, const float (&wx)[ORD],
+                                            const float (&dwx)[ORD], const float (&wy)[ORD], const float (&dwy)[ORD],
+                                            const float (&wz)[ORD], const float (&dwz)[ORD], float dscale,
+                                            float* __restrict__ out_u, float* __restrict__ out_grad) {
     float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
     for (int jx = 0; jx < ORD; ++jx) {
-        float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const float* l0 = base + jx * SX + 2 * p * SY;
-            const float* l1 = l0 + SY;
-            float2 z0 = make_float2(0.f, 0.f), z1 = z0;
-#pragma unroll
-            for (int jz = 0; jz < ORD; ++jz) {
-                const float2 a = make_float2(l0[jz], l1[jz]);
-                z0 = __ffma2_rn(wz2[jz], a, z0);
-                if (GRAD) z1 = __ffma2_rn(dwz2[jz], a, z1);
-            }
-            y00 = __ffma2_rn(wyp[p], z0, y00);
-            if (GRAD) {
-                y10 = __ffma2_rn(dwyp[p], z0, y10);
-                y01 = __ffma2_rn(wyp[p], z1, y01);
-            }
-        }
-        if constexpr (ORD % 2 == 1) {               // the unpaired last line
-            const float* l = base + jx * SX + (ORD - 1) * SY;
-            float z0 = 0.f, z1 = 0.f;
-#pragma unroll
-            for (int jz = 0; jz < ORD; ++jz) {
-                z0 = fmaf(wz[jz], l[jz], z0);
-                if (GRAD) z1 = fmaf(dwz[jz], l[jz], z1);
-            }
-            y00.x = fmaf(wy[ORD - 1], z0, y00.x);
-            if (GRAD) {
-                y10.x = fmaf(dwy[ORD - 1], z0, y10.x);
-                y01.x = fmaf(wy[ORD - 1], z1, y01.x);
-            }
-        }
-        const float s00 = y00.x + y00.y;
-        u = fmaf(wx[jx], s00, u);
-        if (GRAD) {
-            gx = fmaf(dwx[jx], s00, gx);
-            gy = fmaf(wx[jx], y10.x + y10.y, gy);
-            gz = fmaf(wx[jx], y01.x + y01.y, gz);
-        }
+        float s00, s10, s01;
+        row_x2<ORD, GRAD>([&](int jy, int jz) { return ld(jx, jy, jz); }, pw, wy, dwy, wz, dwz, &s00, &s10, &s01);
+        add_row<GRAD>(wx[jx], dwx[jx], s00, s10, s01, &u, &gx, &gy, &gz);
     }
     *out_u = u;
     if (GRAD) {
@@ -490,6 +435,38 @@ __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base
         out_grad[1] = gy * dscale;
         out_grad[2] = gz * dscale;
     }
+}
+
+// All three components of one particle from the staged tile (weights once).
+template <int ORD, bool GRAD, int SX, int SY, int TS>
+__device__ __forceinline__ void eval_particle_x2(const float* __restrict__ base, float tx, float ty, float tz,
+                                                 float dscale, float* __restrict__ out_u,
+                                                 float* __restrict__ out_grad) {
+    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+    bspline_weights<ORD, float>(tx, wx, dwx);
+    bspline_weights<ORD, float>(ty, wy, dwy);
+    bspline_weights<ORD, float>(tz, wz, dwz);
+    const PairWeights<ORD> pw(wz, dwz, wy, dwy);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float* tc = base + c * TS;
+        contract_x2<ORD, GRAD>([&](int jx, int jy, int jz) { return tc[jx * SX + jy * SY + jz]; }, pw, wx, dwx, wy,
+                               dwy, wz, dwz, dscale, &out_u[c], &out_grad[3 * c]);
+    }
+}
+
+// One component of eval_particle_x2; base points at the component's first stencil node.
+template <int ORD, bool GRAD, int SX, int SY>
+__device__ __forceinline__ void eval_component_x2(const float* __restrict__ base, float tx, float ty, float tz,
+                                                  float dscale, float* __restrict__ out_u,
+                                                  float* __restrict__ out_grad) {
+    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+    bspline_weights<ORD, float>(tx, wx, dwx);
+    bspline_weights<ORD, float>(ty, wy, dwy);
+    bspline_weights<ORD, float>(tz, wz, dwz);
+    const PairWeights<ORD> pw(wz, dwz, wy, dwy);
+    contract_x2<ORD, GRAD>([&](int jx, int jy, int jz) { return base[jx * SX + jy * SY + jz]; }, pw, wx, dwx, wy,
+                           dwy, wz, dwz, dscale, out_u, out_grad);
 }
 
 // FP64: one thread per particle (the FP64 pipe, not shared memory, bounds it).
@@ -689,6 +666,66 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     }
 }
 
+// Direct gather for sparse bricks: a warp per brick holding fewer than
+// `below` particles (and at least one) evaluates them straight from the
+// coefficient array, one lane per particle.  A staged work item costs a few
+// microseconds of dependent latency (records, bucketing, the tile copy)
+// whatever its particle count, so for a handful of particles reading the
+// stencils from global memory (through L1, where a brick's particles share
+// rows) is far cheaper.  Same contraction (contract_x2) as the staged gather:
+// the results are the same bits.  The scan gives such bricks no staged items.
+template <int ORD, typename CT, typename TR, bool GRAD>
+__global__ void __launch_bounds__(256)
+gather_direct(const CT* __restrict__ coef, int N, unsigned NB, Ws<TR> w, unsigned below, float* __restrict__ out_u,
+              float* __restrict__ out_grad, float dscale) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const size_t NN = (size_t)N * N;
+    for (unsigned b = wid; b < NB; b += nw) {
+        const unsigned n = w.count[b];
+        if (n == 0 || n >= below) continue;
+        const unsigned beg = w.offset[b];
+        for (unsigned k = lane; k < n; k += 32u) {
+            const Rec<TR> rc = w.s_rec[beg + k];
+            const int ax = (int)(rc.cell >> (2 * kAnchorBits));
+            const int ay = (int)((rc.cell >> kAnchorBits) & 1023u);
+            const int az = (int)(rc.cell & 1023u);
+            float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+            bspline_weights<ORD, float>((float)rc.t[0], wx, dwx);
+            bspline_weights<ORD, float>((float)rc.t[1], wy, dwy);
+            bspline_weights<ORD, float>((float)rc.t[2], wz, dwz);
+            const PairWeights<ORD> pw(wz, dwz, wy, dwy);
+            int yo[ORD], zo[ORD];
+#pragma unroll
+            for (int j = 0; j < ORD; ++j) {
+                yo[j] = wrap_index(ay + j, N) * N;
+                zo[j] = wrap_index(az + j, N);
+            }
+            const size_t idx = rc.idx;
+#pragma unroll 1
+            for (int c = 0; c < 3; ++c) {
+                const CT* cb = coef + (size_t)c * N * NN;
+                float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                // the x-rows in a rolled loop (unrolled, the 3 ORD^3 global loads would all be hoisted)
+#pragma unroll 1
+                for (int jx = 0; jx < ORD; ++jx) {
+                    const CT* row = cb + (size_t)wrap_index(ax + jx, N) * NN;
+                    float s00, s10, s01;
+                    row_x2<ORD, GRAD>([&](int jy, int jz) { return widen<CT>(row[yo[jy] + zo[jz]]); }, pw, wy, dwy, wz,
+                                      dwz, &s00, &s10, &s01);
+                    add_row<GRAD>(wx[jx], dwx[jx], s00, s10, s01, &u, &gx, &gy, &gz);
+                }
+                out_u[3 * idx + c] = u;
+                if (GRAD) {
+                    out_grad[9 * idx + 3 * c + 0] = gx * dscale;
+                    out_grad[9 * idx + 3 * c + 1] = gy * dscale;
+                    out_grad[9 * idx + 3 * c + 2] = gz * dscale;
+                }
+            }
+        }
+    }
+}
+
 template <typename K> int set_smem(K kernel, size_t bytes) {
     if (bytes > 32 * 1024) {           // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -720,14 +757,37 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, voi
     return BSPLINE_OK;
 }
 
+// The direct gather of the bricks below the plan's split (FP32 accumulation only).
+template <int ORD, typename CT, typename AT, typename TR>
+int run_gather_direct(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u, void* out_grad,
+                      bool grad, unsigned below) {
+    if constexpr (sizeof(AT) == 8) {
+        return BSPLINE_OK;
+    } else {
+        if (below == 0) return BSPLINE_OK;
+        const unsigned NB = g.NB;
+        const float dscale = (float)((double)p->N / p->L);
+        auto k = grad ? gather_direct<ORD, CT, TR, true> : gather_direct<ORD, CT, TR, false>;
+        const unsigned blocks = (NB + 7u) / 8u;          // one warp per brick
+        k<<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, NB, w, below, (float*)out_u,
+                                         grad ? (float*)out_grad : nullptr, dscale);
+        return BSPLINE_OK;
+    }
+}
+
 }  // namespace gather_impl
 
 #define BS_GATHER_EXTERN(ORD, CT, AT, TR)                                                                 \
     extern template int gather_impl::run_gather<ORD, CT, AT, TR>(bspline_plan_s*, const void*,               \
                                                                   gather_impl::Ws<TR>, BrickGrid, void*,     \
-                                                                  void*, bool);
+                                                                  void*, bool);                              \
+    extern template int gather_impl::run_gather_direct<ORD, CT, AT, TR>(                                     \
+        bspline_plan_s*, const void*, gather_impl::Ws<TR>, BrickGrid, void*, void*, bool, unsigned);
 #define BS_GATHER_INSTANTIATE(ORD, CT, AT, TR)                                                          \
     template int gather_impl::run_gather<ORD, CT, AT, TR>(bspline_plan_s*, const void*, gather_impl::Ws<TR>, \
-                                                           BrickGrid, void*, void*, bool);
+                                                           BrickGrid, void*, void*, bool);                  \
+    template int gather_impl::run_gather_direct<ORD, CT, AT, TR>(bspline_plan_s*, const void*,               \
+                                                                  gather_impl::Ws<TR>, BrickGrid, void*,     \
+                                                                  void*, bool, unsigned);
 
 }  // namespace bs

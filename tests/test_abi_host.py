@@ -66,6 +66,8 @@ def test_null_plan_is_rejected_everywhere():
     assert B.bspline_run_host(0, 16, 16, 1, 16, 16) == B.ERR_INVALID_ARG
     assert B.bspline_run_host_async(0, 16, 16, 1, 16, 16) == B.ERR_INVALID_ARG
     assert B.bspline_wait(0) == B.ERR_INVALID_ARG
+    assert B.lib().bspline_plan_set_gather_split(None, 8) == B.ERR_INVALID_ARG
+    assert B.lib().bspline_plan_autotune(None, None, None, 10, None, None, None, None) == B.ERR_INVALID_ARG
     assert B.bspline_spread_adjoint(0, 0, 0, 0, 0, 0, 0, 0, 0) == B.ERR_INVALID_ARG
     assert B.bspline_plan_set_timing(0, 1) == B.ERR_INVALID_ARG
     assert B.bspline_stage_times(0)[0] == B.ERR_INVALID_ARG

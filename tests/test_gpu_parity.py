@@ -392,6 +392,65 @@ def test_eval_rejects_bad_arguments(B):
     assert B.bspline_eval(h, p, q, q, 10, q, q, 0x80) == B.ERR_INVALID_ARG       # unknown flag
 
 
+@pytest.mark.parametrize("dtype,N,order", [("f32", 16, 4), ("f32", 32, 6), ("f32", 48, 3), ("f32", 32, 8),
+                                           ("bf16", 32, 5), ("bf16", 16, 2)])
+def test_direct_and_staged_gathers_agree_bit_for_bit(B, dtype, N, order):
+    """The gather split only moves bricks between the staged gather (tile in shared memory) and the
+    direct one (stencils from global memory): same bits for every split, positions on the periodic
+    seams included; and the result holds against the oracle."""
+    half = synth.kolmogorov_field(N, seed=50 + order).dense()
+    rng = np.random.default_rng(order)
+    h = L / N
+    x = np.concatenate([
+        synth.uniform_particles(300, seed=order),                              # sparse bricks
+        np.array([2.5, 1.5, 3.5]) * h * 4 + rng.uniform(0, 2 * h, (700, 3)),  # one dense clump
+        np.column_stack([rng.uniform(0, L, 64), rng.uniform(0, L, 64),          # near the z, y and x seams
+                         L - rng.uniform(0, 3 * h, 64)]),
+        np.column_stack([L - rng.uniform(0, 3 * h, 64), L - rng.uniform(0, 3 * h, 64),
+                         rng.uniform(0, L, 64)]),
+    ])
+    plan = B.Plan(N, order, dtype)
+    uh = torch.from_numpy(half).to(plan.uhat_dtype).cuda()
+    coef = plan.coeffs(uh)
+    xt = torch.from_numpy(x).cuda()
+    outs = []
+    for split in (0, 8, 100, 2 ** 32 - 1, B.GATHER_SPLIT_AUTO):
+        plan.set_gather_split(split)
+        u, g = plan.interp(coef, xt)
+        outs.append((u.cpu().numpy(), g.cpu().numpy()))
+    for u, g in outs[1:]:
+        assert np.array_equal(u, outs[0][0]) and np.array_equal(g, outs[0][1])
+    plan.set_gather_split(2 ** 32 - 1)
+    u, g = plan.interp(coef, xt, grad=True)
+    u1 = plan.interp(coef, xt, grad=False)
+    assert np.array_equal(u1.cpu().numpy(), outs[0][0])
+    tol = TOL32 if dtype == "f32" else TOL16
+    ru, rg = O.interpolate(rounded_input(half, "f32"), x, order)
+    assert normwise(outs[0][0], ru) < tol["u"] and normwise(outs[0][1], rg) < tol["grad"]
+
+
+def test_gather_autotune_and_its_cache(B, tmp_path, monkeypatch):
+    N, order, P = 32, 6, 4000
+    half = synth.kolmogorov_field(N, seed=60).dense()
+    x = torch.from_numpy(synth.uniform_particles(P, seed=61)).cuda()
+    cache = tmp_path / "autotune.jsonl"
+    monkeypatch.setenv("BSPLINE_AUTOTUNE_CACHE", str(cache))
+    plan = B.Plan(N, order, "f32")
+    coef = plan.coeffs(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
+    split, ms = plan.autotune(coef, x)
+    assert split in (0, 8, 32, 128, 512, 2 ** 32 - 1) and ms > 0
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and f'"direct_below": {split}' in lines[0] and "|N32|o6|f32|p2^12" in lines[0]
+    u_tuned, g_tuned = plan.interp(coef, x)
+    plan2 = B.Plan(N, order, "f32")
+    split2, ms2 = plan2.autotune(coef, x)                # taken from the cache, no timing
+    assert split2 == split and ms2 == 0
+    assert len(cache.read_text().splitlines()) == 1
+    u2, g2 = plan2.interp(coef, x)
+    assert torch.equal(u_tuned, u2) and torch.equal(g_tuned, g2)
+    assert B.lib().bspline_plan_autotune(plan.handle, 0, 0, P, 0, 0, None, None) == B.ERR_INVALID_ARG
+
+
 def test_custom_domain_length(B):
     N, order, Lc = 16, 4, 3.0
     half = synth.kolmogorov_field(N, seed=12).dense()
