@@ -389,6 +389,7 @@ def run_ours(args):
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=12)
         out["adjoint"] = run_adjoint(B, device)
         out["batch"] = run_batch(B, device)
+        out["sparse"] = run_sparse(B, wl, F, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(samples=1 << 17)
     if world > 1:
@@ -459,6 +460,52 @@ def run_adjoint(B, device, steps=10, warmup=3):
            "hbm_frac": {s: abytes[s] / (stages[s] / 1e3) / 1e9 / pk["hbm_gbs"] for s in abytes if stages[s] > 0}}
     del uh, coef, x, gu, gg, g_coef, g_uh, g_x
     plan.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_sparse(B, wl, F, device, reps=5):
+    """The gather split on sparse particle sets (same 512^3 quintic field, FP32): per-call interpolation time
+    with every brick staged, with the automatic split, and with the split bspline_plan_autotune picks."""
+    import numpy as np
+    import torch
+    from paper_1201_4060_gb300 import synth
+    N, order = wl["N"], wl["order"]
+    plan = B.Plan(N, order, "f32")
+    coef = plan.coeffs(dense_field_on_gpu(F, plan.uhat_dtype, device))
+    out = {"workload": f"{N}^3 field of the headline, order {order}, f32 coefficients, uniform particles (seed 11)",
+           "cases": []}
+
+    def timed(x, u, g):
+        for _ in range(2):
+            plan.interp(coef, x, u, g)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan.interp(coef, x, u, g)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for lp in (18, 20):
+        P = 1 << lp
+        x = torch.from_numpy(synth.uniform_particles(P, seed=11)).to(device)
+        u = torch.empty((P, 3), device=device)
+        g = torch.empty((P, 3, 3), device=device)
+        plan.set_gather_split(0)
+        staged = timed(x, u, g)
+        plan.set_gather_split(B.GATHER_SPLIT_AUTO)
+        auto = timed(x, u, g)
+        split, _ = plan.autotune(coef, x, u, g)
+        tuned = timed(x, u, g)
+        out["cases"].append({"particles": P, "particles_per_brick": P / (-(-N // 16)) ** 2 / (-(-N // 12)),
+                             "interp_ms_all_staged": staged, "interp_ms_auto": auto, "autotuned_split": split,
+                             "interp_ms_autotuned": tuned, "particles_per_s_autotuned": P / (tuned / 1e3)})
+        del x, u, g
+    plan.close()
+    del coef
     torch.cuda.empty_cache()
     return out
 

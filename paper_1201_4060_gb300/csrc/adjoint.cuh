@@ -78,7 +78,7 @@ __device__ __forceinline__ bool item_range(const Ws<TR>& w, unsigned NB, unsigne
     const unsigned lo = w.item[item];
     *brick = lo;
     *beg = w.offset[lo] + (item - w.chunk[lo]) * kChunk;
-    *end = min(*beg + kChunk, w.offset[lo + 1]);
+    *end = min(*beg + kChunk, w.offset[lo] + w.count[lo]);
     return *beg < *end;
 }
 

@@ -177,68 +177,93 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
 }
 
 // ------------------------------------------------------------------ scan (single CTA)
-// Exclusive prefix sums over the NB + 1 bins (NB bricks, then the invalid
-// bin): offset[] of the counts (and a copy, cursor[], for the placement
-// pass), and chunk[] (bricks only) of the number of
-// gather work items per brick, ceil(count / kChunk); item[] maps each work
-// item back to its brick.
+// Places the bricks' segments in the sorted order and counts the staged
+// gather's work items.  Bricks holding at least `below` particles ("dense":
+// every brick when below = 0) come first, in brick order; the bricks below
+// it ("sparse", evaluated by the direct gather) follow, in brick order, so
+// the direct gather runs flat over one contiguous range; the invalid bin NB
+// comes last.  Writes offset[b] (and its copy cursor[b] for the placement
+// pass), offset[NB] = the end of the valid particles, offset[NB + 1] = the
+// end of all, offset[NB + 2] = the start of the sparse range; chunk[] (dense
+// bricks only) the exclusive prefix sum of the work items, ceil(count /
+// kChunk), chunk[NB] their total, and item[] each item's brick.
+__device__ __forceinline__ unsigned warp_inclusive(unsigned v, unsigned lane) {
+#pragma unroll
+    for (unsigned d = 1; d < 32; d <<= 1) {
+        const unsigned a = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += a;
+    }
+    return v;
+}
+
+// SPLIT = false (below = 0: every brick dense) skips the sparse bookkeeping.
+template <bool SPLIT>
 __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__ count, unsigned* __restrict__ offset,
                                                     unsigned* __restrict__ cursor, unsigned* __restrict__ chunk,
                                                     unsigned* __restrict__ item, unsigned NB, unsigned below) {
-    __shared__ unsigned ws[32], wc[32];
-    const unsigned n = NB + 1;
+    __shared__ unsigned wd[32], wsp[32], wc[32], s_total;
     const unsigned t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    unsigned carry = 0, carryc = 0;
-    // tiles of 1024 consecutive bins, one per thread: warp scans, then a scan of the 32 warp totals
-    for (unsigned b0 = 0; b0 < n; b0 += 1024) {
-        const unsigned i = b0 + t;
-        const unsigned ci = i < n ? count[i] : 0u;
-        const unsigned nc = (i < NB && ci >= below) ? (ci + kChunk - 1) / kChunk : 0u;   // below: direct gather
-        unsigned v = ci, vc = nc;
-#pragma unroll
-        for (unsigned d = 1; d < 32; d <<= 1) {
-            const unsigned a = __shfl_up_sync(0xffffffffu, v, d), ac = __shfl_up_sync(0xffffffffu, vc, d);
-            if (lane >= d) {
-                v += a;
-                vc += ac;
-            }
+    // total of the dense bricks (the start of the sparse range)
+    unsigned D = 0;
+    if constexpr (SPLIT) {
+        unsigned dsum = 0;
+        for (unsigned i = t; i < NB; i += 1024) {
+            const unsigned ci = count[i];
+            if (ci >= below) dsum += ci;
         }
+        dsum = __reduce_add_sync(0xffffffffu, dsum);
+        if (lane == 0) wd[warp] = dsum;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, wd[lane]);
+            if (lane == 0) s_total = v;
+        }
+        __syncthreads();
+        D = s_total;
+    }
+    unsigned cd = 0, cs = 0, cc = 0;                      // carries: dense, sparse, items
+    // tiles of 1024 consecutive bricks, one per thread: warp scans, then a scan of the 32 warp totals
+    for (unsigned b0 = 0; b0 < NB; b0 += 1024) {
+        const unsigned i = b0 + t;
+        const unsigned ci = i < NB ? count[i] : 0u;
+        const bool dense = !SPLIT || ci >= below;
+        const unsigned vd0 = dense ? ci : 0u, vs0 = dense ? 0u : ci;
+        const unsigned nc = dense ? (ci + kChunk - 1) / kChunk : 0u;
+        const unsigned vd = warp_inclusive(vd0, lane), vc = warp_inclusive(nc, lane);
+        const unsigned vs = SPLIT ? warp_inclusive(vs0, lane) : 0u;
         if (lane == 31) {
-            ws[warp] = v;
+            wd[warp] = vd;
+            wsp[warp] = vs;
             wc[warp] = vc;
         }
         __syncthreads();
         if (warp == 0) {
-            unsigned x = ws[lane], xc = wc[lane];
-#pragma unroll
-            for (unsigned d = 1; d < 32; d <<= 1) {
-                const unsigned a = __shfl_up_sync(0xffffffffu, x, d), ac = __shfl_up_sync(0xffffffffu, xc, d);
-                if (lane >= d) {
-                    x += a;
-                    xc += ac;
-                }
-            }
-            ws[lane] = x;
-            wc[lane] = xc;
+            wd[lane] = warp_inclusive(wd[lane], lane);
+            if (SPLIT) wsp[lane] = warp_inclusive(wsp[lane], lane);
+            wc[lane] = warp_inclusive(wc[lane], lane);
         }
         __syncthreads();
-        const unsigned ex = carry + (warp ? ws[warp - 1] : 0u) + v - ci;         // exclusive
-        const unsigned exc = carryc + (warp ? wc[warp - 1] : 0u) + vc - nc;
-        if (i < n) {
-            offset[i] = ex;
-            cursor[i] = ex;
-        }
+        const unsigned exd = cd + (warp ? wd[warp - 1] : 0u) + vd - vd0;          // exclusive
+        const unsigned exs = cs + (warp ? wsp[warp - 1] : 0u) + vs - vs0;
+        const unsigned exc = cc + (warp ? wc[warp - 1] : 0u) + vc - nc;
         if (i < NB) {
+            const unsigned o = dense ? exd : D + exs;
+            offset[i] = o;
+            cursor[i] = o;
             chunk[i] = exc;
             for (unsigned k = 0; k < nc; ++k) item[exc + k] = i;
         }
-        carry += ws[31];
-        carryc += wc[31];
+        cd += wd[31];
+        cs += wsp[31];
+        cc += wc[31];
         __syncthreads();                                  // the totals are read before the next tile
     }
     if (t == 0) {
-        offset[n] = carry;
-        chunk[NB] = carryc;
+        offset[NB] = cd + cs;                             // the invalid bin
+        cursor[NB] = cd + cs;
+        offset[NB + 1] = cd + cs + count[NB];
+        offset[NB + 2] = SPLIT ? D : cd;
+        chunk[NB] = cc;
     }
 }
 
@@ -355,7 +380,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, below);
+        if (below > 0) scan_kernel<true><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, below);
+        else scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
@@ -395,7 +421,7 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status, NB < kAggregateBricks);
-    scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
+    scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
                                                              NB < kAggregateBricks);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
@@ -442,7 +468,7 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
-        scan_kernel<<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
+        scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);

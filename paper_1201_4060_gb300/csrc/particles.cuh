@@ -35,7 +35,8 @@ constexpr unsigned kChunk = 2048;
 
 template <typename TR> struct Ws {
     unsigned* count;    // [NB + 1]  particles per brick; slot NB = invalid positions
-    unsigned* offset;   // [NB + 2]  exclusive prefix sum of count
+    unsigned* offset;   // [NB + 3]  start of each brick's sorted segment; [NB] end of the valid
+                        //           particles, [NB + 1] end of all, [NB + 2] start of the sparse range
     unsigned* cursor;   // [NB + 1]  next free sorted slot of each brick (starts at offset)
     unsigned* chunk;    // [NB + 1]  exclusive prefix sum of ceil(count / kChunk): first work item of a brick
     unsigned* item;     // [NB + ceil(P / kChunk)]  brick of each work item (the first chunk[NB] are set)
@@ -54,7 +55,7 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     };
     w->P = P;
     w->count = (unsigned*)take(sizeof(unsigned) * (NB + 1));
-    w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 2));
+    w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 3));
     w->cursor = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->chunk = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->item = (unsigned*)take(sizeof(unsigned) * (NB + (P + kChunk - 1) / kChunk));
@@ -478,7 +479,7 @@ gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, doubl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* tile = reinterpret_cast<double*>(smem_raw);
     const unsigned brick = blockIdx.x;
-    const unsigned beg = w.offset[brick], end = w.offset[brick + 1];
+    const unsigned beg = w.offset[brick], end = beg + w.count[brick];
     if (beg == end) return;
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
@@ -531,7 +532,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     if (item >= w.chunk[NB]) return;
     const unsigned brick = w.item[item];
     const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * kChunk;
-    const unsigned end = w.offset[brick + 1];
+    const unsigned end = w.offset[brick] + w.count[brick];
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
     stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
@@ -666,61 +667,57 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     }
 }
 
-// Direct gather for sparse bricks: a warp per brick holding fewer than
-// `below` particles (and at least one) evaluates them straight from the
-// coefficient array, one lane per particle.  A staged work item costs a few
-// microseconds of dependent latency (records, bucketing, the tile copy)
+// Direct gather for sparse bricks: the particles of bricks holding fewer
+// than the split (placed by the scan in one contiguous range after the dense
+// bricks, still grouped by brick) are evaluated straight from the
+// coefficient array, one thread per particle.  A staged work item costs a
+// few microseconds of dependent latency (records, bucketing, the tile copy)
 // whatever its particle count, so for a handful of particles reading the
-// stencils from global memory (through L1, where a brick's particles share
-// rows) is far cheaper.  Same contraction (contract_x2) as the staged gather:
-// the results are the same bits.  The scan gives such bricks no staged items.
+// stencils from global memory (through L1, where neighbouring threads'
+// particles share rows) is far cheaper.  Same contraction as the staged
+// gather (row_x2 / add_row in the same order), so the results are the same
+// bits.  The x-rows run in a rolled loop: unrolled, all 3 ORD^3 global loads
+// would be hoisted at once.
 template <int ORD, typename CT, typename TR, bool GRAD>
-__global__ void __launch_bounds__(256)
-gather_direct(const CT* __restrict__ coef, int N, unsigned NB, Ws<TR> w, unsigned below, float* __restrict__ out_u,
+__global__ void __launch_bounds__(256, 2)
+gather_direct(const CT* __restrict__ coef, int N, unsigned NB, Ws<TR> w, float* __restrict__ out_u,
               float* __restrict__ out_grad, float dscale) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const unsigned beg = w.offset[NB + 2], end = w.offset[NB];
     const size_t NN = (size_t)N * N;
-    for (unsigned b = wid; b < NB; b += nw) {
-        const unsigned n = w.count[b];
-        if (n == 0 || n >= below) continue;
-        const unsigned beg = w.offset[b];
-        for (unsigned k = lane; k < n; k += 32u) {
-            const Rec<TR> rc = w.s_rec[beg + k];
-            const int ax = (int)(rc.cell >> (2 * kAnchorBits));
-            const int ay = (int)((rc.cell >> kAnchorBits) & 1023u);
-            const int az = (int)(rc.cell & 1023u);
-            float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
-            bspline_weights<ORD, float>((float)rc.t[0], wx, dwx);
-            bspline_weights<ORD, float>((float)rc.t[1], wy, dwy);
-            bspline_weights<ORD, float>((float)rc.t[2], wz, dwz);
-            const PairWeights<ORD> pw(wz, dwz, wy, dwy);
-            int yo[ORD], zo[ORD];
+    for (unsigned i = beg + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
+        const Rec<TR> rc = w.s_rec[i];
+        const int ax = (int)(rc.cell >> (2 * kAnchorBits));
+        const int ay = (int)((rc.cell >> kAnchorBits) & 1023u);
+        const int az = (int)(rc.cell & 1023u);
+        float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+        bspline_weights<ORD, float>((float)rc.t[0], wx, dwx);
+        bspline_weights<ORD, float>((float)rc.t[1], wy, dwy);
+        bspline_weights<ORD, float>((float)rc.t[2], wz, dwz);
+        const PairWeights<ORD> pw(wz, dwz, wy, dwy);
+        int yo[ORD], zo[ORD];
 #pragma unroll
-            for (int j = 0; j < ORD; ++j) {
-                yo[j] = wrap_index(ay + j, N) * N;
-                zo[j] = wrap_index(az + j, N);
+        for (int j = 0; j < ORD; ++j) {
+            yo[j] = wrap_index(ay + j, N) * N;
+            zo[j] = wrap_index(az + j, N);
+        }
+        const size_t idx = rc.idx;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            const CT* cb = coef + (size_t)c * N * NN;
+            float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll 1
+            for (int jx = 0; jx < ORD; ++jx) {
+                const CT* row = cb + (size_t)wrap_index(ax + jx, N) * NN;
+                float s00, s10, s01;
+                row_x2<ORD, GRAD>([&](int jy, int jz) { return widen<CT>(row[yo[jy] + zo[jz]]); }, pw, wy, dwy, wz, dwz,
+                                  &s00, &s10, &s01);
+                add_row<GRAD>(wx[jx], dwx[jx], s00, s10, s01, &u, &gx, &gy, &gz);
             }
-            const size_t idx = rc.idx;
-#pragma unroll 1
-            for (int c = 0; c < 3; ++c) {
-                const CT* cb = coef + (size_t)c * N * NN;
-                float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-                // the x-rows in a rolled loop (unrolled, the 3 ORD^3 global loads would all be hoisted)
-#pragma unroll 1
-                for (int jx = 0; jx < ORD; ++jx) {
-                    const CT* row = cb + (size_t)wrap_index(ax + jx, N) * NN;
-                    float s00, s10, s01;
-                    row_x2<ORD, GRAD>([&](int jy, int jz) { return widen<CT>(row[yo[jy] + zo[jz]]); }, pw, wy, dwy, wz,
-                                      dwz, &s00, &s10, &s01);
-                    add_row<GRAD>(wx[jx], dwx[jx], s00, s10, s01, &u, &gx, &gy, &gz);
-                }
-                out_u[3 * idx + c] = u;
-                if (GRAD) {
-                    out_grad[9 * idx + 3 * c + 0] = gx * dscale;
-                    out_grad[9 * idx + 3 * c + 1] = gy * dscale;
-                    out_grad[9 * idx + 3 * c + 2] = gz * dscale;
-                }
+            out_u[3 * idx + c] = u;
+            if (GRAD) {
+                out_grad[9 * idx + 3 * c + 0] = gx * dscale;
+                out_grad[9 * idx + 3 * c + 1] = gy * dscale;
+                out_grad[9 * idx + 3 * c + 2] = gz * dscale;
             }
         }
     }
@@ -768,8 +765,11 @@ int run_gather_direct(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid
         const unsigned NB = g.NB;
         const float dscale = (float)((double)p->N / p->L);
         auto k = grad ? gather_direct<ORD, CT, TR, true> : gather_direct<ORD, CT, TR, false>;
-        const unsigned blocks = (NB + 7u) / 8u;          // one warp per brick
-        k<<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, NB, w, below, (float*)out_u,
+        // the sparse range's length is known on the device only: enough threads for every particle
+        // up to a few waves, grid-striding beyond
+        const long long want = (w.P + 255) / 256;
+        const unsigned blocks = (unsigned)std::max(1LL, std::min(want, 32LL * p->sms));
+        k<<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, NB, w, (float*)out_u,
                                          grad ? (float*)out_grad : nullptr, dscale);
         return BSPLINE_OK;
     }
