@@ -229,7 +229,8 @@ __device__ __forceinline__ void stage_tile16(float* tile, const float* __restric
 // BF16 coefficients: 16-byte loads of 8 values (rows start at z0, a multiple
 // of 16, and N is a multiple of 8, so a chunk never straddles the wrap),
 // widened to FP32 in registers and stored as two 16-byte words.  All of a
-// lane's loads are issued before its stores.
+// lane's loads of a plane are issued together, and the next plane's before
+// this plane's stores (registers stand in for the asynchronous copy).
 template <int ORD>
 __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16* __restrict__ coef, int N, int x0,
                                                 int y0, int z0) {
@@ -247,14 +248,21 @@ __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16
         soff[i] = iy * S::SY + 8 * ch;
         nst[i] = (S::PZ - 8 * ch) >= 8 ? 2 : 1;       // 16-byte stores that stay inside the row pitch
     }
-    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
+    // a warp's planes (c, ix) in turn, the next plane's loads in flight while this one is widened and stored
+    auto load = [&](int pl, uint4 (&v)[NI]) {
         const int c = pl / S::EX, ix = pl - c * S::EX;
         const __nv_bfloat16* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
-        float* dst = tile + (size_t)pl * S::SX;
-        uint4 v[NI];
 #pragma unroll
         for (int i = 0; i < NI; ++i)
             if (goff[i] >= 0) v[i] = __ldg(reinterpret_cast<const uint4*>(plane + goff[i]));
+    };
+    uint4 v[NI], vn[NI];
+    if (warp < 3 * S::EX) load(warp, vn);
+    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) v[i] = vn[i];
+        if (pl + nw < 3 * S::EX) load(pl + nw, vn);
+        float* dst = tile + (size_t)pl * S::SX;
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
             if (goff[i] < 0) continue;
