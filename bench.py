@@ -386,7 +386,7 @@ def run_ours(args):
         forms["f64"] = {"particles_per_s": P / (ms_64 / 1e3), "ms_per_step": ms_64, "gather_ms": g64,
                         "fft_ms": sum(st_64[s][0] / max(st_64[s][1], 1) for s in ("fft_x", "fft_yz"))}
         out["forms"] = forms
-        out["e2e"] = run_e2e(B, wl, F, xs, device, steps=12)
+        out["e2e"] = run_e2e(B, wl, F, xs, device, steps=24)
         out["adjoint"] = run_adjoint(B, device)
         out["batch"] = run_batch(B, device)
         out["sparse"] = run_sparse(B, wl, F, device)
