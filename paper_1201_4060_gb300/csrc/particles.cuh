@@ -279,6 +279,76 @@ __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16
     }
 }
 
+// BF16 coefficients, asynchronously: the raw BF16 tile (same element layout,
+// half the bytes) is copied with 16-byte cp.async into the upper half of the
+// FP32 tile's shared memory while the gather buckets its particles, then
+// widened in place by expand_bf16_tile.  Needs z rows of a multiple of 8
+// elements (16-byte copies that never straddle the periodic wrap: z0 is a
+// multiple of 16 and N of 8).
+template <int ORD> constexpr bool bf16_async() {
+    return Shape<__nv_bfloat16, ORD>::PZ % 8 == 0 && (3 * Shape<__nv_bfloat16, ORD>::TS) % 8 == 0;
+}
+template <int ORD>
+__device__ __forceinline__ void stage_tile_bf16_async(float* tile, const __nv_bfloat16* __restrict__ coef, int N,
+                                                      int x0, int y0, int z0) {
+    using S = Shape<__nv_bfloat16, ORD>;
+    static_assert(S::PZ % 8 == 0, "16-byte BF16 rows");
+    constexpr int E = 3 * S::TS;                      // elements of the tile
+    constexpr int CH = S::PZ / 8;                     // 16-byte chunks per row
+    constexpr int PER = S::EY * CH;
+    constexpr int NI = (PER + 31) / 32;
+    __nv_bfloat16* raw = reinterpret_cast<__nv_bfloat16*>(tile) + E;   // bytes [2E, 4E) of the tile
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int goff[NI], soff[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int f = lane + 32 * i;
+        const int iy = f / CH, ch = f - iy * CH;
+        goff[i] = f < PER ? wrap_index(y0 + iy, N) * N + wrap_index(z0 + 8 * ch, N) : -1;
+        soff[i] = iy * S::SY + 8 * ch;
+    }
+    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
+        const int c = pl / S::EX, ix = pl - c * S::EX;
+        const __nv_bfloat16* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
+        __nv_bfloat16* dst = raw + (size_t)pl * S::SX;
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+            if (goff[i] >= 0) cp_async16(dst + soff[i], plane + goff[i]);
+    }
+}
+
+// Widens the raw BF16 tile in place, in ascending chunks of 8 elements per
+// thread: FP32 element e goes to bytes [4e, 4e + 4) from BF16 bytes [2E + 2e,
+// 2E + 2e + 2).  A chunk's reads all finish (barrier) before its writes, and
+// a write never reaches BF16 data of a later chunk (4 (k+1) C <= 2E + 2 (k+1) C
+// while (k + 1) C <= E).  Ends with a barrier.
+template <int ORD>
+__device__ __forceinline__ void expand_bf16_tile(float* tile) {
+    using S = Shape<__nv_bfloat16, ORD>;
+    constexpr int E = 3 * S::TS;
+    static_assert(E % 8 == 0, "whole 16-byte chunks");
+    const uint4* raw = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(tile) + E);
+    const int C = 8 * (int)blockDim.x;
+    for (int k0 = 0; k0 < E; k0 += C) {
+        const int e = k0 + 8 * (int)threadIdx.x;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (e < E) v = raw[e / 8];
+        __syncthreads();
+        if (e < E) {
+            const unsigned w4[4] = {v.x, v.y, v.z, v.w};
+            float f[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                f[2 * q] = __uint_as_float(w4[q] << 16);     // bf16 -> fp32: the high half of the word
+                f[2 * q + 1] = __uint_as_float(w4[q] & 0xffff0000u);
+            }
+            *reinterpret_cast<float4*>(tile + e) = make_float4(f[0], f[1], f[2], f[3]);
+            *reinterpret_cast<float4*>(tile + e + 4) = make_float4(f[4], f[5], f[6], f[7]);
+        }
+    }
+    __syncthreads();
+}
+
 template <int ORD, typename CT>
 __device__ __forceinline__ void stage_brick(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                             int y0, int z0) {
@@ -543,7 +613,15 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     const unsigned end = w.offset[brick] + w.count[brick];
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
-    stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+    // BF16 tiles of orders 6-8 are copied raw and asynchronously (widened after the bucketing)
+    constexpr bool kRawBf16 = sizeof(CT) == 2 && bf16_async<ORD>();
+    const bool raw_bf16 = kRawBf16 && N >= 16;
+    if constexpr (kRawBf16) {
+        if (raw_bf16) stage_tile_bf16_async<ORD>(tile, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
+        else stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+    } else {
+        stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
         const int n = (int)min(kChunk, end - c0);
@@ -582,6 +660,9 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
         }
         cp_async_wait_all();
         __syncthreads();                                  // tile and order ready
+        if constexpr (kRawBf16) {
+            if (raw_bf16) expand_bf16_tile<ORD>(tile);
+        }
         // Warp jobs over that order.  Rank j holds #{banks with more than j
         // particles} particles, non-increasing in j.  While a rank holds at
         // least 16 particles it is one job (every load conflict-free); the
