@@ -248,8 +248,12 @@ int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);
  * items of bspline_coeffs skip their completion signals, so the waits that
  * depend on them run out after about a second: the kernel then stops, leaves
  * the coefficients unspecified, and bspline_status reports
- * BSPLINE_ERR_TIMEOUT.  It exists to test that error path; 0 clears. */
+ * BSPLINE_ERR_TIMEOUT.  It exists to test that error path.
+ * BSPLINE_TEST_NO_TMA stages every brick of the FP32 gather with cp.async
+ * instead of TMA tensor copies (same tile, same results), to compare the two
+ * paths.  0 clears. */
 #define BSPLINE_TEST_DROP_TRANSFORM_SIGNALS 0x1
+#define BSPLINE_TEST_NO_TMA 0x2
 int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks);
 
 /* Allocation-free evaluation of u and grad u (no counterpart in the paper: it

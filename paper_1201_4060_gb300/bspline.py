@@ -194,6 +194,7 @@ def bspline_status_string(code: int) -> str:
 NSTAGES = 10
 STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "spread", "grad_x", "adj_fft", "gather_direct"]
 TEST_DROP_TRANSFORM_SIGNALS = 0x1
+TEST_NO_TMA = 0x2
 
 
 def bspline_plan_set_test_hooks(plan: int, hooks: int) -> int:

@@ -518,7 +518,8 @@ int bspline_plan_autotune(bspline_plan_t plan, const void* coeffs, const double*
 }
 
 int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {
-    if (!valid_plan(plan) || (hooks & ~BSPLINE_TEST_DROP_TRANSFORM_SIGNALS)) return BSPLINE_ERR_INVALID_ARG;
+    if (!valid_plan(plan) || (hooks & ~(BSPLINE_TEST_DROP_TRANSFORM_SIGNALS | BSPLINE_TEST_NO_TMA)))
+        return BSPLINE_ERR_INVALID_ARG;
     plan->test_hooks = hooks;
     return BSPLINE_OK;
 }

@@ -31,6 +31,43 @@ BS_ADJ_ORDERS(BS_ADJOINT_EXTERN, double, double)
 BS_ADJ_ORDERS(BS_ADJOINT_EXTERN, float, float)
 BS_ADJ_ORDERS(BS_ADJOINT_EXTERN, __nv_bfloat16, float)
 
+namespace gather_impl {
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+int encode_coef_tmap(CUtensorMap* map, const void* coef, int N, int box_z, int box_y, int box_x) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return BSPLINE_ERR_CUDA;
+    const cuuint64_t n = (cuuint64_t)N;
+    const cuuint64_t dims[4] = {n, n, n, 3};                            // z, y, x, component
+    const cuuint64_t strides[3] = {n * 4, n * n * 4, n * n * n * 4};  // bytes, dims 1..3
+    const cuuint32_t box[4] = {(cuuint32_t)box_z, (cuuint32_t)box_y, (cuuint32_t)box_x, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(coef), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? BSPLINE_OK : BSPLINE_ERR_CUDA;
+}
+
+}  // namespace gather_impl
+
 namespace {
 using namespace gather_impl;
 

@@ -3,10 +3,20 @@
 // translation units that instantiate the gather for each coefficient type and
 // order range (split only to compile in parallel).
 #pragma once
+#include <cuda.h>
+
+#include <cstring>
+
 #include "internal.h"
 
 namespace bs {
 namespace gather_impl {
+
+// Tensor map of the FP32 coefficient array [3][N][N][N] for TMA tile loads:
+// box (z, y, x, component) = (box_z, box_y, box_x, 1).  Defined in
+// particles.cu; BSPLINE_OK, or an error if the driver's encoder is missing
+// or refuses (the caller then stages with cp.async).
+int encode_coef_tmap(CUtensorMap* map, const void* coef, int N, int box_z, int box_y, int box_x);
 
 constexpr int kAnchorBits = 10;          // N <= 1024
 
@@ -117,7 +127,8 @@ template <typename CT, int ORD> struct Shape {
     static constexpr int BZ = BX;
     static constexpr int EX = BX + ORD - 1, EY = BY + ORD - 1, EZ = BZ + ORD - 1;
     static constexpr int PZ = F64 ? EZ : ((EZ + 3) & ~3);
-    static constexpr int SY = PZ, SX = EY * PZ, TS = EX * EY * PZ;   // strides of y, x and the component
+    // strides of y, x and the component; FP32 tiles pad the component to 128 bytes (TMA destinations)
+    static constexpr int SY = PZ, SX = EY * PZ, TS = F64 ? EX * SX : ((EX * SX + 31) & ~31);
 };
 
 template <int ORD, typename CT>
@@ -154,6 +165,43 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ---- TMA tile loads completing on a shared-memory mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");   // visible to the async proxy
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+// Box at coordinates (z, y, x, c) of `map` into shared memory at dst (128-byte aligned).
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int z, int y, int x, int c,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(z), "r"(y), "r"(x), "r"(c), "r"(smem_u32(bar))
+        : "memory");
+}
+// Bounded wait for phase `parity` of the mbarrier (about a second of polls): false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (long long it = 0; it < (1LL << 22); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 // Copy the brick's tile into shared memory, one z-row per warp step: lane =
 // z offset (lanes >= EZ idle).  Rows are walked in (c, ix, iy) order; indices
 // wrap periodically.  Same-type coefficients go through cp.async (no register
@@ -172,7 +220,7 @@ __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT
     for (int pl = warp; pl < 3 * S::EX; pl += nw) {
         const int c = pl / S::EX, ix = pl - c * S::EX;
         const CT* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N + gz;
-        TT* dst = tile + (size_t)pl * S::SX + lane;
+        TT* dst = tile + (size_t)c * S::TS + (size_t)ix * S::SX + lane;
         auto copy = [&](int iy, const CT* s) {
             if constexpr (sizeof(CT) == sizeof(TT)) {
                 if constexpr (sizeof(CT) == 4) cp_async4(dst + iy * S::SY, s);
@@ -219,7 +267,7 @@ __device__ __forceinline__ void stage_tile16(float* tile, const float* __restric
     for (int pl = warp; pl < 3 * S::EX; pl += nw) {
         const int c = pl / S::EX, ix = pl - c * S::EX;
         const float* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
-        float* dst = tile + (size_t)pl * S::SX;
+        float* dst = tile + (size_t)c * S::TS + (size_t)ix * S::SX;
 #pragma unroll
         for (int i = 0; i < NI; ++i)
             if (goff[i] >= 0) cp_async16(dst + soff[i], plane + goff[i]);
@@ -262,7 +310,8 @@ __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16
 #pragma unroll
         for (int i = 0; i < NI; ++i) v[i] = vn[i];
         if (pl + nw < 3 * S::EX) load(pl + nw, vn);
-        float* dst = tile + (size_t)pl * S::SX;
+        const int c = pl / S::EX, ix = pl - c * S::EX;
+        float* dst = tile + (size_t)c * S::TS + (size_t)ix * S::SX;
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
             if (goff[i] < 0) continue;
@@ -310,7 +359,7 @@ __device__ __forceinline__ void stage_tile_bf16_async(float* tile, const __nv_bf
     for (int pl = warp; pl < 3 * S::EX; pl += nw) {
         const int c = pl / S::EX, ix = pl - c * S::EX;
         const __nv_bfloat16* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
-        __nv_bfloat16* dst = raw + (size_t)pl * S::SX;
+        __nv_bfloat16* dst = raw + (size_t)c * S::TS + (size_t)ix * S::SX;
 #pragma unroll
         for (int i = 0; i < NI; ++i)
             if (goff[i] >= 0) cp_async16(dst + soff[i], plane + goff[i]);
@@ -598,14 +647,17 @@ gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, doubl
 template <int ORD, typename CT, typename TR, bool GRAD>
 __global__ void __launch_bounds__(kGatherThreads, 2)
 gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __restrict__ out_u,
-           float* __restrict__ out_grad, float dscale) {
+           float* __restrict__ out_grad, float dscale, const __grid_constant__ CUtensorMap tmap, int use_tma,
+           unsigned long long* __restrict__ status) {
     using S = Shape<CT, ORD>;
     const unsigned NB = bg.NB;
     constexpr int NW = kGatherThreads / 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* tile = reinterpret_cast<float*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
+    float* tile = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ unsigned s_bucket[32];
     __shared__ unsigned short s_order[kChunk];
+    __shared__ __align__(8) unsigned long long s_mbar;
     const unsigned item = blockIdx.x;
     if (item >= w.chunk[NB]) return;
     const unsigned brick = w.item[item];
@@ -616,7 +668,17 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     // BF16 tiles of orders 6-8 are copied raw and asynchronously (widened after the bucketing)
     constexpr bool kRawBf16 = sizeof(CT) == 2 && bf16_async<ORD>();
     const bool raw_bf16 = kRawBf16 && N >= 16;
-    if constexpr (kRawBf16) {
+    // FP32 bricks away from the periodic seams: one TMA box per component (z rows of PZ, the padding
+    // beyond the grid is zero-filled and never read); the others with cp.async
+    const bool tma = sizeof(CT) == 4 && use_tma && x0 + S::EX <= N && y0 + S::EY <= N && z0 + S::EZ <= N;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            mbar_init(&s_mbar, 1);
+            mbar_expect_tx(&s_mbar, 3u * S::PZ * S::EY * S::EX * (unsigned)sizeof(float));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tma_load_4d(tile + c * S::TS, &tmap, z0, y0, x0, c, &s_mbar);
+        }
+    } else if constexpr (kRawBf16) {
         if (raw_bf16) stage_tile_bf16_async<ORD>(tile, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
         else stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
     } else {
@@ -659,6 +721,17 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             }
         }
         cp_async_wait_all();
+        if (tma) {
+            // every thread observes the TMA phase (the tile's bytes are then visible to it); a wait
+            // that runs out (about a second) marks the plan's error word, waits once more for the
+            // copies in flight, and the item is abandoned
+            const bool timed_out = __syncthreads_or(mbar_wait_bounded(&s_mbar, 0) ? 0 : 1) != 0;
+            if (timed_out) {
+                if (threadIdx.x == 0) atomicOr(&status[1], 1ULL);
+                mbar_wait_bounded(&s_mbar, 0);
+                return;
+            }
+        }
         __syncthreads();                                  // tile and order ready
         if constexpr (kRawBf16) {
             if (raw_bf16) expand_bf16_tile<ORD>(tile);
@@ -834,11 +907,20 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, voi
                                       grad ? (double*)out_grad : nullptr, dscale);
     } else {
         auto k = grad ? gather_f32<ORD, CT, TR, true> : gather_f32<ORD, CT, TR, false>;
-        if ((rc = set_smem(k, sm))) return rc;
+        const size_t sm_aligned = sm + 128;              // room to align the tile to 128 bytes
+        if ((rc = set_smem(k, sm_aligned))) return rc;
+        // FP32 coefficients: a TMA tensor map for the interior bricks (cp.async if it cannot be made)
+        using S = Shape<CT, ORD>;
+        CUtensorMap tmap;
+        std::memset(&tmap, 0, sizeof tmap);
+        int use_tma = 0;
+        if (sizeof(CT) == 4 && p->N >= 16 && !(p->test_hooks & BSPLINE_TEST_NO_TMA))
+            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? 1 : 0;
         // work items: at most one partial chunk per brick plus P / kChunk full ones
         const long long items = (long long)NB + (w.P + kChunk - 1) / kChunk;
-        k<<<(unsigned)items, kGatherThreads, sm, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, g, w,
-                                                              (float*)out_u, grad ? (float*)out_grad : nullptr, dscale);
+        k<<<(unsigned)items, kGatherThreads, sm_aligned, p->stream>>>(
+            reinterpret_cast<const CT*>(coeffs), p->N, g, w, (float*)out_u, grad ? (float*)out_grad : nullptr, dscale,
+            tmap, use_tma, p->d_status);
     }
     return BSPLINE_OK;
 }

@@ -429,6 +429,25 @@ def test_direct_and_staged_gathers_agree_bit_for_bit(B, dtype, N, order):
     assert normwise(outs[0][0], ru) < tol["u"] and normwise(outs[0][1], rg) < tol["grad"]
 
 
+@pytest.mark.parametrize("N,order", [(64, 6), (96, 4), (64, 8), (128, 3)])
+def test_tma_and_cp_async_staging_agree_bit_for_bit(B, N, order):
+    """FP32 bricks away from the periodic seams are staged by TMA tensor copies, the others (and all of
+    them with BSPLINE_TEST_NO_TMA) by cp.async: the same tile, so the same bits."""
+    half = synth.kolmogorov_field(N, seed=70 + order).dense()
+    x = torch.from_numpy(synth.clustered_particles(30000, seed=71)).cuda()
+    plan = B.Plan(N, order, "f32")
+    coef = plan.coeffs(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
+    plan.set_gather_split(0)                              # every brick staged
+    u_t, g_t = plan.interp(coef, x)
+    plan.set_test_hooks(B.TEST_NO_TMA)
+    u_c, g_c = plan.interp(coef, x)
+    plan.set_test_hooks(0)
+    assert plan.status() == 0
+    assert torch.equal(u_t, u_c) and torch.equal(g_t, g_c)
+    ru, rg = O.interpolate(rounded_input(half, "f32"), x.cpu().numpy(), order)
+    assert normwise(u_t.cpu().numpy(), ru) < TOL32["u"] and normwise(g_t.cpu().numpy(), rg) < TOL32["grad"]
+
+
 def test_gather_autotune_and_its_cache(B, tmp_path, monkeypatch):
     N, order, P = 32, 6, 4000
     half = synth.kolmogorov_field(N, seed=60).dense()
