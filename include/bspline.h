@@ -101,7 +101,7 @@ int bspline_plan_set_stream(bspline_plan_t plan, void* stream);
  * microseconds of dependent latency, which a handful of particles does not
  * repay.  0 stages every brick.  FP32 and BF16 plans (FP64 plans always
  * stage).  BSPLINE_GATHER_SPLIT_AUTO (the default) takes 32 for a call with
- * fewer than 64 particles per brick on average and 0 otherwise;
+ * fewer than 12 particles per brick on average and 0 otherwise;
  * bspline_plan_autotune picks the split by timing. */
 #define BSPLINE_GATHER_SPLIT_AUTO 0xfffffffeu
 int bspline_plan_set_gather_split(bspline_plan_t plan, unsigned direct_below);

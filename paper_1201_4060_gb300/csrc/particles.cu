@@ -409,7 +409,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     // bricks with fewer particles than this go to the direct gather (FP32 accumulation only)
     unsigned below = p->direct_below;
-    if (below == BSPLINE_GATHER_SPLIT_AUTO) below = P < 64LL * NB ? 32u : 0u;
+    if (below == BSPLINE_GATHER_SPLIT_AUTO) below = P < 12LL * NB ? 32u : 0u;
     if (sizeof(AT) == 8) below = 0u;
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
