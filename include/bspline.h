@@ -249,9 +249,9 @@ int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);
  * depend on them run out after about a second: the kernel then stops, leaves
  * the coefficients unspecified, and bspline_status reports
  * BSPLINE_ERR_TIMEOUT.  It exists to test that error path.
- * BSPLINE_TEST_NO_TMA stages every brick of the FP32 gather with cp.async
- * instead of TMA tensor copies (same tile, same results), to compare the two
- * paths.  0 clears. */
+ * BSPLINE_TEST_NO_TMA stages every brick of the FP32 gather and of the FP32
+ * position gradient with cp.async instead of TMA tensor copies (same tile,
+ * same results), to compare the two paths.  0 clears. */
 #define BSPLINE_TEST_DROP_TRANSFORM_SIGNALS 0x1
 #define BSPLINE_TEST_NO_TMA 0x2
 int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks);

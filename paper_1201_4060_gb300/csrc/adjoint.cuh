@@ -233,17 +233,22 @@ template <int ORD, typename CT, typename TR, bool HESS>
 __global__ void __launch_bounds__(kAdjThreads)
 gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
           const typename TileT<CT>::T* __restrict__ g_u, const typename TileT<CT>::T* __restrict__ g_grad,
-          double* __restrict__ g_x, typename TileT<CT>::T dscale) {
+          double* __restrict__ g_x, typename TileT<CT>::T dscale, const __grid_constant__ CUtensorMap tmap,
+          int use_tma, unsigned long long* __restrict__ status) {
     using A = typename TileT<CT>::T;
     using S = Shape<CT, ORD>;
     const unsigned NB = bg.NB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    A* tile = reinterpret_cast<A*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
+    A* tile = reinterpret_cast<A*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) unsigned long long s_mbar;
     unsigned brick, beg, end;
     if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
-    stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+    bool tma = false;
+    if constexpr (sizeof(A) == 4) tma = stage_tile_tma<ORD, CT>(tile, &tmap, &s_mbar, N, x0, y0, z0, use_tma);
+    if (!tma) stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
     __shared__ unsigned s_bucket[32];
     __shared__ unsigned short s_order[kChunk];
     const unsigned n = end - beg;
@@ -284,6 +289,7 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
         }
     }
     cp_async_wait_all();
+    if (tma && !tma_tile_wait(&s_mbar, status)) return;
     __syncthreads();
     const A s2 = dscale * dscale;
     for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
@@ -374,11 +380,18 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
                                                             (A*)g_coef, dscale);
     }
     if (g_x) {
-        const size_t sm = tile_bytes<ORD, CT>();
+        const size_t sm = tile_bytes<ORD, CT>() + 128;   // room to align the tile to 128 bytes
         auto k = g_grad ? gx_kernel<ORD, CT, TR, true> : gx_kernel<ORD, CT, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
+        using S = Shape<CT, ORD>;
+        CUtensorMap tmap;
+        std::memset(&tmap, 0, sizeof tmap);
+        int use_tma = 0;
+        if (sizeof(CT) == 4 && p->N >= 16 && !(p->test_hooks & BSPLINE_TEST_NO_TMA))
+            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? 1 : 0;
         k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>((const CT*)coeffs, p->N, g, w, (const A*)g_u,
-                                                            (const A*)g_grad, g_x, dscale);
+                                                            (const A*)g_grad, g_x, dscale, tmap, use_tma,
+                                                            p->d_status);
     }
     return BSPLINE_OK;
 }

@@ -398,6 +398,40 @@ __device__ __forceinline__ void expand_bf16_tile(float* tile) {
     __syncthreads();
 }
 
+// TMA staging of an FP32 brick away from the periodic seams: thread 0 arms the
+// mbarrier and issues one box (PZ, EY, EX, 1) per component; the boxes never
+// leave the grid there (z0 <= N - 32 when z0 + EZ <= N), and the padding z
+// rows beyond EZ are never read.  Returns whether the brick was staged this
+// way (the caller stages the others with cp.async).
+template <int ORD, typename CT>
+__device__ __forceinline__ bool stage_tile_tma(float* tile, const CUtensorMap* map, unsigned long long* bar, int N,
+                                               int x0, int y0, int z0, int use_tma) {
+    using S = Shape<CT, ORD>;
+    const bool tma = sizeof(CT) == 4 && use_tma && x0 + S::EX <= N && y0 + S::EY <= N && z0 + S::EZ <= N;
+    if (tma && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, 3u * S::PZ * S::EY * S::EX * (unsigned)sizeof(float));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tma_load_4d(tile + c * S::TS, map, z0, y0, x0, c, bar);
+    }
+    return tma;
+}
+
+// Every thread waits for the TMA tile (observing the barrier's phase makes the
+// bytes visible to it).  A wait that runs out (about a second) sets the error
+// word status[1], waits once more for the copies in flight, and returns
+// false for the whole CTA, which then abandons its item.  Call after a
+// barrier that follows the mbarrier's initialisation.
+__device__ __forceinline__ bool tma_tile_wait(unsigned long long* bar, unsigned long long* status) {
+    const bool timed_out = __syncthreads_or(mbar_wait_bounded(bar, 0) ? 0 : 1) != 0;
+    if (timed_out) {
+        if (threadIdx.x == 0) atomicOr(&status[1], 1ULL);
+        mbar_wait_bounded(bar, 0);
+        return false;
+    }
+    return true;
+}
+
 template <int ORD, typename CT>
 __device__ __forceinline__ void stage_brick(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                             int y0, int z0) {
@@ -692,16 +726,9 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     // BF16 tiles of orders 6-8 are copied raw and asynchronously (widened after the bucketing)
     constexpr bool kRawBf16 = sizeof(CT) == 2 && bf16_async<ORD>();
     const bool raw_bf16 = kRawBf16 && N >= 16;
-    // FP32 bricks away from the periodic seams: one TMA box per component (z rows of PZ, the padding
-    // beyond the grid is zero-filled and never read); the others with cp.async
-    const bool tma = sizeof(CT) == 4 && use_tma && x0 + S::EX <= N && y0 + S::EY <= N && z0 + S::EZ <= N;
+    // FP32 bricks away from the periodic seams by TMA, the others with cp.async
+    const bool tma = stage_tile_tma<ORD, CT>(tile, &tmap, &s_mbar, N, x0, y0, z0, use_tma);
     if (tma) {
-        if (threadIdx.x == 0) {
-            mbar_init(&s_mbar, 1);
-            mbar_expect_tx(&s_mbar, 3u * S::PZ * S::EY * S::EX * (unsigned)sizeof(float));
-#pragma unroll
-            for (int c = 0; c < 3; ++c) tma_load_4d(tile + c * S::TS, &tmap, z0, y0, x0, c, &s_mbar);
-        }
     } else if constexpr (kRawBf16) {
         if (raw_bf16) stage_tile_bf16_async<ORD>(tile, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
         else stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
@@ -747,17 +774,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             }
         }
         cp_async_wait_all();
-        if (tma) {
-            // every thread observes the TMA phase (the tile's bytes are then visible to it); a wait
-            // that runs out (about a second) marks the plan's error word, waits once more for the
-            // copies in flight, and the item is abandoned
-            const bool timed_out = __syncthreads_or(mbar_wait_bounded(&s_mbar, 0) ? 0 : 1) != 0;
-            if (timed_out) {
-                if (threadIdx.x == 0) atomicOr(&status[1], 1ULL);
-                mbar_wait_bounded(&s_mbar, 0);
-                return;
-            }
-        }
+        if (tma && !tma_tile_wait(&s_mbar, status)) return;
         __syncthreads();                                  // tile and order ready
         if constexpr (kRawBf16) {
             if (raw_bf16) expand_bf16_tile<ORD>(tile);

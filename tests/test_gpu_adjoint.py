@@ -158,6 +158,27 @@ def test_position_gradient_f32(B, order, dtype):
     assert err < (TOL32_GX if dtype == "f32" else 5e-2)
 
 
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_position_gradient_tma_and_cp_async_staging_agree(B, order):
+    """The position gradient stages FP32 bricks away from the periodic seams by TMA tensor copies and
+    the others (all of them with TEST_NO_TMA) by cp.async: the same tile, and each particle's gradient
+    is written once, so the same bits."""
+    N, P = 64, 20000
+    half = synth.kolmogorov_field(N, seed=90 + order).dense()
+    x = _dev(synth.clustered_particles(P, seed=91), torch.float64)
+    plan = B.Plan(N, order, "f32")
+    coef = plan.coeffs(_dev(half, torch.complex64))
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=92)
+    _, gx_t, _ = plan.spread_adjoint(x, gu_t, gg_t, coef=coef, u_hat_grad=False)
+    plan.set_test_hooks(B.TEST_NO_TMA)
+    _, gx_c, _ = plan.spread_adjoint(x, gu_t, gg_t, coef=coef, u_hat_grad=False)
+    plan.set_test_hooks(0)
+    assert plan.status() == 0
+    assert torch.equal(gx_t, gx_c)
+    ref = O.position_gradient(coef.double().cpu().numpy(), x.cpu().numpy(), gu, gg, order)
+    assert normwise(gx_t.cpu().numpy(), ref) < TOL32_GX
+
+
 def test_position_gradient_matches_fd_of_gpu_forward(B):
     N, order, P = 32, 6, 4096
     half = synth.kolmogorov_field(N, seed=8).dense()
