@@ -4,7 +4,9 @@
 One step = the whole path on one batch: prefilter + inverse real 3D FFT of a
 512^3 3-component Kolmogorov-spectrum field into quintic (order 6) B-spline
 coefficients, then locate/bin/sort 2^24 clustered particles and evaluate u
-and grad u at each of them.  Metric: particles/s (whole job over all ranks).
+and grad u at each of them, issued as one bspline_eval call (the particle
+sort runs on a second stream beside the transform; the evaluation waits for
+both).  Metric: particles/s (whole job over all ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -88,7 +90,7 @@ def config_block(wl, dtype, world):
                     f"{wl['P']} clustered particles per GPU, u + grad u, {dtype} coefficients",
         "N": wl["N"], "order": wl["order"], "particles_per_gpu": wl["P"], "coeff_dtype": dtype,
         "particles": "clustered: 60% uniform, 40% Gaussian clumps sigma=0.1 around 64 centres",
-        "step": "prefilter+inverse real FFT, bin+counting sort, weights+stencil contraction",
+        "step": "one bspline_eval call: prefilter+inverse real FFT beside the bin+counting sort (second stream), then weights+stencil contraction",
         "parallelism": f"replicas x{world} (particle shard per GPU, no collective)",
         "l2": "no flush: inputs larger than L2 (u_hat 1.62 GB, coefficients 1.61 GB, positions 0.40 GB)",
     }
@@ -231,8 +233,7 @@ def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True):
     stream = torch.cuda.current_stream()
 
     def step():
-        plan.coeffs(uh, coef)
-        plan.interp(coef, x, u, g)
+        plan.eval(uh, x, coef, u, g)
 
     for _ in range(warmup):
         step()
@@ -290,8 +291,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        plan.coeffs(uh, coef)
-        plan.interp(coef, x, u, g)
+        plan.eval(uh, x, coef, u, g)
 
     for _ in range(args.warmup):
         step()
@@ -577,7 +577,8 @@ def run_e2e(B, wl, F, xs, device, steps):
     host memory to the device and u and grad u back, all inside the timed region.  Steps alternate
     between two plans on two streams (bspline_run_host_async, then bspline_wait before a plan is
     reused), so one step's result copy overlaps the next step's input copy, as a caller streaming
-    steps would run them; the value is the whole sequence over its step count.  A single
+    steps would run them; the value is a whole sequence over its step count, the median of three
+    sequences.  A single
     synchronous bspline_run_host call is timed as well, for reference."""
     import numpy as np
     import torch
@@ -593,14 +594,19 @@ def run_e2e(B, wl, F, xs, device, steps):
     t = time.perf_counter()
     plans[0].run_host(uh, xh, *outs[0], stream=streams[0])
     single = time.perf_counter() - t
-    t0 = time.perf_counter()
-    for k in range(steps):
-        i = k % 2
-        plans[i].wait()                                  # its previous step is done: buffers free
-        plans[i].run_host(uh, xh, *outs[i], stream=streams[i], wait=False)
-    for p in plans:
-        p.wait()
-    t = (time.perf_counter() - t0) / steps
+    # three sequences of `steps` steps, their median: the host link is shared with the host's other work,
+    # and single sequences have varied between runs from 10.7 to 17.7 ms per step at 512^3 / 2^24
+    seqs = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        for k in range(steps):
+            i = k % 2
+            plans[i].wait()                              # its previous step is done: buffers free
+            plans[i].run_host(uh, xh, *outs[i], stream=streams[i], wait=False)
+        for p in plans:
+            p.wait()
+        seqs.append((time.perf_counter() - t0) / steps)
+    t = statistics.median(seqs)
     for p in plans:
         p.close()
     h2d = uh.numel() * 8 + xh.numel() * 8
@@ -608,7 +614,8 @@ def run_e2e(B, wl, F, xs, device, steps):
     del uh, xh, outs
     torch.cuda.empty_cache()
     return {"value": P / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": t * 1e3, "steps": steps, "single_call_ms": single * 1e3,
+            "ms_per_step": t * 1e3, "steps": steps, "sequences_ms_per_step": [s * 1e3 for s in seqs],
+            "single_call_ms": single * 1e3,
             "api": "bspline_run_host_async + bspline_wait on two alternating plans (pinned host buffers)"}
 
 

@@ -145,7 +145,8 @@ int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int
 /* Steps 1-3 in one call on device buffers: bspline_coeffs(u_hat -> coeffs)
  * then bspline_interp(coeffs, x -> out_u, out_grad), arguments and checks as
  * those two.  The particle sort needs only x, so it runs on a second stream
- * of the plan, concurrently with the coefficient transform, and the
+ * of the plan (created on first use at the device's greatest stream
+ * priority), concurrently with the coefficient transform, and the
  * evaluation starts once both are done; the call returns after queueing and
  * everything it queued is ordered after earlier work on the plan's stream
  * and before later work on it.  Same results as the two calls. */

@@ -238,7 +238,7 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
     using A = typename TileT<CT>::T;
     using S = Shape<CT, ORD>;
     const unsigned NB = bg.NB;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
     A* tile = reinterpret_cast<A*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) unsigned long long s_mbar;

@@ -241,7 +241,13 @@ void free_plan(bspline_plan_s* p) {
 // The plan's second stream and its two events, created on first use.
 int ensure_aux(bspline_plan_s* plan) {
     cudaError_t e = cudaSuccess;
-    if (!plan->aux_stream) e = cudaStreamCreateWithFlags(&plan->aux_stream, cudaStreamNonBlocking);
+    // the sort is short and gates the gather: at the greatest priority its blocks are dispatched ahead of the
+    // transform's waiting blocks, so it runs alongside the transform instead of after it
+    if (!plan->aux_stream) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&plan->aux_stream, cudaStreamNonBlocking, greatest);
+    }
     if (e == cudaSuccess && !plan->ev_start) e = cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess && !plan->ev_sorted) e = cudaEventCreateWithFlags(&plan->ev_sorted, cudaEventDisableTiming);
     return set_cuda_error(e);

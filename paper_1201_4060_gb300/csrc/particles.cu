@@ -407,13 +407,19 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
+    // Beside the transform (sort_stream given), the locate passes run as a small grid-stride grid, two
+    // 256-thread CTAs per SM: they then share the SMs with the transform's CTAs instead of taking them in
+    // turn, and use the HBM bandwidth the transform leaves (512^3, 2^24 particles: 5.33 -> 5.04 ms per
+    // step; one CTA per SM or more than three were slower).  Alone, the full grid is faster.
+    unsigned sort_grid = grid_for(P, 256);
+    if (sort_stream && 2LL * p->sms < (long long)sort_grid) sort_grid = (unsigned)(2 * p->sms);
     // bricks with fewer particles than this go to the direct gather (FP32 accumulation only)
     unsigned below = p->direct_below;
     if (below == BSPLINE_GATHER_SPLIT_AUTO) below = P < 12LL * NB ? 32u : 0u;
     if (sizeof(AT) == 8) below = 0u;
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
+        bin_kernel<TR><<<sort_grid, 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -422,7 +428,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u,
+        scatter_kernel<TR, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u,
                                                                  grad ? (AT*)out_grad : nullptr, NB < kAggregateBricks);
     }
     if (sort_stream) {

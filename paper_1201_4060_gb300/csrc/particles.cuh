@@ -710,7 +710,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     using S = Shape<CT, ORD>;
     const unsigned NB = bg.NB;
     constexpr int NW = kGatherThreads / 32;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
     float* tile = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ unsigned s_bucket[32];

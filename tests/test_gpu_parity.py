@@ -377,6 +377,30 @@ def test_eval_matches_coeffs_then_interp(B, dtype, N, order):
     assert np.array_equal(c3, c_ref)
 
 
+@pytest.mark.parametrize("N,order,P", [(32, 6, 400000), (256, 4, 600000)])
+def test_eval_grid_stride_sort_matches_coeffs_then_interp(B, N, order, P):
+    """Beside the transform the sort runs as a bounded grid (two CTAs per SM) whose threads loop over the
+    particles; with more particles than that grid's threads it must give the two-call results bit for
+    bit: 12 bricks (warp-aggregated counters) and 5632 bricks (one atomic per particle)."""
+    half = synth.kolmogorov_field(N, seed=31).dense()
+    plan = B.Plan(N, order, "f32")
+    uh = torch.from_numpy(half).to(plan.uhat_dtype).cuda()
+    x = synth.clustered_particles(P, seed=32)
+    x[7, 0] = np.nan
+    xt = torch.from_numpy(x).cuda()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert P > 2 * sms * 256 * 1.5
+    coef = plan.coeffs(uh)
+    u_ref, g_ref = plan.interp(coef, xt)
+    for _ in range(2):
+        coef2, u, g = plan.eval(uh, xt)
+        assert plan.status() == 1
+        assert torch.equal(coef2, coef)
+        assert torch.equal(torch.nan_to_num(u, 7.0), torch.nan_to_num(u_ref, 7.0))
+        assert torch.equal(torch.nan_to_num(g, 7.0), torch.nan_to_num(g_ref, 7.0))
+    assert torch.isnan(u[7]).all()
+
+
 def test_eval_rejects_bad_arguments(B):
     plan = B.Plan(16, 4, "f32")
     h = plan.handle
