@@ -35,6 +35,9 @@
  *     with bspline_status after synchronising that stream.
  *   - Every function returns 0 (BSPLINE_OK) or a negative status code and
  *     never aborts or throws; a failed call leaves the outputs unspecified.
+ *   - A plan holds mutable state (workspace, streams, timers): calls on one
+ *     plan must not run concurrently from several host threads.  Distinct
+ *     plans are independent and may be used from different threads.
  */
 #ifndef BSPLINE_H
 #define BSPLINE_H
