@@ -110,6 +110,16 @@ def _check(code: int, where: str) -> None:
         raise BSplineError(code, where)
 
 
+def _require(t, name: str, shape, dtype, where: str) -> None:
+    """Raise ValueError unless t is a contiguous tensor of this shape and dtype on the given side
+    (where = "cuda" or "cpu"): the library reads and writes exactly that many elements through the
+    pointer, so a smaller or strided buffer would be overrun."""
+    on_side = t.is_cuda if where == "cuda" else t.device.type == "cpu"
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous() or not on_side:
+        raise ValueError(f"{name} must be a contiguous {where} {dtype} tensor of shape {tuple(shape)}; got "
+                         f"{t.dtype} {tuple(t.shape)} on {t.device}{'' if t.is_contiguous() else ', strided'}")
+
+
 # ---- ABI-named thin wrappers (raw pointers / ints) --------------------------------
 
 def bspline_plan(N: int, order: int, dtype: int) -> tuple[int, int]:
@@ -277,6 +287,21 @@ class Plan:
         import torch
         return torch.empty((3, self.N, self.N, self.N), dtype=self.coef_dtype, device="cuda")
 
+    def _require_coef(self, coef) -> None:
+        _require(coef, "coef", (3, self.N, self.N, self.N), self.coef_dtype, "cuda")
+
+    def _outputs(self, P, device, out_u, out_grad, grad):
+        """The u and grad u buffers: allocated where not given, checked where given."""
+        import torch
+        if out_u is None:
+            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=device)
+        _require(out_u, "out_u", (P, 3), self.out_dtype, "cuda")
+        if grad:
+            if out_grad is None:
+                out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=device)
+            _require(out_grad, "out_grad", (P, 3, 3), self.out_dtype, "cuda")
+        return out_u, out_grad
+
     def coeffs(self, u_hat, out=None, stream=None):
         import torch
         N = self.N
@@ -285,8 +310,7 @@ class Plan:
             raise ValueError(f"u_hat must be contiguous CUDA {self.uhat_dtype} of shape {(3, N, N, N // 2 + 1)}")
         if out is None:
             out = self.empty_coeffs()
-        if out.shape != (3, N, N, N) or out.dtype != self.coef_dtype or not out.is_contiguous():
-            raise ValueError("bad coefficient buffer")
+        _require(out, "out", (3, N, N, N), self.coef_dtype, "cuda")
         self._stream(stream)
         _check(bspline_coeffs(self.handle, u_hat.data_ptr(), out.data_ptr()), "bspline_coeffs")
         return out
@@ -296,10 +320,8 @@ class Plan:
         if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
             raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
         P = x.shape[0]
-        if out_u is None:
-            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=x.device)
-        if grad and out_grad is None:
-            out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=x.device)
+        self._require_coef(coef)
+        out_u, out_grad = self._outputs(P, x.device, out_u, out_grad, grad)
         self._stream(stream)
         rc = bspline_interp(self.handle, coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
                             out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
@@ -320,13 +342,9 @@ class Plan:
             raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
         if coef is None:
             coef = self.empty_coeffs()
-        if coef.shape != (3, N, N, N) or coef.dtype != self.coef_dtype or not coef.is_contiguous():
-            raise ValueError("bad coefficient buffer")
+        self._require_coef(coef)
         P = x.shape[0]
-        if out_u is None:
-            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=x.device)
-        if grad and out_grad is None:
-            out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=x.device)
+        out_u, out_grad = self._outputs(P, x.device, out_u, out_grad, grad)
         self._stream(stream)
         rc = bspline_eval(self.handle, u_hat.data_ptr(), coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
                           out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
@@ -349,10 +367,12 @@ class Plan:
             if tns is not None and (tns.shape != shape or tns.dtype != self.out_dtype or not tns.is_contiguous()
                                     or not tns.is_cuda):
                 raise ValueError(f"{name} must be a contiguous CUDA {self.out_dtype} tensor {shape}")
+        if coef is not None:
+            self._require_coef(coef)
         if g_coef is None:
             g_coef = torch.zeros((3, N, N, N), dtype=self.out_dtype, device=x.device)
-        elif g_coef.shape != (3, N, N, N) or g_coef.dtype != self.out_dtype or not g_coef.is_contiguous():
-            raise ValueError("bad g_coef buffer")
+        else:
+            _require(g_coef, "g_coef", (3, N, N, N), self.out_dtype, "cuda")
         g_u_hat = torch.empty((3, N, N, N // 2 + 1), dtype=self.uhat_dtype, device=x.device) if u_hat_grad \
             else None
         g_x = torch.empty((P, 3), dtype=torch.float64, device=x.device) if coef is not None else None
@@ -382,10 +402,8 @@ class Plan:
         if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
             raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
         P = x.shape[0]
-        if out_u is None:
-            out_u = torch.empty((P, 3), dtype=self.out_dtype, device=x.device)
-        if grad and out_grad is None:
-            out_grad = torch.empty((P, 3, 3), dtype=self.out_dtype, device=x.device)
+        self._require_coef(coef)
+        out_u, out_grad = self._outputs(P, x.device, out_u, out_grad, grad)
         self._stream(None)
         split = ctypes.c_uint()
         ms = ctypes.c_double()
@@ -417,6 +435,16 @@ class Plan:
         wait=False queues the work and returns (bspline_run_host_async): the tensors must be left
         alone until wait() returns.
         """
+        import torch
+        N = self.N
+        _require(u_hat_host, "u_hat_host", (3, N, N, N // 2 + 1), self.uhat_dtype, "cpu")
+        if x_host.dim() != 2:
+            raise ValueError("x_host must be a contiguous cpu torch.float64 tensor [P, 3]")
+        P = x_host.shape[0]
+        _require(x_host, "x_host", (P, 3), torch.float64, "cpu")
+        _require(u_host, "u_host", (P, 3), self.out_dtype, "cpu")
+        if grad_host is not None:
+            _require(grad_host, "grad_host", (P, 3, 3), self.out_dtype, "cpu")
         self._stream(stream)
         fn = bspline_run_host if wait else bspline_run_host_async
         rc = fn(self.handle, u_hat_host.data_ptr(), x_host.data_ptr(), x_host.shape[0],

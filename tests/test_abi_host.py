@@ -82,3 +82,19 @@ def test_null_plan_is_rejected_everywhere():
     assert lib.bspline_batch_autotune(None, None, None, None) == B.ERR_INVALID_ARG
     assert lib.bspline_batch_capture(None, 1, None, None, None, None, None, None) == B.ERR_INVALID_ARG
     assert lib.bspline_batch_destroy(None) == B.OK
+
+
+def test_binding_checks_buffers_before_passing_their_pointers():
+    """The Python binding refuses buffers the library would overrun: wrong shape, dtype, strides or side."""
+    torch = pytest.importorskip("torch")
+    ok = torch.empty((5, 3), dtype=torch.float32)
+    B._require(ok, "u", (5, 3), torch.float32, "cpu")
+    bad = [
+        (torch.empty((4, 3), dtype=torch.float32), (5, 3), torch.float32, "cpu"),       # too few rows
+        (torch.empty((5, 3), dtype=torch.float64), (5, 3), torch.float32, "cpu"),       # wrong dtype
+        (torch.empty((3, 5), dtype=torch.float32).t(), (5, 3), torch.float32, "cpu"),   # strided view
+        (ok, (5, 3), torch.float32, "cuda"),                                            # host tensor for device
+    ]
+    for t, shape, dtype, side in bad:
+        with pytest.raises(ValueError):
+            B._require(t, "u", shape, dtype, side)
