@@ -98,3 +98,45 @@ def test_binding_checks_buffers_before_passing_their_pointers():
     for t, shape, dtype, side in bad:
         with pytest.raises(ValueError):
             B._require(t, "u", shape, dtype, side)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "bspline.h"
+
+int main(void) {
+    bspline_plan_t plan = 0;
+    size_t bytes = 0;
+    int64_t n = 0;
+    /* argument checks that return before any CUDA call */
+    if (bspline_plan(NULL, 64, 4, BSPLINE_F32) != BSPLINE_ERR_INVALID_ARG) return 1;
+    if (bspline_plan(&plan, 100, 4, BSPLINE_F32) != BSPLINE_ERR_UNSUPPORTED_N || plan) return 2;
+    if (bspline_plan(&plan, 64, 9, BSPLINE_F32) != BSPLINE_ERR_UNSUPPORTED_ORDER) return 3;
+    if (bspline_coeffs_bytes(NULL, &bytes) != BSPLINE_ERR_INVALID_ARG) return 4;
+    if (bspline_status(NULL, &n) != BSPLINE_ERR_INVALID_ARG) return 5;
+    if (bspline_interp(NULL, NULL, NULL, 0, NULL, NULL, 0) != BSPLINE_ERR_INVALID_ARG) return 6;
+    if (strlen(bspline_status_string(BSPLINE_ERR_TIMEOUT)) == 0) return 7;
+    printf("%s\n", bspline_version());
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c99_and_links_from_c(tmp_path):
+    """include/bspline.h is plain C: a C99 client builds with warnings as errors, links against the
+    library and gets the documented status codes from calls that need no GPU."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    lib_dir = os.path.dirname(_build.LIB)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", lib_dir, "-lbspline", "-Wl,-rpath," + lib_dir, "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == B.version()
