@@ -92,12 +92,20 @@ int bspline_plan_set_length(bspline_plan_t plan, double L);
 /* Prefilter choice (default BSPLINE_PREFILTER_INTERP). */
 int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind);
 
+/* The prefilter c(k) that a plan of this N, order and kind applies along each
+ * axis (Section 7: Eq. B_spline_multiplication for INTERP, Eq. B_spline_coeff
+ * for L2), computed on the host in FP64 exactly as bspline_plan computes it.
+ * out: host array of N doubles, out[k] for the signed wavenumber k mod N.
+ * No CUDA call and no plan needed.  Errors: INVALID_ARG (out NULL, bad kind),
+ * UNSUPPORTED_N, UNSUPPORTED_ORDER. */
+int bspline_prefilter_values(int N, int order, bspline_prefilter kind, double* out);
+
 /* Bind the plan to a cudaStream_t (passed as void*; NULL = legacy stream). */
 int bspline_plan_set_stream(bspline_plan_t plan, void* stream);
 
 /* Gather split.  Particles are sorted by brick; a brick holding fewer than
  * direct_below particles is evaluated by the direct gather (each particle's
- * stencil read from global memory, a warp per brick), the others by the
+ * stencil read from global memory, a thread per particle), the others by the
  * staged gather (the brick's coefficient tile staged in shared memory, a CTA
  * per up to 2048 of its particles).  Both give the same results bit for bit;
  * only the time differs: a staged brick carries a fixed cost of a few

@@ -56,6 +56,7 @@ def _load() -> ctypes.CDLL:
         "bspline_plan": (i32, [ctypes.POINTER(vp), i32, i32, i32]),
         "bspline_plan_set_length": (i32, [vp, ctypes.c_double]),
         "bspline_plan_set_prefilter": (i32, [vp, i32]),
+        "bspline_prefilter_values": (i32, [i32, i32, i32, ctypes.POINTER(ctypes.c_double)]),
         "bspline_plan_set_stream": (i32, [vp, vp]),
         "bspline_coeffs_bytes": (i32, [vp, ctypes.POINTER(sz)]),
         "bspline_uhat_bytes": (i32, [vp, ctypes.POINTER(sz)]),
@@ -134,6 +135,13 @@ def bspline_plan_set_length(plan: int, L: float) -> int:
 
 def bspline_plan_set_prefilter(plan: int, kind: int) -> int:
     return _load().bspline_plan_set_prefilter(plan, kind)
+
+
+def bspline_prefilter_values(N: int, order: int, kind: int) -> tuple[int, list[float]]:
+    """(status, [c(k) for k = 0..N-1]) of a plan of this N, order and prefilter kind (host, FP64)."""
+    buf = (ctypes.c_double * max(int(N), 1))()
+    rc = _load().bspline_prefilter_values(N, order, kind, buf)
+    return rc, list(buf)[:max(int(N), 0)]
 
 
 def bspline_plan_set_stream(plan: int, stream: int) -> int:

@@ -119,17 +119,16 @@ void twiddle(int m, int N, double* re, double* im) {
     }
 }
 
-int upload_prefilter(bspline_plan_s* p) {
-    const int N = p->N, n = p->order;
+// The prefilter c(k), k = 0..N-1, of an order-n plan of the given kind, in FP64.
+std::vector<double> prefilter_table(int N, int n, int kind) {
     const std::vector<double> b = node_values(n);
     const std::vector<double> b2 = node_values(2 * n);
     const int h = n / 2 + 1, h2 = n + 1;
     std::vector<double> c(N);
-    std::vector<float> cf(N);
     for (int k = 0; k < N; ++k) {
         const int ks = (k < N / 2) ? k : k - N;
         double v;
-        if (p->prefilter == BSPLINE_PREFILTER_INTERP) {
+        if (kind == BSPLINE_PREFILTER_INTERP) {
             // F_D[B_D](k) = sum_d B(d) cos(2 pi k d / N), phase k d reduced mod N exactly
             double s = 0.0;
             for (int d = -h; d <= h; ++d) {
@@ -152,8 +151,15 @@ int upload_prefilter(bspline_plan_s* p) {
             v = std::pow(sinc, n) / s;
         }
         c[k] = v;
-        cf[k] = (float)v;
     }
+    return c;
+}
+
+int upload_prefilter(bspline_plan_s* p) {
+    const int N = p->N;
+    const std::vector<double> c = prefilter_table(N, p->order, p->prefilter);
+    std::vector<float> cf(N);
+    for (int k = 0; k < N; ++k) cf[k] = (float)c[k];
     cudaError_t e = cudaMemcpy(p->d_c64, c.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_c32, cf.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
     return set_cuda_error(e);
@@ -301,6 +307,16 @@ int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype) {
         return rc;
     }
     *out = p;
+    return BSPLINE_OK;
+}
+
+int bspline_prefilter_values(int N, int order, bspline_prefilter kind, double* out) {
+    if (!out) return BSPLINE_ERR_INVALID_ARG;
+    if (kind != BSPLINE_PREFILTER_INTERP && kind != BSPLINE_PREFILTER_L2) return BSPLINE_ERR_INVALID_ARG;
+    if (!bs::supported_grid(N)) return BSPLINE_ERR_UNSUPPORTED_N;
+    if (order < 2 || order > 8) return BSPLINE_ERR_UNSUPPORTED_ORDER;
+    const std::vector<double> c = prefilter_table(N, order, kind);
+    std::memcpy(out, c.data(), sizeof(double) * N);
     return BSPLINE_OK;
 }
 

@@ -140,3 +140,35 @@ def test_header_compiles_as_c99_and_links_from_c(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.strip() == B.version()
+
+
+@pytest.mark.parametrize("N", [8, 16, 48, 64, 96, 512])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
+def test_library_prefilter_table_matches_the_oracle(N, order):
+    """The c(k) the library computes on the host (node values by the Cox-de Boor recurrence, cosines
+    of k d reduced mod N, angle reduced to an octant) against the oracle's literal DFT sum
+    (interpolating prefilter) and its sinc / Poisson-sum form (L2 prefilter).
+
+    Bound: the oracle's angles 2 pi k x / N reach 2 pi N, so each cosine carries up to 2 pi N eps of
+    phase rounding; F = 1/c is a sum with weights summing to one, and |dc| = c^2 |dF|, so
+    |dc| / max c <= max c * 2 pi N eps (plus a few eps for the sums themselves)."""
+    import math
+
+    import numpy as np
+    from oracle import bspline_oracle as O
+    eps = np.finfo(np.float64).eps
+    for kind, ref in ((B.PREFILTER_INTERP, O.prefilter(N, order)), (B.PREFILTER_L2, O.prefilter_l2(N, order))):
+        rc, c = B.bspline_prefilter_values(N, order, kind)
+        assert rc == B.OK
+        c = np.asarray(c)
+        assert c.shape == (N,)
+        cmax = np.abs(ref).max()
+        tol = cmax * 2 * math.pi * N * eps + 16 * eps
+        assert np.abs(c - ref).max() <= tol * cmax
+
+
+def test_prefilter_values_argument_checks():
+    assert B.bspline_prefilter_values(100, 4, B.PREFILTER_INTERP)[0] == B.ERR_UNSUPPORTED_N
+    assert B.bspline_prefilter_values(64, 9, B.PREFILTER_INTERP)[0] == B.ERR_UNSUPPORTED_ORDER
+    assert B.bspline_prefilter_values(64, 4, 7)[0] == B.ERR_INVALID_ARG
+    assert B.lib().bspline_prefilter_values(64, 4, 0, None) == B.ERR_INVALID_ARG
