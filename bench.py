@@ -38,6 +38,8 @@ METRIC = "particles/s for u+grad-u (quintic B-spline, 512^3), FP32 vs FP64 form,
 UNIT = "particles/s"
 WORKLOAD_NAME = "throughput512"
 STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "gather_direct"]
+ERR_SAMPLE = 1500          # particles at which each form's outputs are compared with the oracle
+ERR_SAMPLE_SEED = 42
 
 
 def peaks() -> dict:
@@ -221,8 +223,9 @@ def dense_field_on_gpu(F, dtype_torch, device):
     return uh
 
 
-def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True):
-    """Time `steps` whole-path steps with one plan of coefficient type dtype; returns (ms/step, stage dict)."""
+def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True, sample=None):
+    """Time `steps` whole-path steps with one plan of coefficient type dtype; returns (ms/step, stage dict,
+    non-finite count, outputs at the sampled particle indices (host FP64 arrays) or None)."""
     import torch
     plan = B.Plan(wl["N"], wl["order"], dtype)
     uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
@@ -251,10 +254,13 @@ def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True):
     stages = plan.stage_times() if timed_stages else {}
     nonfinite = plan.status()
     plan.set_timing(False)
+    sampled = None
+    if sample is not None:
+        sampled = (u[sample].double().cpu().numpy(), g[sample].double().cpu().numpy())
     del uh, coef, u, g
     plan.close()
     torch.cuda.empty_cache()
-    return ms / steps, stages, nonfinite
+    return ms / steps, stages, nonfinite, sampled
 
 
 def run_ours(args):
@@ -360,6 +366,10 @@ def run_ours(args):
               "traffic": measured_traffic("gather", "f32", N, order)}
     stages_ms = {s: {"total_ms": stages[s][0], "launches": stages[s][1],
                      "share": stages[s][0] / max(sum(v[0] for v in stages.values()), 1e-30)} for s in STAGES}
+    # outputs at a fixed sample of particles, for the error against the oracle (computed after the run)
+    sample_idx = np.sort(np.random.default_rng(ERR_SAMPLE_SEED).choice(P, ERR_SAMPLE, replace=False))
+    sample_t = torch.from_numpy(sample_idx).to(device)
+    sampled = {"f32": (u[sample_t].double().cpu().numpy(), g[sample_t].double().cpu().numpy())}
     del uh, coef, u, g
     plan.close()
     torch.cuda.empty_cache()
@@ -376,15 +386,22 @@ def run_ours(args):
     if world == 1 and not args.quick:
         forms = {"f32": {"particles_per_s": value, "ms_per_step": ms_total / args.steps}}
         ks = max(3, min(args.steps, 20))
-        ms_bf, st_bf, _ = run_form(B, wl, F, x, "bf16", ks, 2, device)
+        ms_bf, st_bf, _, sampled["bf16"] = run_form(B, wl, F, x, "bf16", ks, 2, device, sample=sample_t)
         gb = st_bf["gather"][0] / max(st_bf["gather"][1], 1)
         forms["bf16"] = {"particles_per_s": P / (ms_bf / 1e3), "ms_per_step": ms_bf, "gather_ms": gb,
                          "gather_hbm_frac": algorithmic_bytes("gather", N, P, "bf16", order) / (gb / 1e3) / 1e9 /
                          pk["hbm_gbs"]}
-        ms_64, st_64, _ = run_form(B, wl, F, x, "f64", 2, 1, device)
+        ms_64, st_64, _, sampled["f64"] = run_form(B, wl, F, x, "f64", 2, 1, device, sample=sample_t)
         g64 = st_64["gather"][0] / max(st_64["gather"][1], 1)
         forms["f64"] = {"particles_per_s": P / (ms_64 / 1e3), "ms_per_step": ms_64, "gather_ms": g64,
                         "fft_ms": sum(st_64[s][0] / max(st_64[s][1], 1) for s in ("fft_x", "fft_yz"))}
+        forms["f32"]["gather_ms"] = g_ms
+        if not args.no_cpu_baseline:
+            errs = form_errors(sampled, sample_idx)
+            for k, v in errs["forms"].items():
+                forms[k]["err_vs_oracle"] = v
+            forms["f32"]["e_trunc"] = errs["e_trunc"]
+            forms["f32"]["e_prec_below_e_trunc"] = errs["e_prec_below_e_trunc"]
         out["forms"] = forms
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=24)
         out["adjoint"] = run_adjoint(B, device)
@@ -620,8 +637,40 @@ def run_e2e(B, wl, F, xs, device, steps):
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)
+# The oracle runs only here, in child processes (single-threaded numpy each): the CPU baseline (one core,
+# and every host core as separate processes), and the error of each form's sampled outputs against it.
 
 ORACLE_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _component_half(F, c):
+    import numpy as np
+    N = F.N
+    half = np.zeros((1, N, N, N // 2 + 1), np.complex128)
+    half[0, F.idx[:, 0], F.idx[:, 1], F.idx[:, 2]] = F.val[c]
+    return half
 
 
 def cpu_worker(mode: str, samples: int, steps: int = 1, warmup: int = 0) -> dict:
@@ -632,10 +681,8 @@ def cpu_worker(mode: str, samples: int, steps: int = 1, warmup: int = 0) -> dict
     wl = workload()
     N, order, P = wl["N"], wl["order"], wl["P"]
     F = synth.kolmogorov_field(N, seed=wl["field_seed"])
-    H = N // 2 + 1
     # coefficient build of one component at full size (the three components are identical work)
-    half = np.zeros((1, N, N, H), np.complex128)
-    half[0, F.idx[:, 0], F.idx[:, 1], F.idx[:, 2]] = F.val[0]
+    half = _component_half(F, 0)
     t = time.perf_counter()
     c = O.coefficients(half, order)
     t_coef1 = time.perf_counter() - t
@@ -656,25 +703,197 @@ def cpu_worker(mode: str, samples: int, steps: int = 1, warmup: int = 0) -> dict
             "t_step_est_s": t_step, "per_step_est_s": [3 * t_coef1 + tg * (P / samples) for tg in g_times]}
 
 
-def _spawn_worker(mode, samples, steps=1, warmup=0):
+# --- every host core: one process per core (spawned), the coefficients in shared memory
+
+def _pool_init():
+    for k, v in ORACLE_ENV.items():
+        os.environ[k] = v
+
+
+def _pool_noop(_):
+    import numpy  # noqa: F401  (imports paid before the timed region)
+    from oracle import bspline_oracle  # noqa: F401
+    return os.getpid()
+
+
+def _pool_build(args):
+    """One component's coefficients (prefilter + inverse real FFT, oracle) into the shared array."""
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import bspline_oracle as O
+    shm_half, shm_coef, c, N, order = args
+    h = shared_memory.SharedMemory(name=shm_half)
+    k = shared_memory.SharedMemory(name=shm_coef)
+    try:
+        half = np.ndarray((3, N, N, N // 2 + 1), np.complex128, buffer=h.buf)
+        coef = np.ndarray((3, N, N, N), np.float64, buffer=k.buf)
+        coef[c] = O.coefficients(half[c:c + 1], order)[0]
+        del half, coef
+    finally:
+        h.close()
+        k.close()
+    return c
+
+
+def _pool_eval(args):
+    """u and grad u of one chunk of the sample (oracle), from the shared coefficients."""
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import bspline_oracle as O
+    shm_coef, N, order, xs = args
+    k = shared_memory.SharedMemory(name=shm_coef)
+    try:
+        coef = np.ndarray((3, N, N, N), np.float64, buffer=k.buf)
+        u, g = O.evaluate(coef, xs, order)
+        del coef
+    finally:
+        k.close()
+    return float(np.abs(u).sum() + np.abs(g).sum())
+
+
+def cpu_worker_all_cores(samples: int) -> dict:
+    """The oracle on every host core: the three components' coefficient builds in parallel processes,
+    then u / grad u of a sample of particles split over one process per core; wall-clock per stage."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    from paper_1201_4060_gb300 import synth
+    wl = workload()
+    N, order, P = wl["N"], wl["order"], wl["P"]
+    cores = os.cpu_count() or 1
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    x = synth.clustered_particles(P, seed=wl["particle_seed"])
+    sel = x[np.random.default_rng(0).integers(0, P, samples)]
+    hb = 3 * N * N * (N // 2 + 1) * 16
+    cbytes = 3 * N ** 3 * 8
+    sh = shared_memory.SharedMemory(create=True, size=hb)
+    sk = shared_memory.SharedMemory(create=True, size=cbytes)
+    try:
+        half = np.ndarray((3, N, N, N // 2 + 1), np.complex128, buffer=sh.buf)
+        half[...] = F.dense()
+        del half
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_pool_init) as pool:
+            pool.map(_pool_noop, range(cores))
+            t = time.perf_counter()
+            pool.map(_pool_build, [(sh.name, sk.name, c, N, order) for c in range(3)])
+            t_coef = time.perf_counter() - t
+            chunks = np.array_split(sel, cores)
+            t = time.perf_counter()
+            pool.map(_pool_eval, [(sk.name, N, order, ch) for ch in chunks], chunksize=1)
+            t_g = time.perf_counter() - t
+    finally:
+        sh.close()
+        sh.unlink()
+        sk.close()
+        sk.unlink()
+    return {"cores": cores, "t_coef_s": t_coef, "t_gather_sample_s": t_g, "gather_sample": samples,
+            "t_step_est_s": t_coef + t_g * (P / samples)}
+
+
+def cpu_worker_errors(path: str) -> dict:
+    """Errors of each form's sampled outputs against the oracle (FP64): normwise max and RMS, per quantity,
+    against the oracle of the exact FP64 spectrum and (FP32 / BF16 forms, which take a complex64
+    spectrum) of that rounded input; the method's truncation error E_trunc (Section 5, Eqs. l2-error /
+    l2-error-der, closed form over the field's modes) beside the FP32 form's E_prec."""
+    import math as m
+    import numpy as np
+    from oracle import bspline_oracle as O
+    from paper_1201_4060_gb300 import synth
+    wl = workload()
+    N, order = wl["N"], wl["order"]
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    d = np.load(path)
+    xs = d["x"]
+
+    def oracle_at(field):
+        ou = np.empty((xs.shape[0], 3))
+        og = np.empty((xs.shape[0], 3, 3))
+        for c in range(3):
+            coef_c = O.coefficients(_component_half(field, c), order)[0]
+            uc, gc = O.evaluate(np.broadcast_to(coef_c, (3, N, N, N)), xs, order)
+            ou[:, c] = uc[:, 0]
+            og[:, c, :] = gc[:, 0, :]
+            del coef_c
+        return ou, og
+
+    def errs(u, g, ou, og):
+        return {"u_normwise": float(np.abs(u - ou).max() / np.abs(ou).max()),
+                "grad_normwise": float(np.abs(g - og).max() / np.abs(og).max()),
+                "u_rms_rel": float(m.sqrt(np.mean((u - ou) ** 2) / np.mean(ou ** 2))),
+                "grad_rms_rel": float(m.sqrt(np.mean((g - og) ** 2) / np.mean(og ** 2)))}
+
+    exact = oracle_at(F)
+    rounded = oracle_at(F.rounded(np.complex64))
+    out = {"forms": {}}
+    for form in ("f32", "bf16", "f64"):
+        if f"{form}_u" not in d:
+            continue
+        u, g = d[f"{form}_u"], d[f"{form}_g"]
+        e = {"vs_exact_input": errs(u, g, *exact), "sample": int(xs.shape[0])}
+        if form != "f64":
+            e["vs_complex64_input"] = errs(u, g, *rounded)
+        out["forms"][form] = e
+    mse_u, mse_g = O.l2_error_field(N, F.idx, F.val, order)
+    ou, og = exact
+    tr = {"u": m.sqrt(mse_u.sum() / 3.0 / np.mean(ou ** 2)), "grad": m.sqrt(mse_g.sum() / 9.0 / np.mean(og ** 2))}
+    out["e_trunc"] = {"u_rms_rel": tr["u"], "grad_rms_rel": tr["grad"],
+                      "how": "closed form of Section 5 (l2-error, l2-error-der) over the field's modes"}
+    if "f32" in out["forms"]:
+        ep = out["forms"]["f32"]["vs_exact_input"]
+        out["e_prec_below_e_trunc"] = bool(ep["u_rms_rel"] < tr["u"] and ep["grad_rms_rel"] < tr["grad"])
+    return out
+
+
+def _spawn_worker(mode, samples, steps=1, warmup=0, extra=()):
     env = dict(os.environ, **ORACLE_ENV)
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", mode, "--samples", str(samples),
-           "--steps", str(steps), "--warmup", str(warmup)]
+           "--steps", str(steps), "--warmup", str(warmup), *extra]
+    for k, v in _OVERRIDE.items():
+        cmd += [f"--{k}", str(v)]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"oracle worker failed:\n{r.stderr[-2000:]}")
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def form_errors(sampled: dict, sample_idx) -> dict:
+    """Each form's error at the sampled particles, against the oracle run in a child process."""
+    import tempfile
+    import numpy as np
+    from paper_1201_4060_gb300 import synth
+    wl = workload()
+    x = synth.clustered_particles(wl["P"], seed=wl["particle_seed"])[sample_idx]
+    arrays = {"x": x}
+    for k, (u, g) in sampled.items():
+        arrays[f"{k}_u"] = u
+        arrays[f"{k}_g"] = g
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "sampled.npz")
+        np.savez(path, **arrays)
+        return _spawn_worker("errors", 0, extra=("--in", path))
+
+
 def cpu_baseline(samples: int) -> dict:
     wl = workload()
-    w = _spawn_worker("baseline", samples)
-    return {"value": wl["P"] / w["t_step_est_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"numpy FP64 oracle, 1 thread: coefficient build of one of the 3 components at full "
-                      f"{wl['N']}^3 (x3) + u/grad u at {samples} of the {wl['P']} particles "
-                      f"(x{wl['P'] // samples}); {w['t_coef_one_component_s']:.2f} s + "
-                      f"{w['t_gather_sample_s']:.2f} s measured",
-            "t_step_est_s": w["t_step_est_s"]}
+    one = _spawn_worker("baseline", samples)
+    allc = _spawn_worker("baseline-all", samples * 16)
+    cores = allc["cores"]
+    model = cpu_model()
+    return {"value": wl["P"] / allc["t_step_est_s"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": model,
+            "sample": f"numpy FP64 oracle, {cores} single-threaded processes ({model}): the 3 components' "
+                      f"coefficient builds at full {wl['N']}^3 in parallel ({allc['t_coef_s']:.2f} s) + u/grad u "
+                      f"at {samples * 16} of the {wl['P']} particles split over {cores} processes "
+                      f"({allc['t_gather_sample_s']:.2f} s, x{wl['P'] / (samples * 16):g})",
+            "t_step_est_s": allc["t_step_est_s"],
+            "cores_all": {"value": wl["P"] / allc["t_step_est_s"], "cores": cores, **allc},
+            "cores_1": {"value": wl["P"] / one["t_step_est_s"], "cores": 1,
+                        "sample": f"one thread: coefficient build of one of the 3 components at full {wl['N']}^3 "
+                                  f"(x3) + u/grad u at {samples} of the {wl['P']} particles "
+                                  f"(x{wl['P'] // samples}); {one['t_coef_one_component_s']:.2f} s + "
+                                  f"{one['t_gather_sample_s']:.2f} s measured",
+                        **one}}
 
 
 def run_reference(args):
@@ -710,6 +929,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--samples", type=int, default=4096, help=argparse.SUPPRESS)
+    ap.add_argument("--in", dest="input", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--N", type=int, default=None, help="grid size override (profiling captures only)")
     ap.add_argument("--P", type=int, default=None, help="particle count override (profiling captures only)")
     args = ap.parse_args()
@@ -717,6 +937,12 @@ def main():
         _OVERRIDE["N"] = args.N
     if args.P:
         _OVERRIDE["P"] = args.P
+    if args.cpu_worker == "baseline-all":
+        print(json.dumps(cpu_worker_all_cores(args.samples)))
+        return
+    if args.cpu_worker == "errors":
+        print(json.dumps(cpu_worker_errors(args.input)))
+        return
     if args.cpu_worker:
         print(json.dumps(cpu_worker(args.cpu_worker, args.samples, args.steps, args.warmup)))
         return

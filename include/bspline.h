@@ -72,7 +72,9 @@ enum {
     BSPLINE_ERR_TIMEOUT = -6,           /* a bounded device-side wait gave up */
     BSPLINE_ERR_NOT_IMPLEMENTED = -7,
     BSPLINE_ERR_OUT_OF_MEMORY = -8,     /* workspace allocation failed */
-    BSPLINE_ERR_TOO_LARGE = -9          /* beyond the fixed scratch of bspline_interp_noalloc */
+    BSPLINE_ERR_TOO_LARGE = -9,         /* beyond the fixed scratch of bspline_interp_noalloc */
+    BSPLINE_ERR_BOUNDS = -10            /* returned by bspline_status: an index check of a
+                                           BSPLINE_CHECKS build failed (the access was skipped) */
 };
 
 /* Flags of bspline_interp. */
@@ -195,11 +197,19 @@ int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double
 /* Device workspace bspline_interp needs for P positions. */
 int bspline_workspace_bytes(bspline_plan_t plan, int64_t P, size_t* bytes);
 
-/* Synchronise the plan's stream and report the device status words:
- * BSPLINE_ERR_TIMEOUT if a bounded wait of the last bspline_coeffs ran out
- * (its coefficients are then unspecified), else BSPLINE_ERR_NONFINITE_INPUT
- * if the last bspline_interp met non-finite positions, else BSPLINE_OK.
- * *nonfinite (may be NULL) receives that count of non-finite positions. */
+/* Synchronise the plan's stream and report the device status words.  Two
+ * groups of words: the transform's (cleared when bspline_coeffs, bspline_eval
+ * or the transform half of bspline_run_host starts) and the particle side's
+ * (cleared when bspline_interp, bspline_eval, bspline_run_host or the particle
+ * half of bspline_spread_adjoint starts); each holds until its next start.
+ * Returns BSPLINE_ERR_TIMEOUT if a bounded device wait of either ran out: in
+ * the transform the coefficients are then unspecified; in the evaluation (a
+ * coefficient tile that never arrived) the particles of the abandoned tile get
+ * NaN outputs (NaN position gradients in the adjoint).  Else
+ * BSPLINE_ERR_BOUNDS if an index check of a BSPLINE_CHECKS build failed, else
+ * BSPLINE_ERR_NONFINITE_INPUT if the last particle call met non-finite
+ * positions, else BSPLINE_OK.  *nonfinite (may be NULL) receives that count
+ * of non-finite positions. */
 int bspline_status(bspline_plan_t plan, int64_t* nonfinite);
 
 /* Whole path with HOST buffers: copies u_hat_host and x_host to plan-owned
@@ -266,6 +276,12 @@ int bspline_stage_times(bspline_plan_t plan, double* ms, int64_t* launches);
  * same results), to compare the two paths.  0 clears. */
 #define BSPLINE_TEST_DROP_TRANSFORM_SIGNALS 0x1
 #define BSPLINE_TEST_NO_TMA 0x2
+/* BSPLINE_TEST_SKIP_TMA_ISSUE: FP32 tiles that would come by TMA arm their
+ * shared-memory barrier for the tile's bytes but issue no copy, so the tile
+ * wait runs out after about a second with nothing in flight: those items are
+ * abandoned with NaN outputs and bspline_status reports BSPLINE_ERR_TIMEOUT.
+ * It exists to test that error path. */
+#define BSPLINE_TEST_SKIP_TMA_ISSUE 0x4
 int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks);
 
 /* Allocation-free evaluation of u and grad u (no counterpart in the paper: it
@@ -289,7 +305,12 @@ int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks);
  * calls; each call clears the parts that must start at zero.  Calls that
  * overlap on the GPU (concurrent streams or host threads) race on the array,
  * so serialise them.  Non-finite positions give NaN outputs; their count is
- * not reported (there is no plan to hold a status word). */
+ * not reported (there is no plan to hold a status word).  A coefficient tile
+ * whose copy never completes (a bounded wait of about a second runs out)
+ * leaves NaN outputs for the particles of that tile; this is not reported
+ * otherwise either.  The cached address belongs to the device's primary
+ * context: after cudaDeviceReset the library must be reloaded before this
+ * entry point is used again. */
 #define BSPLINE_NOALLOC_MAX_N 256
 #define BSPLINE_NOALLOC_MAX_PARTICLES 131072
 int bspline_interp_noalloc(const void* coeffs, int N, int order, bspline_dtype dtype, double L,

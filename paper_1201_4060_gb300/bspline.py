@@ -24,6 +24,7 @@ ERR_TIMEOUT = -6
 ERR_NOT_IMPLEMENTED = -7
 ERR_OUT_OF_MEMORY = -8
 ERR_TOO_LARGE = -9
+ERR_BOUNDS = -10
 NOALLOC_MAX_N = 256
 NOALLOC_MAX_PARTICLES = 131072
 
@@ -213,6 +214,7 @@ NSTAGES = 10
 STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "spread", "grad_x", "adj_fft", "gather_direct"]
 TEST_DROP_TRANSFORM_SIGNALS = 0x1
 TEST_NO_TMA = 0x2
+TEST_SKIP_TMA_ISSUE = 0x4
 
 
 def bspline_plan_set_test_hooks(plan: int, hooks: int) -> int:

@@ -289,7 +289,10 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
         }
     }
     cp_async_wait_all();
-    if (tma && !tma_tile_wait(&s_mbar, status)) return;
+    if (tma && !tma_tile_wait(&s_mbar, status + kStatusParticleTimeout)) {
+        fill_nan_item<TR, double>(w, beg, n, g_x, nullptr, 3);
+        return;
+    }
     __syncthreads();
     const A s2 = dscale * dscale;
     for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
@@ -388,7 +391,8 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
         std::memset(&tmap, 0, sizeof tmap);
         int use_tma = 0;
         if (sizeof(CT) == 4 && p->N >= 16 && !(p->test_hooks & BSPLINE_TEST_NO_TMA))
-            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? 1 : 0;
+            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? kTmaOn : 0;
+        if (use_tma && (p->test_hooks & BSPLINE_TEST_SKIP_TMA_ISSUE)) use_tma = kTmaArmOnly;
         k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>((const CT*)coeffs, p->N, g, w, (const A*)g_u,
                                                             (const A*)g_grad, g_x, dscale, tmap, use_tma,
                                                             p->d_status);

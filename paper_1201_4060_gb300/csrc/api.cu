@@ -293,8 +293,8 @@ int bspline_plan(bspline_plan_t* out, int N, int order, bspline_dtype dtype) {
     if (e == cudaSuccess) e = cudaMalloc(&p->d_c32, sizeof(float) * N);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw64, sizeof(double2) * N);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw32, sizeof(float2) * N);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned long long) * 2);
-    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(unsigned long long) * kStatusWords);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(unsigned long long) * kStatusWords);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
@@ -445,13 +445,14 @@ int bspline_status(bspline_plan_t plan, int64_t* nonfinite) {
     if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     if (!g.ok) return BSPLINE_ERR_CUDA;
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[kStatusWords] = {};
     cudaError_t e = cudaStreamSynchronize(plan->stream);
     if (e == cudaSuccess) e = cudaMemcpy(h, plan->d_status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(e);
-    if (nonfinite) *nonfinite = (int64_t)h[0];
-    if (h[1]) return BSPLINE_ERR_TIMEOUT;
-    return h[0] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
+    if (nonfinite) *nonfinite = (int64_t)h[kStatusNonfinite];
+    if (h[kStatusParticleTimeout] || h[kStatusTransformTimeout]) return BSPLINE_ERR_TIMEOUT;
+    if (h[kStatusBounds]) return BSPLINE_ERR_BOUNDS;
+    return h[kStatusNonfinite] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
 }
 
 int bspline_plan_set_gather_split(bspline_plan_t plan, unsigned direct_below) {
@@ -540,7 +541,8 @@ int bspline_plan_autotune(bspline_plan_t plan, const void* coeffs, const double*
 }
 
 int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {
-    if (!valid_plan(plan) || (hooks & ~(BSPLINE_TEST_DROP_TRANSFORM_SIGNALS | BSPLINE_TEST_NO_TMA)))
+    if (!valid_plan(plan) ||
+        (hooks & ~(BSPLINE_TEST_DROP_TRANSFORM_SIGNALS | BSPLINE_TEST_NO_TMA | BSPLINE_TEST_SKIP_TMA_ISSUE)))
         return BSPLINE_ERR_INVALID_ARG;
     plan->test_hooks = hooks;
     return BSPLINE_OK;
@@ -644,6 +646,7 @@ const char* bspline_status_string(int status) {
         case BSPLINE_ERR_NOT_IMPLEMENTED: return "not implemented";
         case BSPLINE_ERR_OUT_OF_MEMORY: return "out of device memory";
         case BSPLINE_ERR_TOO_LARGE: return "size beyond the fixed scratch of bspline_interp_noalloc";
+        case BSPLINE_ERR_BOUNDS: return "an index check of a BSPLINE_CHECKS build failed";
     }
     return "unknown status";
 }

@@ -420,7 +420,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) 
         if (e != cudaSuccess) return set_cuda_error(e);
         StageTimer tm(p, BSPLINE_STAGE_FFT_YZ);
         k<<<(unsigned)grid, T, sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), ring, tw, ctr,
-                                         reinterpret_cast<unsigned*>(p->d_status + 1), lag, ring_slots,
+                                         reinterpret_cast<unsigned*>(p->d_status + kStatusTransformTimeout), lag, ring_slots,
                                          (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0,
                                          (long long)c0 * N, planes);
     }
@@ -446,7 +446,7 @@ int launch_coeffs_range(bspline_plan_s* p, const void* u_hat, void* coeffs, int 
     int rc = p->work.grow(coeffs_workspace_bytes(p));
     if (rc) return rc;
     if (c0 == 0) {
-        cudaError_t e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(unsigned long long), p->stream);
+        cudaError_t e = cudaMemsetAsync(p->d_status + kStatusTransformTimeout, 0, sizeof(unsigned long long), p->stream);
         if (e != cudaSuccess) return set_cuda_error(e);
     }
     switch (p->N) {

@@ -50,6 +50,15 @@ inline bool supported_grid(int N) {
     return N % 3 == 0 && (q & (q - 1)) == 0 && N % 16 == 0;
 }
 
+// Device status words of a plan, read by bspline_status.  Particle calls
+// (interp, eval, the adjoint's particle side) clear words 0-1 when they start,
+// the transform clears word 2.
+constexpr int kStatusNonfinite = 0;          // non-finite positions of the last particle call
+constexpr int kStatusParticleTimeout = 1;    // a tile wait of the last particle call ran out
+constexpr int kStatusTransformTimeout = 2;   // a wait of the last transform ran out
+constexpr int kStatusBounds = 3;             // index checks that failed (BSPLINE_CHECKS builds)
+constexpr int kStatusWords = 4;
+
 struct PendingTiming {
     int stage;
     cudaEvent_t start, stop;
@@ -84,8 +93,7 @@ struct bspline_plan_s {
     bs::DeviceBuffer work;
     // Particle workspace (binning, sort, sorted particle records).
     bs::DeviceBuffer pws;
-    // Device status words: [0] = count of non-finite positions of the last
-    // interp; [1] = nonzero if a bounded wait of the last transform ran out.
+    // Device status words (bs::kStatus*): non-finite count and wait time-outs.
     unsigned long long* d_status = nullptr;
     int sms = 1;            // streaming multiprocessors of the plan's device
     int test_hooks = 0;     // BSPLINE_TEST_* flags

@@ -24,7 +24,8 @@
 namespace {
 
 constexpr size_t kScratchBytes = (size_t)16 << 20;      // 16 MiB on every GPU that loads the library
-constexpr size_t kStatusBytes = 256;                      // status word, kept apart from the workspace
+constexpr size_t kStatusBytes = 256;                      // status words, kept apart from the workspace
+static_assert(sizeof(unsigned long long) * bs::kStatusWords <= kStatusBytes, "status words fit");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -86,7 +87,7 @@ extern "C" int bspline_interp_noalloc(const void* coeffs, int N, int order, bspl
     int rc = scratch_for_device(dev, &base);
     if (rc == BSPLINE_OK) {
         auto* status = reinterpret_cast<unsigned long long*>(base);
-        p.d_status = status;                       // the gather's wait-timeout flag goes to status[1]
+        p.d_status = status;                       // words 0-1 are cleared by every call (non-finite, tile wait)
         void* ws = static_cast<unsigned char*>(base) + kStatusBytes;
         rc = bs::launch_interp_ws(&p, ws, status, coeffs, x, P, out_u, out_grad, flags);
     }

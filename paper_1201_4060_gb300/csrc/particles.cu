@@ -405,7 +405,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     } restore{p, main_stream};
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
+        return set_cuda_error(e);                       // non-finite count and tile-wait flag
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     // Beside the transform (sort_stream given), the locate passes run as a small grid-stride grid, two
     // 256-thread CTAs per SM: they then share the SMs with the transform's CTAs instead of taking them in
@@ -461,7 +462,8 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     cudaStream_t st = p->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
+        return set_cuda_error(e);                       // non-finite count and tile-wait flag
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status, NB < kAggregateBricks);
     scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
@@ -504,7 +506,8 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     cudaStream_t st = p->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
+        return set_cuda_error(e);                       // non-finite count and tile-wait flag
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
         bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);

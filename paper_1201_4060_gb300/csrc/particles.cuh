@@ -402,7 +402,10 @@ __device__ __forceinline__ void expand_bf16_tile(float* tile) {
 // mbarrier and issues one box (PZ, EY, EX, 1) per component; the boxes never
 // leave the grid there (z0 <= N - 32 when z0 + EZ <= N), and the padding z
 // rows beyond EZ are never read.  Returns whether the brick was staged this
-// way (the caller stages the others with cp.async).
+// way (the caller stages the others with cp.async).  use_tma: 0 = never,
+// kTmaOn = interior bricks, kTmaArmOnly = arm the barrier for the tile's bytes
+// but issue no copy (test hook: the wait then runs out with nothing in flight).
+constexpr int kTmaOn = 1, kTmaArmOnly = 2;
 template <int ORD, typename CT>
 __device__ __forceinline__ bool stage_tile_tma(float* tile, const CUtensorMap* map, unsigned long long* bar, int N,
                                                int x0, int y0, int z0, int use_tma) {
@@ -411,25 +414,45 @@ __device__ __forceinline__ bool stage_tile_tma(float* tile, const CUtensorMap* m
     if (tma && threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, 3u * S::PZ * S::EY * S::EX * (unsigned)sizeof(float));
+        if (use_tma != kTmaArmOnly) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) tma_load_4d(tile + c * S::TS, map, z0, y0, x0, c, bar);
+            for (int c = 0; c < 3; ++c) tma_load_4d(tile + c * S::TS, map, z0, y0, x0, c, bar);
+        }
     }
     return tma;
 }
 
 // Every thread waits for the TMA tile (observing the barrier's phase makes the
-// bytes visible to it).  A wait that runs out (about a second) sets the error
-// word status[1], waits once more for the copies in flight, and returns
-// false for the whole CTA, which then abandons its item.  Call after a
-// barrier that follows the mbarrier's initialisation.
-__device__ __forceinline__ bool tma_tile_wait(unsigned long long* bar, unsigned long long* status) {
+// bytes visible to it).  A wait that runs out (about a second) sets *flag,
+// waits once more for the copies in flight, and returns false for the whole
+// CTA, which then abandons its item.  Call after a barrier that follows the
+// mbarrier's initialisation.
+__device__ __forceinline__ bool tma_tile_wait(unsigned long long* bar, unsigned long long* flag) {
     const bool timed_out = __syncthreads_or(mbar_wait_bounded(bar, 0) ? 0 : 1) != 0;
     if (timed_out) {
-        if (threadIdx.x == 0) atomicOr(&status[1], 1ULL);
+        if (threadIdx.x == 0) atomicOr(flag, 1ULL);
         mbar_wait_bounded(bar, 0);
         return false;
     }
     return true;
+}
+
+// Outputs of an abandoned work item: NaN for each of its particles, so that a
+// time-out never leaves stale values behind (the status word says why).
+template <typename TR, typename AT>
+__device__ __forceinline__ void fill_nan_item(const Ws<TR>& w, unsigned c0, unsigned n, AT* __restrict__ out_u,
+                                              AT* __restrict__ out_grad, int ncomp_u) {
+    const AT nan = (AT)NAN;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t idx = w.s_rec[c0 + i].idx;
+        if (out_u) {
+            for (int k = 0; k < ncomp_u; ++k) out_u[(size_t)ncomp_u * idx + k] = nan;
+        }
+        if (out_grad) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) out_grad[9 * idx + k] = nan;
+        }
+    }
 }
 
 template <int ORD, typename CT>
@@ -774,7 +797,10 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             }
         }
         cp_async_wait_all();
-        if (tma && !tma_tile_wait(&s_mbar, status)) return;
+        if (tma && !tma_tile_wait(&s_mbar, status + kStatusParticleTimeout)) {
+            fill_nan_item<TR, float>(w, c0, (unsigned)n, out_u, GRAD ? out_grad : nullptr, 3);
+            return;
+        }
         __syncthreads();                                  // tile and order ready
         if constexpr (kRawBf16) {
             if (raw_bf16) expand_bf16_tile<ORD>(tile);
@@ -963,7 +989,8 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, voi
         std::memset(&tmap, 0, sizeof tmap);
         int use_tma = 0;
         if (sizeof(CT) == 4 && p->N >= 16 && !(p->test_hooks & BSPLINE_TEST_NO_TMA))
-            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? 1 : 0;
+            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? kTmaOn : 0;
+        if (use_tma && (p->test_hooks & BSPLINE_TEST_SKIP_TMA_ISSUE)) use_tma = kTmaArmOnly;
         // work items: at most one partial chunk per brick plus P / kChunk full ones
         const long long items = (long long)NB + (w.P + kChunk - 1) / kChunk;
         k<<<(unsigned)items, kGatherThreads, sm_aligned, p->stream>>>(

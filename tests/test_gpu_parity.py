@@ -291,6 +291,49 @@ def test_transform_wait_timeout_is_reported_and_context_survives(B, dtype):
     assert normwise(coef.double().cpu().numpy(), ref) < (TOL64 if dtype == "f64" else 2e-6)
 
 
+def test_tile_wait_timeout_gives_nan_and_status_and_context_survives(B):
+    """A TMA tile wait runs out (a test hook arms the tile's barrier but issues no copy): the particles of
+    that tile get NaN outputs (NaN position gradients in the adjoint), bspline_status reports TIMEOUT,
+    particles of tiles staged by cp.async on the periodic seams are still right, and the next call
+    without the hook is correct everywhere with an OK status."""
+    N, order = 64, 4
+    half = synth.kolmogorov_field(N, seed=17).dense()
+    h = L / N
+    # a few particles of the interior brick (16..31, 12..23, 16..31): stencil origin floor(s) - 1 there, so TMA
+    inner = np.array([[20.3, 14.6, 21.2], [25.9, 18.1, 30.4], [17.5, 22.7, 17.05]]) * h
+    # and a few of a seam brick (x from 48): staged by cp.async
+    seam = np.array([[55.2, 5.4, 3.3], [61.7, 60.2, 62.9]]) * h
+    xs = np.concatenate([inner, seam])
+    plan = B.Plan(N, order, "f32")
+    coef = plan.coeffs(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
+    plan.set_gather_split(0)
+    x = torch.from_numpy(xs).cuda()
+    ru, rg = O.interpolate(rounded_input(half, "f32"), xs, order)
+    plan.set_test_hooks(B.TEST_SKIP_TMA_ISSUE)
+    u, g = plan.interp(coef, x)
+    rc, _ = B.bspline_status(plan.handle)
+    assert rc == B.ERR_TIMEOUT
+    u, g = u.cpu().numpy(), g.cpu().numpy()
+    ni = len(inner)
+    assert np.isnan(u[:ni]).all() and np.isnan(g[:ni]).all()
+    assert normwise(u[ni:], ru[ni:]) < TOL32["u"] and normwise(g[ni:], rg[ni:]) < TOL32["grad"]
+    # the adjoint's position gradient stages its tiles the same way
+    gu = torch.ones((len(xs), 3), dtype=torch.float32, device="cuda")
+    _, g_x, _ = plan.spread_adjoint(x, g_u=gu, coef=coef, u_hat_grad=False)
+    rc, _ = B.bspline_status(plan.handle)
+    assert rc == B.ERR_TIMEOUT
+    gx_bad = g_x.cpu().numpy()
+    assert np.isnan(gx_bad[:ni]).all() and np.isfinite(gx_bad[ni:]).all()
+    plan.set_test_hooks(0)
+    u, g = plan.interp(coef, x)
+    assert plan.status() == 0
+    assert normwise(u.cpu().numpy(), ru) < TOL32["u"] and normwise(g.cpu().numpy(), rg) < TOL32["grad"]
+    _, g_x, _ = plan.spread_adjoint(x, g_u=gu, coef=coef, u_hat_grad=False)
+    assert plan.status() == 0
+    assert np.isfinite(g_x.cpu().numpy()).all()
+    assert np.allclose(g_x.cpu().numpy()[ni:], gx_bad[ni:], rtol=0, atol=0)
+
+
 def test_run_host_matches_device_path(B):
     N, order = 32, 4
     half = synth.kolmogorov_field(N, seed=8).dense().astype(np.complex64)

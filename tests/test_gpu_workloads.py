@@ -5,8 +5,9 @@
   error (E_trunc), both normalised by the RMS of the quantity; the FP64 form
   matches the oracle to 1e-12 on sampled particles.
 * 512^3, order 6, 2^24 clustered particles (the benchmark's launch
-  configuration): sampled outputs match the oracle, computed particle by
-  particle from the oracle's full-size FP64 coefficients.
+  configuration): sampled outputs of the FP32, BF16 and FP64 forms match the
+  oracle, computed particle by particle from the oracle's full-size FP64
+  coefficients (FP64 to 1e-12).
 """
 import math
 
@@ -95,11 +96,11 @@ def test_full_size_512_quintic_sampled_parity(B):
     sample = np.sort(rng.choice(P, 1500, replace=False))
     got = {}
     xt = torch.from_numpy(x).cuda()
-    for dtype in ("f32", "bf16"):
+    for dtype in ("f32", "bf16", "f64"):
         plan = B.Plan(N, order, dtype)
-        uh = torch.zeros((3, N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+        uh = torch.zeros((3, N, N, N // 2 + 1), dtype=plan.uhat_dtype, device="cuda")
         idx = torch.from_numpy(F.idx).cuda()
-        uh[:, idx[:, 0], idx[:, 1], idx[:, 2]] = torch.from_numpy(F.val).cuda().to(torch.complex64)
+        uh[:, idx[:, 0], idx[:, 1], idx[:, 2]] = torch.from_numpy(F.val).cuda().to(plan.uhat_dtype)
         coef = plan.coeffs(uh)
         u, g = plan.interp(coef, xt)
         assert plan.status() == 0
@@ -109,23 +110,32 @@ def test_full_size_512_quintic_sampled_parity(B):
         del uh, coef, u, g
         plan.close()
         torch.cuda.empty_cache()
-    Fr = F.rounded(np.complex64)
-    ou = np.empty((sample.size, 3))
-    og = np.empty((sample.size, 3, 3))
-    for c in range(3):     # one component at a time keeps the oracle's host memory bounded
-        half = np.zeros((1, N, N, N // 2 + 1), np.complex128)
-        half[0, Fr.idx[:, 0], Fr.idx[:, 1], Fr.idx[:, 2]] = Fr.val[c]
-        coef_c = O.coefficients(half, order)[0]
-        cb = np.broadcast_to(coef_c, (3, N, N, N))
-        uc, gc = O.evaluate(cb, x[sample], order)
-        ou[:, c] = uc[:, 0]
-        og[:, c, :] = gc[:, 0, :]
-        del coef_c, cb, half
+    def oracle_at_sample(field):
+        ou = np.empty((sample.size, 3))
+        og = np.empty((sample.size, 3, 3))
+        for c in range(3):     # one component at a time keeps the oracle's host memory bounded
+            half = np.zeros((1, N, N, N // 2 + 1), np.complex128)
+            half[0, field.idx[:, 0], field.idx[:, 1], field.idx[:, 2]] = field.val[c]
+            coef_c = O.coefficients(half, order)[0]
+            cb = np.broadcast_to(coef_c, (3, N, N, N))
+            uc, gc = O.evaluate(cb, x[sample], order)
+            ou[:, c] = uc[:, 0]
+            og[:, c, :] = gc[:, 0, :]
+            del coef_c, cb, half
+        return ou, og
+
+    # FP32 and BF16 plans take a complex64 spectrum: held to the oracle of that rounded input
+    ou, og = oracle_at_sample(F.rounded(np.complex64))
     eu32, eg32 = normwise(got["f32"][0], ou), normwise(got["f32"][1], og)
     eu16, eg16 = normwise(got["bf16"][0], ou), normwise(got["bf16"][1], og)
-    print(f"512^3 quintic: FP32 normwise u {eu32:.2e} grad {eg32:.2e}; BF16 u {eu16:.2e} grad {eg16:.2e}")
+    # the FP64 form (the plain GPU path the FP32 form is compared with) on the exact input
+    ou64, og64 = oracle_at_sample(F)
+    eu64, eg64 = normwise(got["f64"][0], ou64), normwise(got["f64"][1], og64)
+    print(f"512^3 quintic: FP32 normwise u {eu32:.2e} grad {eg32:.2e}; BF16 u {eu16:.2e} grad {eg16:.2e}; "
+          f"FP64 u {eu64:.2e} grad {eg64:.2e}")
     assert eu32 < 2e-5 and eg32 < 5e-5
     assert eu16 < 2e-2 and eg16 < 5e-2
+    assert eu64 < 1e-12 and eg64 < 1e-12
 
 
 @pytest.mark.parametrize("N", [768, 1024])

@@ -58,6 +58,9 @@ def test_noalloc_matches_plan_path_on_consecutive_calls(B):
         (64, 6, "f64", L, synth.clustered_particles(B.NOALLOC_MAX_PARTICLES, seed=7), 31),
         (32, 4, "f32", L, synth.uniform_particles(5003, seed=8), 32),
         (16, 5, "bf16", 3.0, np.random.default_rng(9).uniform(-3.0, 6.0, (777, 3)), 33),
+        # the largest scratch the documented limits allow: N at its maximum, FP64 (8^3 bricks, 32-byte
+        # records), order 8, the maximum particle count
+        (B.NOALLOC_MAX_N, 8, "f64", L, synth.uniform_particles(B.NOALLOC_MAX_PARTICLES, seed=10), 34),
     ]
     for N, order, dtype, Lc, xs, seed in cases:
         x = torch.from_numpy(xs).cuda()
