@@ -404,6 +404,16 @@ def run_ours(args):
             forms["f32"]["e_prec_below_e_trunc"] = errs["e_prec_below_e_trunc"]
         out["forms"] = forms
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=24)
+        orders, o_sampled, o_idx = run_orders(B, device)
+        if not args.no_cpu_baseline:
+            oe = orders_errors(o_sampled, o_idx)
+            for row in orders["rows"]:
+                e = oe[f"o{row['order']}_{row['dtype']}"]
+                row["err_vs_oracle"] = e["err"]
+                row["e_trunc"] = e["e_trunc"]
+                if row["dtype"] == "f32":
+                    row["e_prec_below_e_trunc"] = e["e_prec_below_e_trunc"]
+        out["orders256"] = orders
         out["adjoint"] = run_adjoint(B, device)
         out["batch"] = run_batch(B, device)
         out["sparse"] = run_sparse(B, wl, F, device)
@@ -479,6 +489,67 @@ def run_adjoint(B, device, steps=10, warmup=3):
     plan.close()
     torch.cuda.empty_cache()
     return out
+
+
+def run_orders(B, device, reps=10, sample=ERR_SAMPLE):
+    """Config of the orders: 256^3 Kolmogorov field, orders 2/4/6/8, 10^6 uniform particles sorted by cell,
+    FP32 and FP64 coefficients.  Per order and form: the evaluation (bspline_interp on built coefficients)
+    as given (the library sorts), and with BSPLINE_INTERP_SORTED on the same particles put in the plan's
+    brick order (bspline_sort_order, outside the timed region); and the transform alone.  Returns the
+    block and the sampled outputs (for the errors against the oracle)."""
+    import numpy as np
+    import torch
+    from paper_1201_4060_gb300 import synth
+    wl = synth.WORKLOADS["orders256"]
+    N, P = wl["N"], wl["P"]
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    xs = synth.make_particles(wl["particles"], P, wl["particle_seed"], N)
+    x = torch.from_numpy(xs).to(device)
+    sample_idx = np.sort(np.random.default_rng(ERR_SAMPLE_SEED).choice(P, sample, replace=False))
+    st = torch.from_numpy(sample_idx).to(device)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows, sampled = [], {}
+    for order in wl["order"]:
+        for dtype in ("f32", "f64"):
+            plan = B.Plan(N, order, dtype)
+            uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
+            coef = plan.empty_coeffs()
+            t_coef = timed(lambda: plan.coeffs(uh, coef))
+            u = torch.empty((P, 3), dtype=plan.out_dtype, device=device)
+            g = torch.empty((P, 3, 3), dtype=plan.out_dtype, device=device)
+            t_given = timed(lambda: plan.interp(coef, x, u, g))
+            sampled[f"o{order}_{dtype}"] = (u[st].double().cpu().numpy(), g[st].double().cpu().numpy())
+            perm = plan.sort_order(x).long()
+            xp = x[perm].contiguous()
+            t_sorted = timed(lambda: plan.interp(coef, xp, u, g, sorted=True))
+            # the flagged call's outputs come in the brick order: compare them at the same particles
+            inv = torch.empty_like(perm)
+            inv[perm] = torch.arange(P, device=device)
+            ok = torch.equal(u[inv[st]].double(), torch.from_numpy(sampled[f"o{order}_{dtype}"][0]).to(device))
+            rows.append({"order": order, "dtype": dtype, "coeffs_ms": t_coef, "interp_ms": t_given,
+                         "particles_per_s": P / (t_given / 1e3), "interp_sorted_flag_ms": t_sorted,
+                         "particles_per_s_sorted_flag": P / (t_sorted / 1e3), "sorted_flag_same_u": bool(ok)})
+            del uh, coef, u, g, perm, xp, inv
+            plan.close()
+            torch.cuda.empty_cache()
+    out = {"workload": f"{N}^3 Kolmogorov field (seed {wl['field_seed']}), orders {list(wl['order'])}, {P} uniform "
+                       f"particles sorted by cell (seed {wl['particle_seed']}), u + grad u",
+           "step": "bspline_interp on built coefficients (A3-A6); coeffs_ms = bspline_coeffs (A1-A2) alone",
+           "rows": rows, "reps": reps}
+    return out, sampled, sample_idx
 
 
 def run_sparse(B, wl, F, device, reps=5):
@@ -874,6 +945,50 @@ def form_errors(sampled: dict, sample_idx) -> dict:
         return _spawn_worker("errors", 0, extra=("--in", path))
 
 
+def cpu_worker_orders_errors(path: str) -> dict:
+    """Per order and form of the orders block: the sampled outputs' error against the oracle (FP64, on the
+    exact spectrum), E_prec (RMS) beside E_trunc (closed form of Section 5) per order."""
+    import math as m
+    import numpy as np
+    from oracle import bspline_oracle as O
+    from paper_1201_4060_gb300 import synth
+    wl = synth.WORKLOADS["orders256"]
+    N, P = wl["N"], wl["P"]
+    F = synth.kolmogorov_field(N, seed=wl["field_seed"])
+    d = np.load(path)
+    xs = synth.make_particles(wl["particles"], P, wl["particle_seed"], N)[d["idx"]]
+    half = F.dense()
+    out = {}
+    for order in wl["order"]:
+        ou, og = O.evaluate(O.coefficients(half, order), xs, order)
+        mse_u, mse_g = O.l2_error_field(N, F.idx, F.val, order)
+        tr_u = m.sqrt(mse_u.sum() / 3.0 / np.mean(ou ** 2))
+        tr_g = m.sqrt(mse_g.sum() / 9.0 / np.mean(og ** 2))
+        for dtype in ("f32", "f64"):
+            u, g = d[f"o{order}_{dtype}_u"], d[f"o{order}_{dtype}_g"]
+            err = {"u_normwise": float(np.abs(u - ou).max() / np.abs(ou).max()),
+                   "grad_normwise": float(np.abs(g - og).max() / np.abs(og).max()),
+                   "u_rms_rel": float(m.sqrt(np.mean((u - ou) ** 2) / np.mean(ou ** 2))),
+                   "grad_rms_rel": float(m.sqrt(np.mean((g - og) ** 2) / np.mean(og ** 2)))}
+            out[f"o{order}_{dtype}"] = {"err": err, "e_trunc": {"u_rms_rel": tr_u, "grad_rms_rel": tr_g},
+                                        "e_prec_below_e_trunc": bool(err["u_rms_rel"] < tr_u and
+                                                                     err["grad_rms_rel"] < tr_g)}
+    return out
+
+
+def orders_errors(sampled: dict, sample_idx) -> dict:
+    import tempfile
+    import numpy as np
+    arrays = {"idx": sample_idx}
+    for k, (u, g) in sampled.items():
+        arrays[f"{k}_u"] = u
+        arrays[f"{k}_g"] = g
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "orders.npz")
+        np.savez(path, **arrays)
+        return _spawn_worker("orders-errors", 0, extra=("--in", path))
+
+
 def cpu_baseline(samples: int) -> dict:
     wl = workload()
     one = _spawn_worker("baseline", samples)
@@ -942,6 +1057,9 @@ def main():
         return
     if args.cpu_worker == "errors":
         print(json.dumps(cpu_worker_errors(args.input)))
+        return
+    if args.cpu_worker == "orders-errors":
+        print(json.dumps(cpu_worker_orders_errors(args.input)))
         return
     if args.cpu_worker:
         print(json.dumps(cpu_worker(args.cpu_worker, args.samples, args.steps, args.warmup)))

@@ -77,8 +77,18 @@ enum {
                                            BSPLINE_CHECKS build failed (the access was skipped) */
 };
 
-/* Flags of bspline_interp. */
+/* Flags of bspline_interp and bspline_eval. */
 #define BSPLINE_INTERP_NO_GRAD 0x1      /* out_grad may be NULL; only u is evaluated */
+/* BSPLINE_INTERP_SORTED: the positions are already grouped by the plan's
+ * brick (the order bspline_sort_order gives, or any order with the same
+ * brick sequence): the evaluation reads them in place and writes each
+ * particle's outputs at its own index, so the placement pass of the sort is
+ * skipped and the output stores stay within each brick's range (Section 5:
+ * the stencil nodes of Eq. alg-int-6 pick the brick).  The count pass checks
+ * the promise: if the order is broken anywhere, the call sorts as without
+ * the flag (same results, the time of an unsorted call).  Bricks are never
+ * split off to the direct gather under this flag. */
+#define BSPLINE_INTERP_SORTED 0x2
 
 /* Create a plan for an N^3 periodic grid, B-spline order `order` (the
  * paper's N: stencil width, degree order-1), coefficient type `dtype`.
@@ -154,6 +164,18 @@ int bspline_coeffs(bspline_plan_t plan, const void* u_hat, void* coeffs);
  * workspace sized for P (grown on demand; growth synchronises the device). */
 int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
                    void* out_u, void* out_grad, int flags);
+
+/* The order in which a plan evaluates particles (Section 5, Eq. alg-int-6:
+ * each particle belongs to the brick of cells holding its first stencil
+ * node; bricks of 16 x 12 x 16 cells, 16 x 8 x 16 above order 6, 8^3 for
+ * FP64 plans, in x-major key order): perm (device int32 [P]) receives the
+ * original index of the particle that comes i-th, bricks in key order and
+ * non-finite positions last; the order within a brick is arbitrary.  A caller
+ * that permutes its positions (and whatever it carries per particle) by perm
+ * can then pass BSPLINE_INTERP_SORTED until particles change bricks.  x:
+ * device double [P][3].  Uses the plan's particle workspace; asynchronous on
+ * the plan's stream. */
+int bspline_sort_order(bspline_plan_t plan, const double* x, int64_t P, int32_t* perm);
 
 /* Steps 1-3 in one call on device buffers: bspline_coeffs(u_hat -> coeffs)
  * then bspline_interp(coeffs, x -> out_u, out_grad), arguments and checks as

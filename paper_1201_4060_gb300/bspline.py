@@ -31,6 +31,7 @@ NOALLOC_MAX_PARTICLES = 131072
 F64, F32, BF16 = 0, 1, 2
 PREFILTER_INTERP, PREFILTER_L2 = 0, 1
 INTERP_NO_GRAD = 0x1
+INTERP_SORTED = 0x2
 GATHER_SPLIT_AUTO = 0xFFFFFFFE
 
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
@@ -65,6 +66,7 @@ def _load() -> ctypes.CDLL:
         "bspline_interp": (i32, [vp, vp, vp, i64, vp, vp, i32]),
         "bspline_eval": (i32, [vp, vp, vp, vp, i64, vp, vp, i32]),
         "bspline_spread_adjoint": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "bspline_sort_order": (i32, [vp, vp, i64, vp]),
         "bspline_workspace_bytes": (i32, [vp, i64, ctypes.POINTER(sz)]),
         "bspline_status": (i32, [vp, ctypes.POINTER(i64)]),
         "bspline_run_host": (i32, [vp, vp, vp, i64, vp, vp]),
@@ -168,6 +170,10 @@ def bspline_wait(plan: int) -> int:
 def bspline_eval(plan: int, u_hat_ptr: int, coeffs_ptr: int, x_ptr: int, P: int, u_ptr: int, grad_ptr: int,
                  flags: int) -> int:
     return _load().bspline_eval(plan, u_hat_ptr, coeffs_ptr, x_ptr, P, u_ptr, grad_ptr, flags)
+
+
+def bspline_sort_order(plan: int, x_ptr: int, P: int, perm_ptr: int) -> int:
+    return _load().bspline_sort_order(plan, x_ptr, P, perm_ptr)
 
 
 def bspline_spread_adjoint(plan, coeffs_ptr, x_ptr, P, gu_ptr, ggrad_ptr, gcoef_ptr, guhat_ptr, gx_ptr) -> int:
@@ -325,7 +331,8 @@ class Plan:
         _check(bspline_coeffs(self.handle, u_hat.data_ptr(), out.data_ptr()), "bspline_coeffs")
         return out
 
-    def interp(self, coef, x, out_u=None, out_grad=None, grad: bool = True, stream=None):
+    def interp(self, coef, x, out_u=None, out_grad=None, grad: bool = True, stream=None, sorted: bool = False):
+        """u (and grad u) at x; sorted=True passes BSPLINE_INTERP_SORTED (x in the order of sort_order)."""
         import torch
         if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
             raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
@@ -333,12 +340,25 @@ class Plan:
         self._require_coef(coef)
         out_u, out_grad = self._outputs(P, x.device, out_u, out_grad, grad)
         self._stream(stream)
+        flags = (0 if grad else INTERP_NO_GRAD) | (INTERP_SORTED if sorted else 0)
         rc = bspline_interp(self.handle, coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
-                            out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
+                            out_grad.data_ptr() if grad else 0, flags)
         _check(rc, "bspline_interp")
         return (out_u, out_grad) if grad else out_u
 
-    def eval(self, u_hat, x, coef=None, out_u=None, out_grad=None, grad: bool = True, stream=None):
+    def sort_order(self, x, stream=None):
+        """perm (int32 [P], device): original index of the particle evaluated i-th (bspline_sort_order);
+        x[perm] can then be passed with sorted=True."""
+        import torch
+        if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA float64 tensor [P, 3]")
+        perm = torch.empty((x.shape[0],), dtype=torch.int32, device=x.device)
+        self._stream(stream)
+        _check(bspline_sort_order(self.handle, x.data_ptr(), x.shape[0], perm.data_ptr()), "bspline_sort_order")
+        return perm
+
+    def eval(self, u_hat, x, coef=None, out_u=None, out_grad=None, grad: bool = True, stream=None,
+             sorted: bool = False):
         """coeffs(u_hat) then interp at x in one call, the particle sort overlapping the transform.
 
         Returns (coef, u, grad_u), or (coef, u) with grad=False.
@@ -356,8 +376,9 @@ class Plan:
         P = x.shape[0]
         out_u, out_grad = self._outputs(P, x.device, out_u, out_grad, grad)
         self._stream(stream)
+        flags = (0 if grad else INTERP_NO_GRAD) | (INTERP_SORTED if sorted else 0)
         rc = bspline_eval(self.handle, u_hat.data_ptr(), coef.data_ptr(), x.data_ptr(), P, out_u.data_ptr(),
-                          out_grad.data_ptr() if grad else 0, 0 if grad else INTERP_NO_GRAD)
+                          out_grad.data_ptr() if grad else 0, flags)
         _check(rc, "bspline_eval")
         return (coef, out_u, out_grad) if grad else (coef, out_u)
 

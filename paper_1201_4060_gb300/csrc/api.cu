@@ -369,7 +369,7 @@ int bspline_coeffs(bspline_plan_t plan, const void* u_hat, void* coeffs) {
 int bspline_interp(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, void* out_u,
                    void* out_grad, int flags) {
     if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
-    if (flags & ~BSPLINE_INTERP_NO_GRAD) return BSPLINE_ERR_INVALID_ARG;
+    if (flags & ~(BSPLINE_INTERP_NO_GRAD | BSPLINE_INTERP_SORTED)) return BSPLINE_ERR_INVALID_ARG;
     if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
     if (P == 0) return BSPLINE_OK;
     if (!coeffs || !x || !out_u) return BSPLINE_ERR_INVALID_ARG;
@@ -389,7 +389,7 @@ int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const dou
     const char* a = (const char*)u_hat;
     const char* b = (const char*)coeffs;
     if (a < b + coef_bytes_of(plan) && b < a + uhat_bytes_of(plan)) return BSPLINE_ERR_INVALID_ARG;
-    if (flags & ~BSPLINE_INTERP_NO_GRAD) return BSPLINE_ERR_INVALID_ARG;
+    if (flags & ~(BSPLINE_INTERP_NO_GRAD | BSPLINE_INTERP_SORTED)) return BSPLINE_ERR_INVALID_ARG;
     if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
     if (P > 0) {
         if (!x || !out_u) return BSPLINE_ERR_INVALID_ARG;
@@ -409,6 +409,16 @@ int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const dou
     if (e != cudaSuccess) return set_cuda_error(e);
     if ((rc = launch_coeffs(plan, u_hat, coeffs))) return rc;
     return launch_interp_split(plan, coeffs, x, P, out_u, out_grad, flags, plan->aux_stream, plan->ev_sorted);
+}
+
+int bspline_sort_order(bspline_plan_t plan, const double* x, int64_t P, int32_t* perm) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (P < 0 || P > 0x7fffffffLL) return BSPLINE_ERR_INVALID_ARG;
+    if (P == 0) return BSPLINE_OK;
+    if (!x || !perm || !aligned(x, 8) || !aligned(perm, 4)) return BSPLINE_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    return launch_sort_order(plan, x, P, perm);
 }
 
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P, const void* g_u,

@@ -143,6 +143,10 @@ int launch_interp_split(bspline_plan_s* p, const void* coeffs, const double* x, 
 int launch_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const void* coeffs,
                      const double* x, int64_t P, void* out_u, void* out_grad, int flags);
 
+// Brick order of P positions: perm[i] = original index of the i-th particle in
+// the order the gather evaluates them (bricks in key order, invalid positions last).
+int launch_sort_order(bspline_plan_s* p, const double* x, int64_t P, int* perm);
+
 // Adjoint: bin/sort, then spread cotangents into g_coef (accumulate; skipped
 // if NULL) and write position gradients g_x (skipped if NULL).
 int launch_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, const void* g_u,

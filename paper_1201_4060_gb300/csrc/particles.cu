@@ -72,103 +72,6 @@ namespace {
 using namespace gather_impl;
 
 // ------------------------------------------------------------------ bin
-// For 0 <= s < 2^52: base = floor(s - n/2) and t = (s - n/2) - base rounded to
-// float, computed exactly from the bits of s with integer operations (GB300's
-// FP64 pipe is narrow: only s = x N / L stays in FP64).  s = fl + fr 2^-sa
-// with integer fl and an sa-bit fraction fr; for odd n the half is folded
-// into the fraction.  Returns false outside that range.
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
-
-__device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, float* t) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
-    if (b >> 63) return false;                                 // negative
-    const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
-    if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
-    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
-    const long long hfl = n >> 1;                              // floor(n / 2)
-    if (e < 0) {                                               // s in [0, 1)
-        // below 2^-60 (or subnormal) s is 0 to the FP32 accuracy of the weights
-        const float sf = (e < -60) ? 0.f : __ull2float_rn(m) * pow2f(e - 52);
-        if (!(n & 1)) {
-            *base = -hfl;
-            *t = sf;
-        } else if (e == -1) {                                  // s in [0.5, 1): s - 1/2 = (m - 2^52) 2^-53
-            *base = -hfl;
-            *t = __ull2float_rn(m - (1ULL << 52)) * pow2f(-53);
-        } else {                                               // s in [0, 0.5)
-            *base = -hfl - 1;
-            *t = sf + 0.5f;
-        }
-        return true;
-    }
-    const int sa = 52 - e;                                     // fraction bits, 1..52
-    const long long fl = (long long)(m >> sa);
-    const unsigned long long fr = m & ((1ULL << sa) - 1);
-    if (!(n & 1)) {
-        *base = fl - hfl;
-        *t = __ull2float_rn(fr) * pow2f(-sa);
-    } else {
-        const unsigned long long hb = 1ULL << (sa - 1);        // one half in the fraction's units
-        if (fr >= hb) {
-            *base = fl - hfl;
-            *t = __ull2float_rn(fr - hb) * pow2f(-sa);
-        } else {
-            *base = fl - hfl - 1;
-            *t = __ull2float_rn(fr + hb) * pow2f(-sa);
-        }
-    }
-    return true;
-}
-
-// First stencil node modulo N (N a power of two, or 3 times one).
-__device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
-    if ((N & (N - 1)) == 0) return (unsigned)(a & (long long)(N - 1));
-    long long r = a % N;
-    return (unsigned)(r < 0 ? r + N : r);
-}
-
-// Locate one particle (Eq. alg-int-6): its brick key and record; the key is NB
-// for a non-finite position or one with no fractional bits left.
-template <typename TR>
-__device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
-                                                    int order, const BrickGrid& g, Rec<TR>* r) {
-    const unsigned NB = g.NB;
-    unsigned anc[3];
-    TR tt[3];
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double s = x[3 * p + a] * scale;
-        if constexpr (sizeof(TR) == 4) {
-            long long base;
-            float tf;
-            if (locate_nonneg(s, order, &base, &tf)) {
-                tt[a] = tf;
-                anc[a] = wrap_anchor(base + 1, N);
-                continue;
-            }
-        }
-        const double sh = s - 0.5 * order;
-        if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
-            ok = false;
-            anc[a] = 0;
-            tt[a] = 0;
-            continue;
-        }
-        const double f = floor(sh);
-        tt[a] = (TR)(sh - f);
-        anc[a] = wrap_anchor((long long)f + 1, N);
-    }
-    if (!ok) return NB;
-    r->cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
-    r->t[0] = tt[0];
-    r->t[1] = tt[1];
-    r->t[2] = tt[2];
-    return ((anc[0] >> g.bshift) * (unsigned)g.nby + anc[1] / (unsigned)g.by) * (unsigned)g.nbz + (anc[2] >> g.bshift);
-}
-
-// Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
-// counted in the status word).
 // Below this many bricks, particles of one warp often share a brick: aggregate their counter updates.
 constexpr unsigned kAggregateBricks = 4096;
 
@@ -188,10 +91,15 @@ __device__ __forceinline__ unsigned warp_increment(unsigned* counter, unsigned k
 
 // Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
 // counted in the status word).  The grid-stride loop runs warp-uniformly so that
-// lanes can aggregate their increments (aggregate = few bricks).
-template <typename TR>
+// lanes can aggregate their increments (aggregate = few bricks).  SORTED: the
+// caller passed the positions grouped by brick; each particle's key is checked
+// against its predecessor's (the lane below, or located again at a warp's
+// first lane) and *w.unsorted is set if the order is broken anywhere; invalid
+// positions get their NaN outputs here, since the placement pass may not run.
+template <typename TR, bool SORTED, typename OT>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
-                           BrickGrid g, Ws<TR> w, unsigned long long* __restrict__ status, int aggregate) {
+                           BrickGrid g, Ws<TR> w, unsigned long long* __restrict__ status, int aggregate,
+                           OT* __restrict__ out_u, OT* __restrict__ out_grad) {
     const unsigned NB = g.NB;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long lane = threadIdx.x & 31;
@@ -203,6 +111,26 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
             Rec<TR> r;
             k = locate_particle<TR>(x, p, N, scale, order, g, &r);
             if (k == NB) atomicAdd(status, 1ULL);
+        }
+        if constexpr (SORTED) {
+            unsigned prev = __shfl_up_sync(0xffffffffu, k, 1);
+            if (lane == 0 && valid && p > 0) {
+                Rec<TR> r;
+                prev = locate_particle<TR>(x, p - 1, N, scale, order, g, &r);
+            }
+            const bool broken = valid && p > 0 && prev > k;
+            if (__any_sync(0xffffffffu, broken) && lane == 0) atomicOr(w.unsorted, 1u);
+            if (valid && k == NB) {
+                const OT nan = (OT)NAN;
+                if (out_u) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) out_u[3 * p + i] = nan;
+                }
+                if (out_grad) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) out_grad[9 * p + i] = nan;
+                }
+            }
         }
         if (aggregate) {
             const unsigned active = __ballot_sync(0xffffffffu, valid);
@@ -307,12 +235,27 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
 // ------------------------------------------------------------------ place
 // Counting sort, pass 2: locate again (cheaper than storing and re-reading the
 // records) and write each record and its original index to the next free slot
-// of its brick.  Invalid positions get NaN outputs.
-template <typename TR, typename OT>
+// of its brick.  Invalid positions get NaN outputs.  SORTED: nothing to do
+// unless the count pass found the order broken.  PERM (bspline_sort_order):
+// every particle, invalid ones included (bin NB, last), gets a slot, and only
+// its original index is written there, to perm.
+template <typename TR, typename OT, bool SORTED = false, bool PERM = false>
 __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                                BrickGrid g, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
-                               int aggregate) {
+                               int aggregate, int* __restrict__ perm = nullptr) {
     const unsigned NB = g.NB;
+    if constexpr (SORTED) {
+        if (*w.unsorted == 0u) return;
+    }
+    if constexpr (PERM) {
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+            Rec<TR> r;
+            const unsigned k = locate_particle<TR>(x, p, N, scale, order, g, &r);
+            perm[atomicAdd(&w.cursor[k], 1u)] = (int)p;
+        }
+        return;
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long lane = threadIdx.x & 31;
     for (long long pw = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; pw < P; pw += stride) {
@@ -349,15 +292,15 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
 
 template <typename CT, typename AT, typename TR>
 int dispatch_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u,
-                   void* out_grad, bool grad) {
+                   void* out_grad, bool grad, SortedX sx) {
     switch (p->order) {
-        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
-        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
-        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
-        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
-        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
-        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
-        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
     }
     return BSPLINE_ERR_UNSUPPORTED_ORDER;
 }
@@ -404,10 +347,15 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
         ~Restore() { p->stream = s; }
     } restore{p, main_stream};
     cudaError_t e;
-    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
         return set_cuda_error(e);                       // non-finite count and tile-wait flag
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
+    const bool presorted = (flags & BSPLINE_INTERP_SORTED) != 0;
+    const double scale = (double)p->N / p->L;
+    const SortedX sx{presorted ? x : nullptr, scale};
+    AT* ou = (AT*)out_u;
+    AT* og = grad ? (AT*)out_grad : nullptr;
     // Beside the transform (sort_stream given), the locate passes run as a small grid-stride grid, two
     // 256-thread CTAs per SM: they then share the SMs with the transform's CTAs instead of taking them in
     // turn, and use the HBM bandwidth the transform leaves (512^3, 2^24 particles: 5.33 -> 5.04 ms per
@@ -417,10 +365,12 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     // bricks with fewer particles than this go to the direct gather (FP32 accumulation only)
     unsigned below = p->direct_below;
     if (below == BSPLINE_GATHER_SPLIT_AUTO) below = P < 12LL * NB ? 32u : 0u;
-    if (sizeof(AT) == 8) below = 0u;
+    if (sizeof(AT) == 8 || presorted) below = 0u;       // sorted input: bricks stay in input order
+    const int agg = NB < kAggregateBricks;
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<sort_grid, 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
+        if (presorted) bin_kernel<TR, true, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, p->d_status, agg, ou, og);
+        else bin_kernel<TR, false, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, p->d_status, agg, ou, og);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -429,8 +379,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u,
-                                                                 grad ? (AT*)out_grad : nullptr, NB < kAggregateBricks);
+        if (presorted) scatter_kernel<TR, AT, true><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, ou, og, agg);
+        else scatter_kernel<TR, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, ou, og, agg);
     }
     if (sort_stream) {
         if ((e = cudaEventRecord(sorted, sort_stream)) != cudaSuccess) return set_cuda_error(e);
@@ -439,7 +389,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     p->stream = main_stream;
     {
         StageTimer tm(p, BSPLINE_STAGE_GATHER);
-        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
     }
     if (rc) return rc;
     if (below > 0) {
@@ -461,15 +411,16 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     carve<TR>(&w, ws, NB, P);
     cudaStream_t st = p->stream;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
         return set_cuda_error(e);                       // non-finite count and tile-wait flag
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
-    bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status, NB < kAggregateBricks);
+    bin_kernel<TR, false, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status,
+                                                               NB < kAggregateBricks, (AT*)nullptr, (AT*)nullptr);
     scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
                                                              NB < kAggregateBricks);
-    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, SortedX{nullptr, 0.0});
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
 }
@@ -505,12 +456,14 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     carve<TR>(&w, p->pws.ptr, NB, P);
     cudaStream_t st = p->stream;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 1), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
         return set_cuda_error(e);                       // non-finite count and tile-wait flag
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
-        bin_kernel<TR><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, p->d_status, NB < kAggregateBricks);
+        bin_kernel<TR, false, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w,
+                                                                        p->d_status, NB < kAggregateBricks,
+                                                                        (double*)nullptr, (double*)nullptr);
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCAN);
@@ -534,7 +487,39 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     return set_cuda_error(cudaGetLastError());
 }
 
+// Brick order of the particles (bspline_sort_order): count, scan, then each
+// particle's original index written to its sorted slot.
+template <typename TR>
+int run_sort_order(bspline_plan_s* p, const double* x, int64_t P, int* perm) {
+    const BrickGrid g = brick_grid(p->N, p->dtype, p->order);
+    const unsigned NB = g.NB;
+    Ws<TR> w;
+    const size_t need = carve<TR>(&w, nullptr, NB, P);
+    int rc = p->pws.grow(need);
+    if (rc) return rc;
+    carve<TR>(&w, p->pws.ptr, NB, P);
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
+        return set_cuda_error(e);
+    const double scale = (double)p->N / p->L;
+    const int agg = NB < kAggregateBricks;
+    bin_kernel<TR, false, float><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, p->d_status, agg,
+                                                                   (float*)nullptr, (float*)nullptr);
+    scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
+    scatter_kernel<TR, float, false, true><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, scale, p->order, g, w,
+                                                                            (float*)nullptr, (float*)nullptr, agg,
+                                                                            perm);
+    return set_cuda_error(cudaGetLastError());
+}
+
 }  // namespace
+
+int launch_sort_order(bspline_plan_s* p, const double* x, int64_t P, int* perm) {
+    if (p->dtype == BSPLINE_F64) return run_sort_order<double>(p, x, P, perm);
+    return run_sort_order<float>(p, x, P, perm);
+}
 
 int launch_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, const void* g_u,
                              const void* g_grad, void* g_coef, double* g_x) {

@@ -515,6 +515,77 @@ def test_tma_and_cp_async_staging_agree_bit_for_bit(B, N, order):
     assert normwise(u_t.cpu().numpy(), ru) < TOL32["u"] and normwise(g_t.cpu().numpy(), rg) < TOL32["grad"]
 
 
+def brick_keys(x, N, order, dtype):
+    """Brick key of each particle from the oracle's locate (first stencil node, Eq. alg-int-6), bricks of
+    16 x 12 x 16 cells (16 x 8 x 16 above order 6; 8^3 for FP64) in x-major order; -1 for non-finite."""
+    bx, by = (8, 8) if dtype == "f64" else (16, 12 if order <= 6 else 8)
+    nbx, nby = -(-N // bx), -(-N // by)
+    ok = np.isfinite(x).all(axis=1)
+    nodes, _ = O.locate(np.where(ok[:, None], x, 0.0), N, order)
+    a = nodes[:, :, 0]
+    key = ((a[:, 0] // bx) * nby + a[:, 1] // by) * nbx + a[:, 2] // bx
+    return np.where(ok, key, -1)
+
+
+@pytest.mark.parametrize("dtype,N,order", [("f32", 64, 6), ("f32", 96, 4), ("bf16", 64, 8), ("f64", 32, 4),
+                                           ("f32", 16, 3)])
+def test_sorted_flag_bit_equal_to_unsorted_and_oracle(B, dtype, N, order):
+    """bspline_sort_order gives a permutation in brick order (keys from the oracle's locate); positions
+    permuted by it and passed with BSPLINE_INTERP_SORTED give the same bits as the sorting call, and match
+    the oracle; with the promise broken (unsorted input) the flagged call still gives the same bits."""
+    half = synth.kolmogorov_field(N, seed=80 + order).dense()
+    xs = synth.clustered_particles(20000, seed=81)
+    plan = B.Plan(N, order, dtype)
+    coef = plan.coeffs(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
+    x = torch.from_numpy(xs).cuda()
+    perm = plan.sort_order(x).long()
+    pm = perm.cpu().numpy()
+    assert np.array_equal(np.sort(pm), np.arange(len(xs)))
+    keys = brick_keys(xs, N, order, dtype)[pm]
+    assert (np.diff(keys) >= 0).all()
+    xp = x[perm].contiguous()
+    u_s, g_s = plan.interp(coef, xp, sorted=True)
+    assert plan.status() == 0
+    u_r, g_r = plan.interp(coef, xp)
+    assert torch.equal(u_s, u_r) and torch.equal(g_s, g_r)
+    # promise broken: the flagged call sorts after all
+    u_b, g_b = plan.interp(coef, x, sorted=True)
+    u_n, g_n = plan.interp(coef, x)
+    assert torch.equal(u_b, u_n) and torch.equal(g_b, g_n)
+    assert torch.equal(u_b[perm], u_s) and torch.equal(g_b[perm], g_s)
+    ru, rg = O.interpolate(rounded_input(half, dtype), xp.cpu().numpy(), order)
+    tol = {"f64": (TOL64, TOL64), "f32": (TOL32["u"], TOL32["grad"]), "bf16": (TOL16["u"], TOL16["grad"])}[dtype]
+    assert normwise(u_s.cpu().numpy(), ru) < tol[0] and normwise(g_s.cpu().numpy(), rg) < tol[1]
+
+
+def test_sorted_flag_with_nonfinite_tail_and_eval(B):
+    """Sorted positions with non-finite ones last (where bspline_sort_order puts them): NaN outputs and the
+    count in the status word; bspline_eval with the flag gives the interp call's bits."""
+    N, order = 64, 4
+    half = synth.kolmogorov_field(N, seed=90).dense()
+    xs = synth.uniform_particles(5000, seed=91)
+    xs[[7, 100, 4000]] = [[np.nan, 1.0, 1.0], [1.0, np.inf, 2.0], [0.5, 0.5, -np.inf]]
+    plan = B.Plan(N, order, "f32")
+    uh = torch.from_numpy(half).to(plan.uhat_dtype).cuda()
+    coef = plan.coeffs(uh)
+    x = torch.from_numpy(xs).cuda()
+    perm = plan.sort_order(x).long()
+    pm = perm.cpu().numpy()
+    assert set(pm[-3:].tolist()) == {7, 100, 4000}
+    xp = x[perm].contiguous()
+    u_s, g_s = plan.interp(coef, xp, sorted=True)
+    assert plan.status() == 3
+    assert torch.isnan(u_s[-3:]).all() and torch.isnan(g_s[-3:]).all()
+    assert torch.isfinite(u_s[:-3]).all() and torch.isfinite(g_s[:-3]).all()
+    u_r, g_r = plan.interp(coef, xp)
+    assert torch.equal(u_s[:-3], u_r[:-3]) and torch.equal(g_s[:-3], g_r[:-3])
+    _, u_e, g_e = plan.eval(uh, xp, sorted=True)
+    assert plan.status() == 3
+    assert torch.equal(u_e[:-3], u_s[:-3]) and torch.equal(g_e[:-3], g_s[:-3])
+    ru, rg = O.interpolate(rounded_input(half, "f32"), xp[:-3].cpu().numpy(), order)
+    assert normwise(u_s[:-3].cpu().numpy(), ru) < TOL32["u"] and normwise(g_s[:-3].cpu().numpy(), rg) < TOL32["grad"]
+
+
 def test_outputs_only_4_byte_aligned(B):
     """Outputs may start on any 4-byte boundary: the gather's 8-byte stores are used only on 8-byte
     aligned arrays, with the same results either way."""
