@@ -81,9 +81,9 @@ enum {
 #define BSPLINE_INTERP_NO_GRAD 0x1      /* out_grad may be NULL; only u is evaluated */
 /* BSPLINE_INTERP_SORTED: the positions are already grouped by the plan's
  * brick (the order bspline_sort_order gives, or any order with the same
- * brick sequence): the evaluation reads them in place and writes each
- * particle's outputs at its own index, so the placement pass of the sort is
- * skipped and the output stores stay within each brick's range (Section 5:
+ * brick sequence): the count pass writes each particle's located record in
+ * place, so the placement pass of the sort is skipped, and each particle's
+ * outputs are written at its own index within its brick's range (Section 5:
  * the stencil nodes of Eq. alg-int-6 pick the brick).  The count pass checks
  * the promise: if the order is broken anywhere, the call sorts as without
  * the flag (same results, the time of an unsorted call).  Bricks are never

@@ -72,6 +72,101 @@ namespace {
 using namespace gather_impl;
 
 // ------------------------------------------------------------------ bin
+// For 0 <= s < 2^52: base = floor(s - n/2) and t = (s - n/2) - base rounded to
+// float, computed exactly from the bits of s with integer operations (GB300's
+// FP64 pipe is narrow: only s = x N / L stays in FP64).  s = fl + fr 2^-sa
+// with integer fl and an sa-bit fraction fr; for odd n the half is folded
+// into the fraction.  Returns false outside that range.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
+
+__device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, float* t) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    if (b >> 63) return false;                                 // negative
+    const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
+    if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
+    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
+    const long long hfl = n >> 1;                              // floor(n / 2)
+    if (e < 0) {                                               // s in [0, 1)
+        // below 2^-60 (or subnormal) s is 0 to the FP32 accuracy of the weights
+        const float sf = (e < -60) ? 0.f : __ull2float_rn(m) * pow2f(e - 52);
+        if (!(n & 1)) {
+            *base = -hfl;
+            *t = sf;
+        } else if (e == -1) {                                  // s in [0.5, 1): s - 1/2 = (m - 2^52) 2^-53
+            *base = -hfl;
+            *t = __ull2float_rn(m - (1ULL << 52)) * pow2f(-53);
+        } else {                                               // s in [0, 0.5)
+            *base = -hfl - 1;
+            *t = sf + 0.5f;
+        }
+        return true;
+    }
+    const int sa = 52 - e;                                     // fraction bits, 1..52
+    const long long fl = (long long)(m >> sa);
+    const unsigned long long fr = m & ((1ULL << sa) - 1);
+    if (!(n & 1)) {
+        *base = fl - hfl;
+        *t = __ull2float_rn(fr) * pow2f(-sa);
+    } else {
+        const unsigned long long hb = 1ULL << (sa - 1);        // one half in the fraction's units
+        if (fr >= hb) {
+            *base = fl - hfl;
+            *t = __ull2float_rn(fr - hb) * pow2f(-sa);
+        } else {
+            *base = fl - hfl - 1;
+            *t = __ull2float_rn(fr + hb) * pow2f(-sa);
+        }
+    }
+    return true;
+}
+
+// First stencil node modulo N (N a power of two, or 3 times one).
+__device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
+    if ((N & (N - 1)) == 0) return (unsigned)(a & (long long)(N - 1));
+    long long r = a % N;
+    return (unsigned)(r < 0 ? r + N : r);
+}
+
+// Locate one particle (Eq. alg-int-6): its brick key and record; the key is NB
+// for a non-finite position or one with no fractional bits left.
+template <typename TR>
+__device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
+                                                    int order, const BrickGrid& g, Rec<TR>* r) {
+    const unsigned NB = g.NB;
+    unsigned anc[3];
+    TR tt[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double s = x[3 * p + a] * scale;
+        if constexpr (sizeof(TR) == 4) {
+            long long base;
+            float tf;
+            if (locate_nonneg(s, order, &base, &tf)) {
+                tt[a] = tf;
+                anc[a] = wrap_anchor(base + 1, N);
+                continue;
+            }
+        }
+        const double sh = s - 0.5 * order;
+        if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
+            ok = false;
+            anc[a] = 0;
+            tt[a] = 0;
+            continue;
+        }
+        const double f = floor(sh);
+        tt[a] = (TR)(sh - f);
+        anc[a] = wrap_anchor((long long)f + 1, N);
+    }
+    if (!ok) return NB;
+    r->cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
+    r->t[0] = tt[0];
+    r->t[1] = tt[1];
+    r->t[2] = tt[2];
+    return ((anc[0] >> g.bshift) * (unsigned)g.nby + anc[1] / (unsigned)g.by) * (unsigned)g.nbz + (anc[2] >> g.bshift);
+}
+
 // Below this many bricks, particles of one warp often share a brick: aggregate their counter updates.
 constexpr unsigned kAggregateBricks = 4096;
 
@@ -92,10 +187,12 @@ __device__ __forceinline__ unsigned warp_increment(unsigned* counter, unsigned k
 // Counting sort, pass 1: particles per brick (slot NB: invalid positions, also
 // counted in the status word).  The grid-stride loop runs warp-uniformly so that
 // lanes can aggregate their increments (aggregate = few bricks).  SORTED: the
-// caller passed the positions grouped by brick; each particle's key is checked
-// against its predecessor's (the lane below, or located again at a warp's
-// first lane) and *w.unsorted is set if the order is broken anywhere; invalid
-// positions get their NaN outputs here, since the placement pass may not run.
+// caller passed the positions grouped by brick, so position p is also the
+// particle's sorted slot: its record is written there (coalesced, its own
+// index as the original one), each key is checked against its predecessor's
+// (the lane below, or located again at a warp's first lane) and *w.unsorted is
+// set if the order is broken anywhere, in which case the placement pass
+// rewrites every record; invalid positions get their NaN outputs here.
 template <typename TR, bool SORTED, typename OT>
 __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                            BrickGrid g, Ws<TR> w, unsigned long long* __restrict__ status, int aggregate,
@@ -111,6 +208,11 @@ __global__ void bin_kernel(const double* __restrict__ x, long long P, int N, dou
             Rec<TR> r;
             k = locate_particle<TR>(x, p, N, scale, order, g, &r);
             if (k == NB) atomicAdd(status, 1ULL);
+            if (SORTED && k < NB) {
+                r.idx = (unsigned)p;
+                if constexpr (sizeof(TR) == 4) r.pad[0] = r.pad[1] = r.pad[2] = 0u;
+                w.s_rec[p] = r;
+            }
         }
         if constexpr (SORTED) {
             unsigned prev = __shfl_up_sync(0xffffffffu, k, 1);
@@ -292,15 +394,15 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
 
 template <typename CT, typename AT, typename TR>
 int dispatch_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u,
-                   void* out_grad, bool grad, SortedX sx) {
+                   void* out_grad, bool grad) {
     switch (p->order) {
-        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
-        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
-        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
-        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
-        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
-        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
-        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        case 2: return run_gather<2, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 3: return run_gather<3, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 4: return run_gather<4, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 5: return run_gather<5, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 6: return run_gather<6, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 7: return run_gather<7, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
+        case 8: return run_gather<8, CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     }
     return BSPLINE_ERR_UNSUPPORTED_ORDER;
 }
@@ -353,7 +455,6 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     const bool presorted = (flags & BSPLINE_INTERP_SORTED) != 0;
     const double scale = (double)p->N / p->L;
-    const SortedX sx{presorted ? x : nullptr, scale};
     AT* ou = (AT*)out_u;
     AT* og = grad ? (AT*)out_grad : nullptr;
     // Beside the transform (sort_stream given), the locate passes run as a small grid-stride grid, two
@@ -366,7 +467,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     unsigned below = p->direct_below;
     if (below == BSPLINE_GATHER_SPLIT_AUTO) below = P < 12LL * NB ? 32u : 0u;
     if (sizeof(AT) == 8 || presorted) below = 0u;       // sorted input: bricks stay in input order
-    const int agg = NB < kAggregateBricks;
+    const int agg = NB < kAggregateBricks || presorted;  // sorted input: a warp's particles share bricks
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
         if (presorted) bin_kernel<TR, true, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, p->d_status, agg, ou, og);
@@ -389,7 +490,7 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     p->stream = main_stream;
     {
         StageTimer tm(p, BSPLINE_STAGE_GATHER);
-        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, sx);
+        rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     }
     if (rc) return rc;
     if (below > 0) {
@@ -420,7 +521,7 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
                                                              NB < kAggregateBricks);
-    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad, SortedX{nullptr, 0.0});
+    int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
 }

@@ -75,114 +75,8 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     return off;
 }
 
-// Positions passed already grouped by brick (BSPLINE_INTERP_SORTED): the
-// gathers then locate each particle from x at its sorted position, which is
-// also its output index, and the placed records are not used.  If the count
-// pass found the order broken (*w.unsorted set), the placement pass runs and
-// the gathers read the records as for any other call.  x = nullptr: records.
-struct SortedX {
-    const double* x;
-    double scale;       // N / L
-};
-
 // Periodic grid index of i >= 0 (a single subtraction in the common case i < 2N).
 __device__ __forceinline__ int wrap_index(int i, int N) { return i < N ? i : (i < 2 * N ? i - N : i % N); }
-
-// ------------------------------------------------------------------ locate
-// For 0 <= s < 2^52: base = floor(s - n/2) and t = (s - n/2) - base rounded to
-// float, computed exactly from the bits of s with integer operations (GB300's
-// FP64 pipe is narrow: only s = x N / L stays in FP64).  s = fl + fr 2^-sa
-// with integer fl and an sa-bit fraction fr; for odd n the half is folded
-// into the fraction.  Returns false outside that range.
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
-
-__device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, float* t) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
-    if (b >> 63) return false;                                 // negative
-    const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
-    if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
-    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
-    const long long hfl = n >> 1;                              // floor(n / 2)
-    if (e < 0) {                                               // s in [0, 1)
-        // below 2^-60 (or subnormal) s is 0 to the FP32 accuracy of the weights
-        const float sf = (e < -60) ? 0.f : __ull2float_rn(m) * pow2f(e - 52);
-        if (!(n & 1)) {
-            *base = -hfl;
-            *t = sf;
-        } else if (e == -1) {                                  // s in [0.5, 1): s - 1/2 = (m - 2^52) 2^-53
-            *base = -hfl;
-            *t = __ull2float_rn(m - (1ULL << 52)) * pow2f(-53);
-        } else {                                               // s in [0, 0.5)
-            *base = -hfl - 1;
-            *t = sf + 0.5f;
-        }
-        return true;
-    }
-    const int sa = 52 - e;                                     // fraction bits, 1..52
-    const long long fl = (long long)(m >> sa);
-    const unsigned long long fr = m & ((1ULL << sa) - 1);
-    if (!(n & 1)) {
-        *base = fl - hfl;
-        *t = __ull2float_rn(fr) * pow2f(-sa);
-    } else {
-        const unsigned long long hb = 1ULL << (sa - 1);        // one half in the fraction's units
-        if (fr >= hb) {
-            *base = fl - hfl;
-            *t = __ull2float_rn(fr - hb) * pow2f(-sa);
-        } else {
-            *base = fl - hfl - 1;
-            *t = __ull2float_rn(fr + hb) * pow2f(-sa);
-        }
-    }
-    return true;
-}
-
-// First stencil node modulo N (N a power of two, or 3 times one).
-__device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
-    if ((N & (N - 1)) == 0) return (unsigned)(a & (long long)(N - 1));
-    long long r = a % N;
-    return (unsigned)(r < 0 ? r + N : r);
-}
-
-// Locate one particle (Eq. alg-int-6): its brick key and record; the key is NB
-// for a non-finite position or one with no fractional bits left.
-template <typename TR>
-__device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
-                                                    int order, const BrickGrid& g, Rec<TR>* r) {
-    const unsigned NB = g.NB;
-    unsigned anc[3];
-    TR tt[3];
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double s = x[3 * p + a] * scale;
-        if constexpr (sizeof(TR) == 4) {
-            long long base;
-            float tf;
-            if (locate_nonneg(s, order, &base, &tf)) {
-                tt[a] = tf;
-                anc[a] = wrap_anchor(base + 1, N);
-                continue;
-            }
-        }
-        const double sh = s - 0.5 * order;
-        if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
-            ok = false;
-            anc[a] = 0;
-            tt[a] = 0;
-            continue;
-        }
-        const double f = floor(sh);
-        tt[a] = (TR)(sh - f);
-        anc[a] = wrap_anchor((long long)f + 1, N);
-    }
-    if (!ok) return NB;
-    r->cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
-    r->t[0] = tt[0];
-    r->t[1] = tt[1];
-    r->t[2] = tt[2];
-    return ((anc[0] >> g.bshift) * (unsigned)g.nby + anc[1] / (unsigned)g.by) * (unsigned)g.nbz + (anc[2] >> g.bshift);
-}
 
 // ------------------------------------------------------------------ weights
 // v[m] = M_k(t + m), m = 0..k-1, for the cardinal B-spline of order k.
@@ -549,10 +443,10 @@ __device__ __forceinline__ bool tma_tile_wait(unsigned long long* bar, unsigned 
 // time-out never leaves stale values behind (the status word says why).
 template <typename TR, typename AT>
 __device__ __forceinline__ void fill_nan_item(const Ws<TR>& w, unsigned c0, unsigned n, AT* __restrict__ out_u,
-                                              AT* __restrict__ out_grad, int ncomp_u, bool from_x = false) {
+                                              AT* __restrict__ out_grad, int ncomp_u) {
     const AT nan = (AT)NAN;
     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-        const size_t idx = from_x ? (size_t)c0 + i : (size_t)w.s_rec[c0 + i].idx;
+        const size_t idx = w.s_rec[c0 + i].idx;
         if (out_u) {
             for (int k = 0; k < ncomp_u; ++k) out_u[(size_t)ncomp_u * idx + k] = nan;
         }
@@ -766,27 +660,20 @@ __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base
 template <int ORD, typename TR, bool GRAD>
 __global__ void __launch_bounds__(128)
 gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, double* __restrict__ out_u,
-           double* __restrict__ out_grad, double dscale, SortedX sx) {
+           double* __restrict__ out_grad, double dscale) {
     using S = Shape<double, ORD>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* tile = reinterpret_cast<double*>(smem_raw);
     const unsigned brick = blockIdx.x;
     const unsigned beg = w.offset[brick], end = beg + w.count[brick];
     if (beg == end) return;
-    const bool from_x = sx.x != nullptr && *w.unsorted == 0u;
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
     stage_brick<ORD, double>(tile, coef, N, x0, y0, z0);
     cp_async_wait_all();
     __syncthreads();
     for (unsigned i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        Rec<TR> rc;
-        if (from_x) {
-            locate_particle<TR>(sx.x, i, N, sx.scale, ORD, bg, &rc);
-            rc.idx = i;
-        } else {
-            rc = w.s_rec[i];
-        }
+        const Rec<TR> rc = w.s_rec[i];
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
@@ -844,7 +731,7 @@ template <int ORD, typename CT, typename TR, bool GRAD>
 __global__ void __launch_bounds__(kGatherThreads, 2)
 gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __restrict__ out_u,
            float* __restrict__ out_grad, float dscale, const __grid_constant__ CUtensorMap tmap, int use_tma,
-           unsigned long long* __restrict__ status, SortedX sx) {
+           unsigned long long* __restrict__ status) {
     using S = Shape<CT, ORD>;
     const unsigned NB = bg.NB;
     constexpr int NW = kGatherThreads / 32;
@@ -859,18 +746,6 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     const unsigned brick = w.item[item];
     const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * kChunk;
     const unsigned end = w.offset[brick] + w.count[brick];
-    const bool from_x = sx.x != nullptr && *w.unsorted == 0u;
-    // the particle at sorted position i: its record, or located from its position (sorted input)
-    auto rec_at = [&](unsigned i) -> Rec<TR> {
-        Rec<TR> r;
-        if (from_x) {
-            locate_particle<TR>(sx.x, i, N, sx.scale, ORD, bg, &r);
-            r.idx = i;
-        } else {
-            r = w.s_rec[i];
-        }
-        return r;
-    };
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
     // BF16 tiles of orders 6-8 are copied raw and asynchronously (widened after the bucketing)
@@ -899,7 +774,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
         for (int k = 0; k < KT; ++k) {
             const int i = threadIdx.x + k * kGatherThreads;
             if (i < n) {
-                const unsigned cp = rec_at(c0 + i).cell;
+                const unsigned cp = w.s_rec[c0 + i].cell;
                 const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(cp & 1023u) - z0;
@@ -925,7 +800,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
         }
         cp_async_wait_all();
         if (tma && !tma_tile_wait(&s_mbar, status + kStatusParticleTimeout)) {
-            fill_nan_item<TR, float>(w, c0, (unsigned)n, out_u, GRAD ? out_grad : nullptr, 3, from_x);
+            fill_nan_item<TR, float>(w, c0, (unsigned)n, out_u, GRAD ? out_grad : nullptr, 3);
             return;
         }
         __syncthreads();                                  // tile and order ready
@@ -966,7 +841,10 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             job_range(j, &lo, &hi);
             const unsigned pos = lo + (unsigned)lane;
             v_n = pos < hi;
-            if (v_n) rc_n = rec_at(c0 + s_order[pos]);
+            if (v_n) {
+                const unsigned i = c0 + s_order[pos];
+                rc_n = w.s_rec[i];
+            }
         };
         // Jobs are dealt to the NW warps in rounds.  A last, partly filled round
         // of m <= 2 NW / 3 jobs is run per component instead: 3 m shorter warp
@@ -1007,7 +885,8 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             job_range(jfull + q / 3, &lo, &hi);
             const unsigned pos = lo + (unsigned)lane;
             if (pos < hi) {
-                const Rec<TR> rc = rec_at(c0 + s_order[pos]);
+                const unsigned i = c0 + s_order[pos];
+                const Rec<TR> rc = w.s_rec[i];
                 const unsigned idx = rc.idx;
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
@@ -1092,7 +971,7 @@ template <typename K> int set_smem(K kernel, size_t bytes) {
 
 template <int ORD, typename CT, typename AT, typename TR>
 int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, void* out_u, void* out_grad,
-               bool grad, SortedX sx) {
+               bool grad) {
     const unsigned NB = g.NB;
     const size_t sm = tile_bytes<ORD, CT>();
     const AT dscale = (AT)((double)p->N / p->L);
@@ -1101,7 +980,7 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, voi
         auto k = grad ? gather_f64<ORD, TR, true> : gather_f64<ORD, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
         k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const double*>(coeffs), p->N, g, w, (double*)out_u,
-                                      grad ? (double*)out_grad : nullptr, dscale, sx);
+                                      grad ? (double*)out_grad : nullptr, dscale);
     } else {
         auto k = grad ? gather_f32<ORD, CT, TR, true> : gather_f32<ORD, CT, TR, false>;
         const size_t sm_aligned = sm + 128;              // room to align the tile to 128 bytes
@@ -1118,7 +997,7 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, voi
         const long long items = (long long)NB + (w.P + kChunk - 1) / kChunk;
         k<<<(unsigned)items, kGatherThreads, sm_aligned, p->stream>>>(
             reinterpret_cast<const CT*>(coeffs), p->N, g, w, (float*)out_u, grad ? (float*)out_grad : nullptr, dscale,
-            tmap, use_tma, p->d_status, sx);
+            tmap, use_tma, p->d_status);
     }
     return BSPLINE_OK;
 }
@@ -1149,13 +1028,12 @@ int run_gather_direct(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid
 #define BS_GATHER_EXTERN(ORD, CT, AT, TR)                                                                 \
     extern template int gather_impl::run_gather<ORD, CT, AT, TR>(bspline_plan_s*, const void*,               \
                                                                   gather_impl::Ws<TR>, BrickGrid, void*,     \
-                                                                  void*, bool, gather_impl::SortedX);        \
+                                                                  void*, bool);                              \
     extern template int gather_impl::run_gather_direct<ORD, CT, AT, TR>(                                     \
         bspline_plan_s*, const void*, gather_impl::Ws<TR>, BrickGrid, void*, void*, bool, unsigned);
 #define BS_GATHER_INSTANTIATE(ORD, CT, AT, TR)                                                          \
     template int gather_impl::run_gather<ORD, CT, AT, TR>(bspline_plan_s*, const void*, gather_impl::Ws<TR>, \
-                                                           BrickGrid, void*, void*, bool,                   \
-                                                           gather_impl::SortedX);                           \
+                                                           BrickGrid, void*, void*, bool);                  \
     template int gather_impl::run_gather_direct<ORD, CT, AT, TR>(bspline_plan_s*, const void*,               \
                                                                   gather_impl::Ws<TR>, BrickGrid, void*,     \
                                                                   void*, bool, unsigned);
