@@ -637,6 +637,8 @@ def run_batch(B, device, steps=10, warmup=3):
         return e0.elapsed_time(e1) / steps
 
     ms_graph = timed(lambda: batch.launch(stream))
+    cfg = batch.config()
+    status, nonfinite = batch.status()
 
     def eager():
         for i in range(len(plans)):
@@ -649,7 +651,11 @@ def run_batch(B, device, steps=10, warmup=3):
                        f"seed {wl['field_seed']} + i), order-{order} B-spline, f32 coefficients, uniform particles "
                        f"log-uniform 1e3..1e6 per field (seed {wl['particle_seed']}), {total} in all",
            "particles": total, "particles_per_s": total / (ms_graph / 1e3), "ms_per_batch": ms_graph,
-           "graph_streams": k, "launches_per_batch": 1,
+           "graph_streams": k, "graph_launches_per_batch": 1, "kernel_launches_per_batch": cfg["kernel_nodes"],
+           "particle_side": ("one persistent queue kernel (count, scan, placement and gather tasks of every field)"
+                             if cfg["queue"] else "per-field kernels"),
+           "queue_brick_y": cfg["brick_y"], "queue_item_particles": cfg["item_particles"],
+           "status": status, "nonfinite": nonfinite,
            "eager_ms_per_batch": ms_eager, "eager_particles_per_s": total / (ms_eager / 1e3),
            "steps": steps, "warmup": warmup}
     batch.close()

@@ -342,6 +342,15 @@ int bspline_interp_noalloc(const void* coeffs, int N, int order, bspline_dtype d
 /* ---- Batches of independent fields.  No counterpart in the paper: a launch
  * structure for many small fields (grid size, order and dtype may differ per
  * field), whose short kernels would otherwise leave the GPU idle.
+ * When every field has an FP32 plan of one order and u and grad u are wanted
+ * for every field with particles, the particle side of all fields runs as one
+ * persistent kernel after the transforms: a device work queue of count, scan,
+ * placement and gather tasks (the steps of bspline_interp; Section 5 locate,
+ * Sections 3-4 evaluation), taken in order by every CTA, each task waiting
+ * (bounded, about a second) for the tasks of its field that it needs; it
+ * stages bricks of 16 x brick_y x 16 cells and gathers up to item_particles
+ * particles of a brick per task (both tuned by bspline_batch_autotune).
+ * Other batches record each field's bspline_interp after its transform.
  * bspline_batch_create: nfields >= 1 plans (all on one device; one plan may
  * serve several fields, which then run one after another).  The batch keeps
  * the plan handles, not ownership: destroy it before its plans.
@@ -369,6 +378,38 @@ int bspline_batch_capture(bspline_batch_t batch, int streams, const void* const*
 int bspline_batch_launch(bspline_batch_t batch, void* stream);
 int bspline_batch_autotune(bspline_batch_t batch, void* stream, int* best_streams, double* best_ms);
 int bspline_batch_destroy(bspline_batch_t batch);
+
+/* bspline_batch_autotune (continued): for a batch that runs the queue it then
+ * times brick_y in {8, 12, 16} (12 up to order 6) and item_particles in {512,
+ * 1024, 2048} at the best stream count and keeps the fastest.  If the
+ * environment variable BSPLINE_AUTOTUNE_CACHE names a file, a choice recorded
+ * there for the same GPU, order, dtype and fields (grids, particle counts,
+ * grad) is recaptured without timing (*best_ms = 0), and a new choice is
+ * appended as one JSON line.
+ * bspline_batch_set_layout: queue = -1 (use the queue when the fields allow
+ * it, the default), 0 (never), 1 (required: BSPLINE_ERR_NOT_IMPLEMENTED if
+ * the fields do not allow it); brick_y_cells 0 (the plans' default), 8, 12 or
+ * 16 (8 or 16 above order 6); item_particles 32..2048.  Recaptures if
+ * arguments were captured before.
+ * bspline_batch_config: the current graph's choices; queue = 1 if it runs the
+ * queue kernel; kernel_nodes = kernel launches in one replay of the graph.
+ * Any output pointer may be NULL.
+ * bspline_batch_status: synchronises the stream of the last launch and reads
+ * the queue's status: BSPLINE_ERR_TIMEOUT if a wait of that launch ran out
+ * (the outputs of that launch are then unspecified), else
+ * BSPLINE_ERR_NONFINITE_INPUT with the count of non-finite positions over all
+ * fields in *nonfinite, else BSPLINE_OK (also for a batch without the queue,
+ * whose plans report through bspline_status).
+ * bspline_batch_set_test_hooks: BSPLINE_TEST_DROP_QUEUE_SIGNAL makes the
+ * first count task of field 0 skip its completion signal, so the scan of
+ * field 0 waits until its bounded wait runs out; it exists to test that
+ * error path.  0 clears.  Recaptures if arguments were captured before. */
+#define BSPLINE_TEST_DROP_QUEUE_SIGNAL 0x8
+int bspline_batch_set_layout(bspline_batch_t batch, int queue, int brick_y_cells, int item_particles);
+int bspline_batch_config(bspline_batch_t batch, int* queue, int* streams, int* brick_y_cells, int* item_particles,
+                         int* kernel_nodes);
+int bspline_batch_status(bspline_batch_t batch, int64_t* nonfinite);
+int bspline_batch_set_test_hooks(bspline_batch_t batch, int hooks);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbspline.so")
 SOURCES = ["api.cu", "fft.cu", "particles.cu", "gather_f64_lo.cu", "gather_f64_hi.cu", "gather_f32_lo.cu",
            "gather_f32_hi.cu", "gather_bf16_lo.cu", "gather_bf16_hi.cu", "noalloc.cu", "adjoint_fft.cu",
-           "adjoint_f32.cu", "adjoint_bf16.cu", "adjoint_f64.cu", "batch.cu"]
+           "adjoint_f32.cu", "adjoint_bf16.cu", "adjoint_f64.cu", "batch.cu", "batch_q_o2.cu", "batch_q_o3.cu",
+           "batch_q_o4.cu", "batch_q_o5.cu", "batch_q_o6.cu", "batch_q_o7.cu", "batch_q_o8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]

@@ -88,6 +88,10 @@ def _load() -> ctypes.CDLL:
         "bspline_batch_launch": (i32, [vp, vp]),
         "bspline_batch_autotune": (i32, [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]),
         "bspline_batch_destroy": (i32, [vp]),
+        "bspline_batch_set_layout": (i32, [vp, i32, i32, i32]),
+        "bspline_batch_config": (i32, [vp] + [ctypes.POINTER(i32)] * 5),
+        "bspline_batch_status": (i32, [vp, ctypes.POINTER(i64)]),
+        "bspline_batch_set_test_hooks": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -221,6 +225,7 @@ STAGES = ["fft_x", "fft_yz", "bin", "scan", "scatter", "gather", "spread", "grad
 TEST_DROP_TRANSFORM_SIGNALS = 0x1
 TEST_NO_TMA = 0x2
 TEST_SKIP_TMA_ISSUE = 0x4
+TEST_DROP_QUEUE_SIGNAL = 0x8
 
 
 def bspline_plan_set_test_hooks(plan: int, hooks: int) -> int:
@@ -534,6 +539,26 @@ class Batch:
         _check(_load().bspline_batch_autotune(self.handle, s.cuda_stream, ctypes.byref(k), ctypes.byref(ms)),
                "bspline_batch_autotune")
         return k.value, ms.value
+
+    def set_layout(self, queue: int = -1, brick_y: int = 0, item_particles: int = 2048) -> None:
+        """Queue use (-1 auto, 0 never, 1 required), brick y extent and particles per gather item."""
+        _check(_load().bspline_batch_set_layout(self.handle, queue, brick_y, item_particles),
+               "bspline_batch_set_layout")
+
+    def config(self) -> dict:
+        vals = [ctypes.c_int() for _ in range(5)]
+        _check(_load().bspline_batch_config(self.handle, *[ctypes.byref(v) for v in vals]), "bspline_batch_config")
+        keys = ("queue", "streams", "brick_y", "item_particles", "kernel_nodes")
+        return {k: v.value for k, v in zip(keys, vals)}
+
+    def status(self) -> tuple[int, int]:
+        """(status code, non-finite positions) of the last launch's queue (bspline_batch_status)."""
+        n = ctypes.c_int64()
+        rc = _load().bspline_batch_status(self.handle, ctypes.byref(n))
+        return rc, n.value
+
+    def set_test_hooks(self, hooks: int) -> None:
+        _check(_load().bspline_batch_set_test_hooks(self.handle, hooks), "bspline_batch_set_test_hooks")
 
     def close(self) -> None:
         if getattr(self, "handle", 0):

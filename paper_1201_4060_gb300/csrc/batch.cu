@@ -2,17 +2,24 @@
 //
 // The paper evaluates one field at a time; many small fields (different grid
 // sizes and particle counts) leave most of the GPU idle between the short
-// kernels of each.  A batch records the coefficient transform and the
-// evaluation of every field into one graph: fields go round-robin over K
-// concurrent streams (a plan's fields stay on one stream, since they share
-// its workspace), and the graph is replayed with one launch.  K is chosen by
-// timing the captured graph for K = 1, 2, 4, ... (bspline_batch_autotune).
+// kernels of each.  A batch records the coefficient transform of every field
+// into one graph, the fields round-robin over K concurrent streams (a plan's
+// fields stay on one stream, since they share its workspace).  The particle
+// side of every field then runs as ONE persistent kernel walking a device
+// work queue of count, scan, placement and gather tasks (batch_queue.cuh),
+// when the fields allow it (FP32 coefficients, one order, u and grad u);
+// otherwise each field's evaluation is recorded after its transform.  The
+// graph is replayed with one launch.  K, the queue's brick y extent and its
+// particles per gather item are chosen by timing (bspline_batch_autotune).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <new>
 #include <vector>
 
-#include "internal.h"
+#include "batch_queue.cuh"
 
 struct bspline_batch_s {
     int n = 0;
@@ -32,6 +39,17 @@ struct bspline_batch_s {
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // persistent particle queue (batch_queue.cuh)
+    int queue = -1;                     // -1: use it when the fields allow; 0: never; 1: required
+    int brick_y = 0;                    // 0: the plans' default
+    int item_particles = 2048;
+    int hooks = 0;
+    bool queue_used = false;            // the current graph runs the queue kernel
+    int kernel_nodes = 0;               // kernel nodes of the current graph
+    bs::DeviceBuffer qbuf;              // status, counters, per-field counts, descriptors, workspaces
+    size_t zero_bytes = 0;              // leading bytes of qbuf cleared before every launch
+    bs::batch_impl::Queue q{};
+    cudaStream_t last_stream = nullptr; // stream of the last launch (bspline_batch_status)
 };
 
 namespace {
@@ -61,8 +79,147 @@ int ensure_streams(bspline_batch_s* b, int k) {
     return set_cuda_error(e);
 }
 
+using batch_impl::FieldDesc;
+
+constexpr unsigned kQueuePartsPerTask = 8192;       // particles of one count / placement task
+
+// Whether the fields can run through the persistent queue: FP32 plans of one
+// order, u and grad u for every field with particles.
+bool queue_eligible(const bspline_batch_s* b) {
+    const int order = b->plans[0]->order;
+    for (int i = 0; i < b->n; ++i) {
+        const bspline_plan_s* p = b->plans[i];
+        if (p->dtype != BSPLINE_F32 || p->order != order) return false;
+        if (b->P[i] > 0 && !b->out_grad[i]) return false;
+    }
+    return true;
+}
+
+// The queue's brick grid of a field: 16 x by x 16 cells.
+BrickGrid queue_grid(int N, int by) {
+    BrickGrid g;
+    g.nbx = (N + 15) / 16;
+    g.nby = (N + by - 1) / by;
+    g.nbz = g.nbx;
+    g.by = by;
+    g.bshift = 4;
+    g.NB = (unsigned)g.nbx * g.nby * g.nbz;
+    return g;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Lay out and upload the queue of the current arguments: [status | counters |
+// every field's brick counts] (cleared before each launch), then the field
+// descriptors, the two task prefix arrays and each field's sort workspace.
+int build_queue(bspline_batch_s* b, int by, unsigned chunk_len) {
+    const int F = b->n;
+    std::vector<BrickGrid> grids(F);
+    std::vector<unsigned> task_pre(F + 1, 0), item_pre(F + 1, 0);
+    size_t counts = 0;
+    for (int i = 0; i < F; ++i) {
+        grids[i] = queue_grid(b->plans[i]->N, by);
+        const long long P = b->P[i];
+        task_pre[i + 1] = task_pre[i] + (unsigned)((P + kQueuePartsPerTask - 1) / kQueuePartsPerTask);
+        item_pre[i + 1] = item_pre[i] + (P > 0 ? grids[i].NB + (unsigned)((P + chunk_len - 1) / chunk_len) : 0u);
+        counts += grids[i].NB + 2;
+    }
+    const size_t off_status = 0;
+    const size_t off_ctr = 16;
+    const size_t off_counts = off_ctr + sizeof(unsigned) * (2 + 3 * (size_t)F);
+    const size_t zero = off_counts + sizeof(unsigned) * counts;
+    const size_t off_desc = align256(zero);
+    const size_t off_tpre = align256(off_desc + sizeof(FieldDesc) * F);
+    const size_t off_ipre = align256(off_tpre + sizeof(unsigned) * (F + 1));
+    size_t off = align256(off_ipre + sizeof(unsigned) * (F + 1));
+    std::vector<size_t> off_ws(F);
+    for (int i = 0; i < F; ++i) {
+        gather_impl::Ws<float> w;
+        off_ws[i] = off;
+        off = align256(off + gather_impl::carve<float>(&w, nullptr, grids[i].NB, b->P[i], chunk_len));
+    }
+    int rc = b->qbuf.grow(off);
+    if (rc) return rc;
+    char* base = static_cast<char*>(b->qbuf.ptr);
+    std::vector<FieldDesc> desc(F);
+    size_t cofs = 0;
+    for (int i = 0; i < F; ++i) {
+        const bspline_plan_s* p = b->plans[i];
+        FieldDesc& d = desc[i];
+        d.coef = static_cast<const float*>(b->coeffs[i]);
+        d.x = b->x[i];
+        d.out_u = static_cast<float*>(b->out_u[i]);
+        d.out_grad = static_cast<float*>(b->out_grad[i]);
+        d.P = b->P[i];
+        d.N = p->N;
+        d.scale = (double)p->N / p->L;
+        d.dscale = (float)((double)p->N / p->L);
+        d.bg = grids[i];
+        gather_impl::carve<float>(&d.w, base + off_ws[i], grids[i].NB, b->P[i], chunk_len);
+        d.w.count = reinterpret_cast<unsigned*>(base + off_counts) + cofs;   // the cleared block
+        d.w.unsorted = d.w.count + grids[i].NB + 1;
+        cofs += grids[i].NB + 2;
+    }
+    cudaError_t e = cudaMemcpy(base + off_desc, desc.data(), sizeof(FieldDesc) * F, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_tpre, task_pre.data(), sizeof(unsigned) * (F + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + off_ipre, item_pre.data(), sizeof(unsigned) * (F + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(base, 0, zero);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    b->zero_bytes = zero;
+    batch_impl::Queue& q = b->q;
+    q.fields = reinterpret_cast<const FieldDesc*>(base + off_desc);
+    q.task_pre = reinterpret_cast<const unsigned*>(base + off_tpre);
+    q.item_pre = reinterpret_cast<const unsigned*>(base + off_ipre);
+    q.ctr = reinterpret_cast<unsigned*>(base + off_ctr);
+    q.status = reinterpret_cast<unsigned long long*>(base + off_status);
+    q.F = F;
+    q.part_per_task = kQueuePartsPerTask;
+    q.chunk_len = chunk_len;
+    q.drop_first_signal = (b->hooks & BSPLINE_TEST_DROP_QUEUE_SIGNAL) ? 1 : 0;
+    return BSPLINE_OK;
+}
+
+int launch_queue(int order, int by, const batch_impl::Queue& q, int sms, cudaStream_t st) {
+    using namespace batch_impl;
+    switch (order) {
+        case 2: return launch_batch_queue_o2(by, q, sms, st);
+        case 3: return launch_batch_queue_o3(by, q, sms, st);
+        case 4: return launch_batch_queue_o4(by, q, sms, st);
+        case 5: return launch_batch_queue_o5(by, q, sms, st);
+        case 6: return launch_batch_queue_o6(by, q, sms, st);
+        case 7: return launch_batch_queue_o7(by, q, sms, st);
+        case 8: return launch_batch_queue_o8(by, q, sms, st);
+    }
+    return BSPLINE_ERR_UNSUPPORTED_ORDER;
+}
+
+int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    int k = 0;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(node, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 // Record every field into a new graph on k streams.
 int capture(bspline_batch_s* b, int k) {
+    if (b->last_stream || b->exec) {                  // the buffers below may still be in use by a launch
+        cudaError_t e = cudaStreamSynchronize(b->last_stream);
+        if (e != cudaSuccess) return set_cuda_error(e);
+    }
     drop_graph(b);
     std::map<bspline_plan_t, int> lane;             // plan -> stream
     for (int i = 0; i < b->n; ++i) {
@@ -73,11 +230,23 @@ int capture(bspline_batch_s* b, int k) {
     k = std::min<int>(k, (int)lane.size());
     int rc = ensure_streams(b, k);
     if (rc) return rc;
+    const bool eligible = queue_eligible(b);
+    if (b->queue == 1 && !eligible) return BSPLINE_ERR_NOT_IMPLEMENTED;
+    const bool use_queue = b->queue != 0 && eligible;
+    const int order = b->plans[0]->order;
+    int by = b->brick_y ? b->brick_y : brick_y(BSPLINE_F32, order);
+    if (use_queue) {
+        if (!batch_impl::queue_brick_y_ok(order, by)) return BSPLINE_ERR_INVALID_ARG;
+        if ((rc = build_queue(b, by, (unsigned)b->item_particles))) return rc;
+    }
+    int sms = 1;
+    cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e0 != cudaSuccess) return set_cuda_error(e0);
     // workspaces are allocated now: no allocation may happen inside the capture
     for (int i = 0; i < b->n; ++i) {
         bspline_plan_t p = b->plans[i];
         if ((rc = p->work.grow(coeffs_workspace_bytes(p)))) return rc;
-        if ((rc = p->pws.grow(interp_workspace_bytes(p, b->P[i])))) return rc;
+        if (!use_queue && (rc = p->pws.grow(interp_workspace_bytes(p, b->P[i])))) return rc;
     }
     std::vector<cudaStream_t> saved(b->n);
     std::vector<bool> timing(b->n);
@@ -87,6 +256,8 @@ int capture(bspline_batch_s* b, int k) {
         b->plans[i]->timing = false;
     }
     cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    // the queue's status, counters and brick counts start at zero (cleared while the transforms run)
+    if (e == cudaSuccess && use_queue) e = cudaMemsetAsync(b->qbuf.ptr, 0, b->zero_bytes, b->origin);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
     for (int s = 0; s < k && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->side[s], b->fork, 0);
     rc = set_cuda_error(e);
@@ -94,7 +265,7 @@ int capture(bspline_batch_s* b, int k) {
         bspline_plan_t p = b->plans[i];
         p->stream = b->side[lane[p] % k];
         rc = bspline_coeffs(p, b->u_hat[i], b->coeffs[i]);
-        if (rc == BSPLINE_OK)
+        if (rc == BSPLINE_OK && !use_queue)
             rc = bspline_interp(p, b->coeffs[i], b->x[i], b->P[i], b->out_u[i], b->out_grad[i],
                                 b->out_grad[i] ? 0 : BSPLINE_INTERP_NO_GRAD);
     }
@@ -102,6 +273,8 @@ int capture(bspline_batch_s* b, int k) {
         cudaEventRecord(b->join[s], b->side[s]);
         cudaStreamWaitEvent(b->origin, b->join[s], 0);
     }
+    // every field's particles, after every transform: one persistent kernel
+    if (rc == BSPLINE_OK && use_queue) rc = launch_queue(order, by, b->q, sms, b->origin);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->origin, &g);
     for (int i = 0; i < b->n; ++i) {
@@ -121,7 +294,45 @@ int capture(bspline_batch_s* b, int k) {
         return set_cuda_error(e);
     }
     b->streams = k;
+    b->queue_used = use_queue;
+    b->kernel_nodes = count_kernel_nodes(g);
     return BSPLINE_OK;
+}
+
+// One graph launch, timed: mean ms of `reps` launches after two warm-ups.
+int time_graph(bspline_batch_s* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms) {
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = cudaGraphLaunch(b->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    *ms /= (float)reps;
+    return set_cuda_error(e);
+}
+
+// Cache key of a batch: GPU, order, dtype, the fields' grids and particle counts (FNV-1a hash).
+void batch_key(const bspline_batch_s* b, char* out, size_t len) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) {
+        cudaGetLastError();
+        std::strcpy(prop.name, "unknown");
+    }
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&](unsigned long long v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xffu;
+            h *= 1099511628211ULL;
+        }
+    };
+    for (int i = 0; i < b->n; ++i) {
+        mix((unsigned long long)b->plans[i]->N);
+        mix((unsigned long long)b->P[i]);
+        mix((unsigned long long)(b->out_grad[i] != nullptr));
+    }
+    std::snprintf(out, len, "batch|%s|F%d|o%d|t%d|%016llx", prop.name, b->n, b->plans[0]->order,
+                  b->plans[0]->dtype, h);
 }
 
 // Device guard for the batch's device.
@@ -182,6 +393,7 @@ int bspline_batch_launch(bspline_batch_t b, void* stream) {
     if (!b || !b->exec) return BSPLINE_ERR_INVALID_ARG;
     Guard g(b->device);
     if (!g.ok) return BSPLINE_ERR_CUDA;
+    b->last_stream = (cudaStream_t)stream;
     return set_cuda_error(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
 }
 
@@ -190,43 +402,150 @@ int bspline_batch_autotune(bspline_batch_t b, void* stream, int* best_streams, d
     Guard g(b->device);
     if (!g.ok) return BSPLINE_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    char key[512];
+    batch_key(b, key, sizeof key);
+    const char* path = std::getenv("BSPLINE_AUTOTUNE_CACHE");
+    if (path && *path) {
+        if (FILE* f = std::fopen(path, "r")) {
+            char line[1024], want[600];
+            std::snprintf(want, sizeof want, "\"key\": \"%s\"", key);
+            int ks = 0, by = 0, ip = 0, found = 0;
+            while (std::fgets(line, sizeof line, f)) {
+                const char* a1 = std::strstr(line, "\"streams\": ");
+                const char* a2 = std::strstr(line, "\"brick_y\": ");
+                const char* a3 = std::strstr(line, "\"item_particles\": ");
+                if (std::strstr(line, want) && a1 && a2 && a3 && std::sscanf(a1 + 11, "%d", &ks) == 1 &&
+                    std::sscanf(a2 + 11, "%d", &by) == 1 && std::sscanf(a3 + 18, "%d", &ip) == 1)
+                    found = 1;                           // the last match wins
+            }
+            std::fclose(f);
+            if (found) {
+                b->brick_y = by;
+                b->item_particles = ip;
+                int rc = capture(b, ks);
+                if (rc) return rc;
+                if (best_streams) *best_streams = b->streams;
+                if (best_ms) *best_ms = 0.0;
+                return BSPLINE_OK;
+            }
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     int rc = set_cuda_error(e);
+    // 1. streams of the transforms, with the queue at its current layout
     int best_k = 1, prev = 0;
     float best = 0.f;
     for (int k = 1; k <= 16 && rc == BSPLINE_OK; k *= 2) {
         if ((rc = capture(b, k))) break;
         if (b->streams == prev) break;             // fewer distinct plans than streams: nothing new to try
         prev = b->streams;
-        for (int w = 0; w < 2 && rc == BSPLINE_OK; ++w) rc = set_cuda_error(cudaGraphLaunch(b->exec, st));
-        if (rc) break;
-        e = cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->exec, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if ((rc = set_cuda_error(e))) break;
+        if ((rc = time_graph(b, st, e0, e1, 3, &ms))) break;
         if (k == 1 || ms < best) {
             best = ms;
             best_k = b->streams;
         }
     }
+    // 2. the queue's brick y extent and particles per gather item
+    int best_by = b->brick_y, best_ip = b->item_particles;
+    if (rc == BSPLINE_OK && b->queue != 0 && queue_eligible(b)) {
+        const int order = b->plans[0]->order;
+        static const int kBy[] = {8, 12, 16};
+        static const int kItem[] = {512, 1024, 2048};
+        for (int by : kBy) {
+            if (!batch_impl::queue_brick_y_ok(order, by)) continue;
+            for (int ip : kItem) {
+                b->brick_y = by;
+                b->item_particles = ip;
+                if ((rc = capture(b, best_k))) break;
+                float ms = 0.f;
+                if ((rc = time_graph(b, st, e0, e1, 3, &ms))) break;
+                if (ms < best) {
+                    best = ms;
+                    best_by = by;
+                    best_ip = ip;
+                }
+            }
+            if (rc) break;
+        }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    b->brick_y = best_by;
+    b->item_particles = best_ip;
     if (rc) return rc;
     if ((rc = capture(b, best_k))) return rc;
     if (best_streams) *best_streams = best_k;
-    if (best_ms) *best_ms = best / 3.0;
+    if (best_ms) *best_ms = best;
+    if (path && *path) {
+        if (FILE* f = std::fopen(path, "a")) {
+            const int by = b->brick_y ? b->brick_y : brick_y(BSPLINE_F32, b->plans[0]->order);
+            std::fprintf(f, "{\"key\": \"%s\", \"streams\": %d, \"brick_y\": %d, \"item_particles\": %d, "
+                            "\"ms\": %.4f}\n", key, best_k, by, b->item_particles, best);
+            std::fclose(f);
+        }
+    }
     return BSPLINE_OK;
+}
+
+int bspline_batch_set_layout(bspline_batch_t b, int queue, int brick_y_cells, int item_particles) {
+    if (!b || queue < -1 || queue > 1) return BSPLINE_ERR_INVALID_ARG;
+    if (brick_y_cells != 0 && brick_y_cells != 8 && brick_y_cells != 12 && brick_y_cells != 16)
+        return BSPLINE_ERR_INVALID_ARG;
+    if (item_particles < 32 || item_particles > (int)gather_impl::kChunk) return BSPLINE_ERR_INVALID_ARG;
+    if (brick_y_cells && !batch_impl::queue_brick_y_ok(b->plans[0]->order, brick_y_cells))
+        return BSPLINE_ERR_INVALID_ARG;
+    b->queue = queue;
+    b->brick_y = brick_y_cells;
+    b->item_particles = item_particles;
+    if (!b->have_args) return BSPLINE_OK;
+    Guard g(b->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    return capture(b, b->streams ? b->streams : 1);
+}
+
+int bspline_batch_config(bspline_batch_t b, int* queue, int* streams, int* brick_y_cells, int* item_particles,
+                         int* kernel_nodes) {
+    if (!b) return BSPLINE_ERR_INVALID_ARG;
+    if (queue) *queue = b->queue_used ? 1 : 0;
+    if (streams) *streams = b->streams;
+    if (brick_y_cells) *brick_y_cells = b->brick_y ? b->brick_y : brick_y(BSPLINE_F32, b->plans[0]->order);
+    if (item_particles) *item_particles = b->item_particles;
+    if (kernel_nodes) *kernel_nodes = b->kernel_nodes;
+    return BSPLINE_OK;
+}
+
+int bspline_batch_set_test_hooks(bspline_batch_t b, int hooks) {
+    if (!b || (hooks & ~BSPLINE_TEST_DROP_QUEUE_SIGNAL)) return BSPLINE_ERR_INVALID_ARG;
+    b->hooks = hooks;
+    if (!b->have_args) return BSPLINE_OK;
+    Guard g(b->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    return capture(b, b->streams ? b->streams : 1);
+}
+
+int bspline_batch_status(bspline_batch_t b, int64_t* nonfinite) {
+    if (!b) return BSPLINE_ERR_INVALID_ARG;
+    if (nonfinite) *nonfinite = 0;
+    if (!b->queue_used) return BSPLINE_OK;
+    Guard g(b->device);
+    if (!g.ok) return BSPLINE_ERR_CUDA;
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaStreamSynchronize(b->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h, b->q.status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (nonfinite) *nonfinite = (int64_t)h[0];
+    if (h[1]) return BSPLINE_ERR_TIMEOUT;
+    return h[0] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
 }
 
 int bspline_batch_destroy(bspline_batch_t b) {
     if (!b) return BSPLINE_OK;
     Guard g(b->device);
     drop_graph(b);
+    b->qbuf.release();
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);

@@ -1,0 +1,10 @@
+// Persistent batch kernel (u and grad u, FP32 coefficients) of order 7, every brick y extent.
+#include "batch_queue.cuh"
+
+namespace bs {
+namespace batch_impl {
+int launch_batch_queue_o7(int by, const Queue& q, int sms, cudaStream_t stream) {
+    return dispatch_brick_y<7>(by, q, sms, stream);
+}
+}  // namespace batch_impl
+}  // namespace bs

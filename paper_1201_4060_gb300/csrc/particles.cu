@@ -72,101 +72,6 @@ namespace {
 using namespace gather_impl;
 
 // ------------------------------------------------------------------ bin
-// For 0 <= s < 2^52: base = floor(s - n/2) and t = (s - n/2) - base rounded to
-// float, computed exactly from the bits of s with integer operations (GB300's
-// FP64 pipe is narrow: only s = x N / L stays in FP64).  s = fl + fr 2^-sa
-// with integer fl and an sa-bit fraction fr; for odd n the half is folded
-// into the fraction.  Returns false outside that range.
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
-
-__device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, float* t) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
-    if (b >> 63) return false;                                 // negative
-    const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
-    if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
-    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
-    const long long hfl = n >> 1;                              // floor(n / 2)
-    if (e < 0) {                                               // s in [0, 1)
-        // below 2^-60 (or subnormal) s is 0 to the FP32 accuracy of the weights
-        const float sf = (e < -60) ? 0.f : __ull2float_rn(m) * pow2f(e - 52);
-        if (!(n & 1)) {
-            *base = -hfl;
-            *t = sf;
-        } else if (e == -1) {                                  // s in [0.5, 1): s - 1/2 = (m - 2^52) 2^-53
-            *base = -hfl;
-            *t = __ull2float_rn(m - (1ULL << 52)) * pow2f(-53);
-        } else {                                               // s in [0, 0.5)
-            *base = -hfl - 1;
-            *t = sf + 0.5f;
-        }
-        return true;
-    }
-    const int sa = 52 - e;                                     // fraction bits, 1..52
-    const long long fl = (long long)(m >> sa);
-    const unsigned long long fr = m & ((1ULL << sa) - 1);
-    if (!(n & 1)) {
-        *base = fl - hfl;
-        *t = __ull2float_rn(fr) * pow2f(-sa);
-    } else {
-        const unsigned long long hb = 1ULL << (sa - 1);        // one half in the fraction's units
-        if (fr >= hb) {
-            *base = fl - hfl;
-            *t = __ull2float_rn(fr - hb) * pow2f(-sa);
-        } else {
-            *base = fl - hfl - 1;
-            *t = __ull2float_rn(fr + hb) * pow2f(-sa);
-        }
-    }
-    return true;
-}
-
-// First stencil node modulo N (N a power of two, or 3 times one).
-__device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
-    if ((N & (N - 1)) == 0) return (unsigned)(a & (long long)(N - 1));
-    long long r = a % N;
-    return (unsigned)(r < 0 ? r + N : r);
-}
-
-// Locate one particle (Eq. alg-int-6): its brick key and record; the key is NB
-// for a non-finite position or one with no fractional bits left.
-template <typename TR>
-__device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
-                                                    int order, const BrickGrid& g, Rec<TR>* r) {
-    const unsigned NB = g.NB;
-    unsigned anc[3];
-    TR tt[3];
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double s = x[3 * p + a] * scale;
-        if constexpr (sizeof(TR) == 4) {
-            long long base;
-            float tf;
-            if (locate_nonneg(s, order, &base, &tf)) {
-                tt[a] = tf;
-                anc[a] = wrap_anchor(base + 1, N);
-                continue;
-            }
-        }
-        const double sh = s - 0.5 * order;
-        if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
-            ok = false;
-            anc[a] = 0;
-            tt[a] = 0;
-            continue;
-        }
-        const double f = floor(sh);
-        tt[a] = (TR)(sh - f);
-        anc[a] = wrap_anchor((long long)f + 1, N);
-    }
-    if (!ok) return NB;
-    r->cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
-    r->t[0] = tt[0];
-    r->t[1] = tt[1];
-    r->t[2] = tt[2];
-    return ((anc[0] >> g.bshift) * (unsigned)g.nby + anc[1] / (unsigned)g.by) * (unsigned)g.nbz + (anc[2] >> g.bshift);
-}
-
 // Below this many bricks, particles of one warp often share a brick: aggregate their counter updates.
 constexpr unsigned kAggregateBricks = 4096;
 

@@ -57,7 +57,7 @@ template <typename TR> struct Ws {
 
 inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t P) {
+template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t P, unsigned chunk_len = kChunk) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         void* ptr = base ? (void*)((char*)base + off) : nullptr;
@@ -70,13 +70,109 @@ template <typename TR> size_t carve(Ws<TR>* w, void* base, unsigned NB, int64_t 
     w->offset = (unsigned*)take(sizeof(unsigned) * (NB + 3));
     w->cursor = (unsigned*)take(sizeof(unsigned) * (NB + 1));
     w->chunk = (unsigned*)take(sizeof(unsigned) * (NB + 1));
-    w->item = (unsigned*)take(sizeof(unsigned) * (NB + (P + kChunk - 1) / kChunk));
+    w->item = (unsigned*)take(sizeof(unsigned) * (NB + (P + chunk_len - 1) / chunk_len));
     w->s_rec = (Rec<TR>*)take(sizeof(Rec<TR>) * P);
     return off;
 }
 
 // Periodic grid index of i >= 0 (a single subtraction in the common case i < 2N).
 __device__ __forceinline__ int wrap_index(int i, int N) { return i < N ? i : (i < 2 * N ? i - N : i % N); }
+
+// ------------------------------------------------------------------ locate
+// For 0 <= s < 2^52: base = floor(s - n/2) and t = (s - n/2) - base rounded to
+// float, computed exactly from the bits of s with integer operations (GB300's
+// FP64 pipe is narrow: only s = x N / L stays in FP64).  s = fl + fr 2^-sa
+// with integer fl and an sa-bit fraction fr; for odd n the half is folded
+// into the fraction.  Returns false outside that range.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // -126 <= k <= 127
+
+__device__ __forceinline__ bool locate_nonneg(double s, int n, long long* base, float* t) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    if (b >> 63) return false;                                 // negative
+    const int e = (int)(b >> 52) - 1023;                       // unbiased exponent
+    if (e >= 52) return false;                                 // >= 2^52, Inf or NaN
+    const unsigned long long m = (b & ((1ULL << 52) - 1)) | (1ULL << 52);
+    const long long hfl = n >> 1;                              // floor(n / 2)
+    if (e < 0) {                                               // s in [0, 1)
+        // below 2^-60 (or subnormal) s is 0 to the FP32 accuracy of the weights
+        const float sf = (e < -60) ? 0.f : __ull2float_rn(m) * pow2f(e - 52);
+        if (!(n & 1)) {
+            *base = -hfl;
+            *t = sf;
+        } else if (e == -1) {                                  // s in [0.5, 1): s - 1/2 = (m - 2^52) 2^-53
+            *base = -hfl;
+            *t = __ull2float_rn(m - (1ULL << 52)) * pow2f(-53);
+        } else {                                               // s in [0, 0.5)
+            *base = -hfl - 1;
+            *t = sf + 0.5f;
+        }
+        return true;
+    }
+    const int sa = 52 - e;                                     // fraction bits, 1..52
+    const long long fl = (long long)(m >> sa);
+    const unsigned long long fr = m & ((1ULL << sa) - 1);
+    if (!(n & 1)) {
+        *base = fl - hfl;
+        *t = __ull2float_rn(fr) * pow2f(-sa);
+    } else {
+        const unsigned long long hb = 1ULL << (sa - 1);        // one half in the fraction's units
+        if (fr >= hb) {
+            *base = fl - hfl;
+            *t = __ull2float_rn(fr - hb) * pow2f(-sa);
+        } else {
+            *base = fl - hfl - 1;
+            *t = __ull2float_rn(fr + hb) * pow2f(-sa);
+        }
+    }
+    return true;
+}
+
+// First stencil node modulo N (N a power of two, or 3 times one).
+__device__ __forceinline__ unsigned wrap_anchor(long long a, int N) {
+    if ((N & (N - 1)) == 0) return (unsigned)(a & (long long)(N - 1));
+    long long r = a % N;
+    return (unsigned)(r < 0 ? r + N : r);
+}
+
+// Locate one particle (Eq. alg-int-6): its brick key and record; the key is NB
+// for a non-finite position or one with no fractional bits left.
+template <typename TR>
+__device__ __forceinline__ unsigned locate_particle(const double* __restrict__ x, long long p, int N, double scale,
+                                                    int order, const BrickGrid& g, Rec<TR>* r) {
+    const unsigned NB = g.NB;
+    unsigned anc[3];
+    TR tt[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double s = x[3 * p + a] * scale;
+        if constexpr (sizeof(TR) == 4) {
+            long long base;
+            float tf;
+            if (locate_nonneg(s, order, &base, &tf)) {
+                tt[a] = tf;
+                anc[a] = wrap_anchor(base + 1, N);
+                continue;
+            }
+        }
+        const double sh = s - 0.5 * order;
+        if (!(fabs(sh) < 4.0e15)) {      // NaN, Inf, or no fractional bits left
+            ok = false;
+            anc[a] = 0;
+            tt[a] = 0;
+            continue;
+        }
+        const double f = floor(sh);
+        tt[a] = (TR)(sh - f);
+        anc[a] = wrap_anchor((long long)f + 1, N);
+    }
+    if (!ok) return NB;
+    r->cell = (anc[0] << (2 * kAnchorBits)) | (anc[1] << kAnchorBits) | anc[2];
+    r->t[0] = tt[0];
+    r->t[1] = tt[1];
+    r->t[2] = tt[2];
+    return ((anc[0] >> g.bshift) * (unsigned)g.nby + anc[1] / (unsigned)g.by) * (unsigned)g.nbz + (anc[2] >> g.bshift);
+}
 
 // ------------------------------------------------------------------ weights
 // v[m] = M_k(t + m), m = 0..k-1, for the cardinal B-spline of order k.
@@ -122,10 +218,11 @@ template <> struct TileT<double> { using T = double; };
 template <typename CT> __device__ __forceinline__ typename TileT<CT>::T widen(CT v) { return v; }
 template <> __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename CT, int ORD> struct Shape {
+// BYO: brick y extent other than the plan's default (batches tune it; 0 = brick_y).
+template <typename CT, int ORD, int BYO = 0> struct Shape {
     static constexpr bool F64 = sizeof(CT) == 8;
     static constexpr int BX = brick_x(F64 ? BSPLINE_F64 : BSPLINE_F32);
-    static constexpr int BY = brick_y(F64 ? BSPLINE_F64 : BSPLINE_F32, ORD);
+    static constexpr int BY = BYO ? BYO : brick_y(F64 ? BSPLINE_F64 : BSPLINE_F32, ORD);
     static constexpr int BZ = BX;
     static constexpr int EX = BX + ORD - 1, EY = BY + ORD - 1, EZ = BZ + ORD - 1;
     static constexpr int PZ = F64 ? EZ : ((EZ + 3) & ~3);
@@ -133,9 +230,9 @@ template <typename CT, int ORD> struct Shape {
     static constexpr int SY = PZ, SX = EY * PZ, TS = F64 ? EX * SX : ((EX * SX + 31) & ~31);
 };
 
-template <int ORD, typename CT>
+template <int ORD, typename CT, int BYO = 0>
 constexpr size_t tile_bytes() {
-    return sizeof(typename TileT<CT>::T) * 3 * (size_t)Shape<CT, ORD>::TS;
+    return sizeof(typename TileT<CT>::T) * 3 * (size_t)Shape<CT, ORD, BYO>::TS;
 }
 
 // Brick index -> first cell of the brick.
@@ -209,11 +306,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 // wrap periodically.  Same-type coefficients go through cp.async (no register
 // round trip); BF16 is widened to FP32 through registers.  The caller
 // synchronises the CTA after cp_async_wait_all.
-template <int ORD, typename CT>
+template <int ORD, typename CT, int BYO = 0>
 __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                            int y0, int z0) {
     using TT = typename TileT<CT>::T;
-    using S = Shape<CT, ORD>;
+    using S = Shape<CT, ORD, BYO>;
     static_assert(S::EZ <= 32, "one z-row per warp step");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane >= S::EZ) return;
@@ -250,10 +347,10 @@ __device__ __forceinline__ void stage_tile(typename TileT<CT>::T* tile, const CT
 // 4, so a chunk never straddles the periodic wrap).  Within a (c, ix) plane
 // the lane -> (row, chunk) assignment and its offsets are the same for every
 // plane, so they are computed once.
-template <int ORD>
+template <int ORD, int BYO = 0>
 __device__ __forceinline__ void stage_tile16(float* tile, const float* __restrict__ coef, int N, int x0, int y0,
                                              int z0) {
-    using S = Shape<float, ORD>;
+    using S = Shape<float, ORD, BYO>;
     constexpr int CH = S::PZ / 4;                     // chunks per row
     constexpr int PER = S::EY * CH;                   // chunks per plane
     constexpr int NI = (PER + 31) / 32;
@@ -281,10 +378,10 @@ __device__ __forceinline__ void stage_tile16(float* tile, const float* __restric
 // widened to FP32 in registers and stored as two 16-byte words.  All of a
 // lane's loads of a plane are issued together, and the next plane's before
 // this plane's stores (registers stand in for the asynchronous copy).
-template <int ORD>
+template <int ORD, int BYO = 0>
 __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16* __restrict__ coef, int N, int x0,
                                                 int y0, int z0) {
-    using S = Shape<__nv_bfloat16, ORD>;
+    using S = Shape<__nv_bfloat16, ORD, BYO>;
     constexpr int CH = (S::PZ + 7) / 8;               // chunks of 8 per row (the last may overhang the pitch)
     constexpr int PER = S::EY * CH;
     constexpr int NI = (PER + 31) / 32;
@@ -336,13 +433,13 @@ __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16
 // widened in place by expand_bf16_tile.  Needs z rows of a multiple of 8
 // elements (16-byte copies that never straddle the periodic wrap: z0 is a
 // multiple of 16 and N of 8).
-template <int ORD> constexpr bool bf16_async() {
-    return Shape<__nv_bfloat16, ORD>::PZ % 8 == 0 && (3 * Shape<__nv_bfloat16, ORD>::TS) % 8 == 0;
+template <int ORD, int BYO = 0> constexpr bool bf16_async() {
+    return Shape<__nv_bfloat16, ORD, BYO>::PZ % 8 == 0 && (3 * Shape<__nv_bfloat16, ORD, BYO>::TS) % 8 == 0;
 }
-template <int ORD>
+template <int ORD, int BYO = 0>
 __device__ __forceinline__ void stage_tile_bf16_async(float* tile, const __nv_bfloat16* __restrict__ coef, int N,
                                                       int x0, int y0, int z0) {
-    using S = Shape<__nv_bfloat16, ORD>;
+    using S = Shape<__nv_bfloat16, ORD, BYO>;
     static_assert(S::PZ % 8 == 0, "16-byte BF16 rows");
     constexpr int E = 3 * S::TS;                      // elements of the tile
     constexpr int CH = S::PZ / 8;                     // 16-byte chunks per row
@@ -373,9 +470,9 @@ __device__ __forceinline__ void stage_tile_bf16_async(float* tile, const __nv_bf
 // 2E + 2e + 2).  A chunk's reads all finish (barrier) before its writes, and
 // a write never reaches BF16 data of a later chunk (4 (k+1) C <= 2E + 2 (k+1) C
 // while (k + 1) C <= E).  Ends with a barrier.
-template <int ORD>
+template <int ORD, int BYO = 0>
 __device__ __forceinline__ void expand_bf16_tile(float* tile) {
-    using S = Shape<__nv_bfloat16, ORD>;
+    using S = Shape<__nv_bfloat16, ORD, BYO>;
     constexpr int E = 3 * S::TS;
     static_assert(E % 8 == 0, "whole 16-byte chunks");
     const uint4* raw = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(tile) + E);
@@ -408,10 +505,10 @@ __device__ __forceinline__ void expand_bf16_tile(float* tile) {
 // kTmaOn = interior bricks, kTmaArmOnly = arm the barrier for the tile's bytes
 // but issue no copy (test hook: the wait then runs out with nothing in flight).
 constexpr int kTmaOn = 1, kTmaArmOnly = 2;
-template <int ORD, typename CT>
+template <int ORD, typename CT, int BYO = 0>
 __device__ __forceinline__ bool stage_tile_tma(float* tile, const CUtensorMap* map, unsigned long long* bar, int N,
                                                int x0, int y0, int z0, int use_tma) {
-    using S = Shape<CT, ORD>;
+    using S = Shape<CT, ORD, BYO>;
     const bool tma = sizeof(CT) == 4 && use_tma && x0 + S::EX <= N && y0 + S::EY <= N && z0 + S::EZ <= N;
     if (tma && threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -457,21 +554,21 @@ __device__ __forceinline__ void fill_nan_item(const Ws<TR>& w, unsigned c0, unsi
     }
 }
 
-template <int ORD, typename CT>
+template <int ORD, typename CT, int BYO = 0>
 __device__ __forceinline__ void stage_brick(typename TileT<CT>::T* tile, const CT* __restrict__ coef, int N, int x0,
                                             int y0, int z0) {
     if constexpr (sizeof(CT) == 4) {
         if (N >= 16) {
-            stage_tile16<ORD>(tile, coef, N, x0, y0, z0);
+            stage_tile16<ORD, BYO>(tile, coef, N, x0, y0, z0);
             return;
         }
     } else if constexpr (sizeof(CT) == 2) {
         if (N >= 16) {
-            stage_tile_bf16<ORD>(tile, coef, N, x0, y0, z0);
+            stage_tile_bf16<ORD, BYO>(tile, coef, N, x0, y0, z0);
             return;
         }
     }
-    stage_tile<ORD, CT>(tile, coef, N, x0, y0, z0);
+    stage_tile<ORD, CT, BYO>(tile, coef, N, x0, y0, z0);
 }
 
 // u and grad u of one particle from the staged tile (Table 1 contraction,
@@ -727,13 +824,16 @@ __device__ __forceinline__ void store_g9(float* p, unsigned odd, const float (&g
 // upper bound on the number of items and surplus CTAs return at once.
 // Two CTAs per SM (80 registers): orders 7 and 8 would otherwise take 84 and
 // 102 registers and run one CTA per SM, 22 % and 16 % slower at 256^3.
-template <int ORD, typename CT, typename TR, bool GRAD>
-__global__ void __launch_bounds__(kGatherThreads, 2)
-gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __restrict__ out_u,
-           float* __restrict__ out_grad, float dscale, const __grid_constant__ CUtensorMap tmap, int use_tma,
-           unsigned long long* __restrict__ status) {
-    using S = Shape<CT, ORD>;
-    const unsigned NB = bg.NB;
+// gather_f32_item evaluates work item `item` (at most chunk_len <= kChunk
+// particles of one brick); the kernel gather_f32 runs one item per CTA, the
+// batch kernel many per CTA (BYO: its brick y extent).  The caller has
+// checked item < w.chunk[NB] and keeps every thread of the CTA here.
+template <int ORD, typename CT, typename TR, bool GRAD, int BYO = 0>
+__device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_len, const CT* __restrict__ coef, int N,
+                                                const BrickGrid& bg, const Ws<TR>& w, float* __restrict__ out_u,
+                                                float* __restrict__ out_grad, float dscale, const CUtensorMap* tmap,
+                                                int use_tma, unsigned long long* __restrict__ status) {
+    using S = Shape<CT, ORD, BYO>;
     constexpr int NW = kGatherThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
@@ -741,30 +841,29 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
     __shared__ unsigned s_bucket[32];
     __shared__ unsigned short s_order[kChunk];
     __shared__ __align__(8) unsigned long long s_mbar;
-    const unsigned item = blockIdx.x;
-    if (item >= w.chunk[NB]) return;
     const unsigned brick = w.item[item];
-    const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * kChunk;
+    const unsigned c0 = w.offset[brick] + (item - w.chunk[brick]) * chunk_len;
     const unsigned end = w.offset[brick] + w.count[brick];
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
     // BF16 tiles of orders 6-8 are copied raw and asynchronously (widened after the bucketing)
-    constexpr bool kRawBf16 = sizeof(CT) == 2 && bf16_async<ORD>();
+    constexpr bool kRawBf16 = sizeof(CT) == 2 && bf16_async<ORD, BYO>();
     const bool raw_bf16 = kRawBf16 && N >= 16;
     // FP32 bricks away from the periodic seams by TMA, the others with cp.async
-    const bool tma = stage_tile_tma<ORD, CT>(tile, &tmap, &s_mbar, N, x0, y0, z0, use_tma);
+    const bool tma = stage_tile_tma<ORD, CT, BYO>(tile, tmap, &s_mbar, N, x0, y0, z0, use_tma);
     if (tma) {
     } else if constexpr (kRawBf16) {
-        if (raw_bf16) stage_tile_bf16_async<ORD>(tile, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
-        else stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+        if (raw_bf16)
+            stage_tile_bf16_async<ORD, BYO>(tile, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
+        else stage_brick<ORD, CT, BYO>(tile, coef, N, x0, y0, z0);
     } else {
-        stage_brick<ORD, CT>(tile, coef, N, x0, y0, z0);
+        stage_brick<ORD, CT, BYO>(tile, coef, N, x0, y0, z0);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec_out = ((reinterpret_cast<uintptr_t>(out_u) | (GRAD ? reinterpret_cast<uintptr_t>(out_grad) : 0u)) &
                           7u) == 0u;
     {
-        const int n = (int)min(kChunk, end - c0);
+        const int n = (int)min(chunk_len, end - c0);
         if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
         __syncthreads();                                  // the tile copies stay in flight while bucketing
         // bucket (bank residue of the stencil origin) and rank within it, kept in registers
@@ -805,7 +904,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
         }
         __syncthreads();                                  // tile and order ready
         if constexpr (kRawBf16) {
-            if (raw_bf16) expand_bf16_tile<ORD>(tile);
+            if (raw_bf16) expand_bf16_tile<ORD, BYO>(tile);
         }
         // Warp jobs over that order.  Rank j holds #{banks with more than j
         // particles} particles, non-increasing in j.  While a rank holds at
@@ -903,6 +1002,16 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
             }
         }
     }
+}
+
+template <int ORD, typename CT, typename TR, bool GRAD>
+__global__ void __launch_bounds__(kGatherThreads, 2)
+gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __restrict__ out_u,
+           float* __restrict__ out_grad, float dscale, const __grid_constant__ CUtensorMap tmap, int use_tma,
+           unsigned long long* __restrict__ status) {
+    if (blockIdx.x >= w.chunk[bg.NB]) return;
+    gather_f32_item<ORD, CT, TR, GRAD>(blockIdx.x, kChunk, coef, N, bg, w, out_u, out_grad, dscale, &tmap, use_tma,
+                                       status);
 }
 
 // Direct gather for sparse bricks: the particles of bricks holding fewer

@@ -138,3 +138,120 @@ def test_batch_rejects_bad_arguments(B):
     with pytest.raises(B.BSplineError):
         batch.capture(uh, co_bad, xs, ou, og, streams=1)
     batch.close()
+
+
+def _single_field(plans, uh, xs, i):
+    c = plans[i].coeffs(uh[i])
+    u, g = plans[i].interp(c, xs[i])
+    torch.cuda.synchronize()
+    return c, u, g
+
+
+@pytest.mark.parametrize("by,item", [(12, 2048), (8, 512), (16, 1024)])
+def test_batch_queue_layouts_equal_single_field_calls(B, by, item):
+    """The persistent queue kernel (every field's count, scan, placement and gather tasks in one launch)
+    gives the single-field calls' bits at every brick y extent and item size."""
+    plans, uh, co, xs, ou, og, halves, xnp = _fields(B, SPEC)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=2)
+    batch.set_layout(queue=1, brick_y=by, item_particles=item)
+    cfg = batch.config()
+    assert cfg["queue"] == 1 and cfg["brick_y"] == by and cfg["item_particles"] == item
+    # two transform kernels per field and the one queue kernel
+    assert cfg["kernel_nodes"] == 2 * len(SPEC) + 1
+    batch.launch()
+    assert batch.status() == (B.OK, 0)
+    for i, f in enumerate(SPEC):
+        c, u, g = _single_field(plans, uh, xs, i)
+        assert torch.equal(c, co[i])
+        if f["P"]:
+            assert torch.equal(u, ou[i]) and torch.equal(g, og[i]), (i, by, item)
+    ru, rg = O.interpolate(halves[6].astype(np.complex64).astype(np.complex128), xnp[6], 4)
+    assert normwise(ou[6].cpu().numpy(), ru) < TOL32["u"] and normwise(og[6].cpu().numpy(), rg) < TOL32["grad"]
+    batch.close()
+
+
+def test_batch_queue_wait_timeout_and_next_launch(B):
+    """A queue entry left unpublished (the first count task of field 0 skips its signal): the scan of field
+    0 waits until its bounded wait runs out, the launch ends, bspline_batch_status reports TIMEOUT; the next
+    launch without the hook is correct and reports OK."""
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, SPEC)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=2)
+    batch.set_layout(queue=1)
+    batch.set_test_hooks(B.TEST_DROP_QUEUE_SIGNAL)
+    batch.launch()
+    rc, _ = batch.status()
+    assert rc == B.ERR_TIMEOUT
+    batch.set_test_hooks(0)
+    for t in ou + og:
+        t.fill_(float("nan"))
+    batch.launch()
+    assert batch.status() == (B.OK, 0)
+    for i, f in enumerate(SPEC):
+        if f["P"]:
+            _, u, g = _single_field(plans, uh, xs, i)
+            assert torch.equal(u, ou[i]) and torch.equal(g, og[i])
+    batch.close()
+
+
+def test_batch_queue_nonfinite_positions(B):
+    spec = [dict(N=32, field_seed=21, particle_seed=31, P=3000), dict(N=48, field_seed=22, particle_seed=32, P=900)]
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, spec)
+    xs[1][[5, 17]] = torch.tensor([[float("nan"), 0.0, 0.0], [1.0, float("inf"), 1.0]], dtype=torch.float64,
+                                  device="cuda")
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=1)
+    assert batch.config()["queue"] == 1
+    batch.launch()
+    assert batch.status() == (B.ERR_NONFINITE_INPUT, 2)
+    assert torch.isnan(ou[1][[5, 17]]).all() and torch.isnan(og[1][[5, 17]]).all()
+    _, u, g = _single_field(plans, uh, xs, 1)
+    assert torch.equal(torch.isnan(u), torch.isnan(ou[1]))
+    ok = ~torch.isnan(u[:, 0])
+    assert torch.equal(u[ok], ou[1][ok]) and torch.equal(g[ok], og[1][ok])
+    batch.close()
+
+
+def test_batch_queue_only_where_fields_allow(B):
+    """u only or FP64: the per-field graph; requiring the queue there is refused."""
+    spec = SPEC[:2]
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, spec, dtype="f64", order=4)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=1)
+    assert batch.config()["queue"] == 0
+    with pytest.raises(B.BSplineError) as exc:
+        batch.set_layout(queue=1)
+    assert exc.value.code == B.ERR_NOT_IMPLEMENTED
+    batch.close()
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, spec)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, None, streams=1)            # u only
+    assert batch.config()["queue"] == 0
+    batch.close()
+
+
+def test_batch_queue_autotune_and_its_cache(B, tmp_path, monkeypatch):
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("BSPLINE_AUTOTUNE_CACHE", str(cache))
+    plans, uh, co, xs, ou, og, _, _ = _fields(B, SPEC)
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=1)
+    k, ms = batch.autotune()
+    cfg = batch.config()
+    assert ms > 0 and cfg["queue"] == 1 and cfg["brick_y"] in (8, 12, 16) and cfg["item_particles"] in (512, 1024,
+                                                                                                          2048)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and '"brick_y"' in lines[0]
+    batch.launch()
+    assert batch.status() == (B.OK, 0)
+    ref = [t.clone() for t in ou]
+    batch.close()
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=1)
+    k2, ms2 = batch.autotune()                                # from the cache: no timing
+    assert ms2 == 0.0 and k2 == k and batch.config()["brick_y"] == cfg["brick_y"]
+    batch.launch()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(ref, ou))
+    batch.close()
