@@ -288,12 +288,13 @@ def run_ours(args):
     xs = synth.clustered_particles(P, seed=rank_particle_seed(wl, rank))
     x = torch.from_numpy(xs).to(device)
 
-    # ---- headline: FP32 coefficients, whole path, timed region of exactly K steps
-    plan = B.Plan(N, order, "f32")
+    # ---- headline: FP32 coefficients (--dtype: another form, for profiling captures), whole path, K steps
+    hd = args.dtype
+    plan = B.Plan(N, order, hd)
     uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
     coef = plan.empty_coeffs()
-    u = torch.empty((P, 3), dtype=torch.float32, device=device)
-    g = torch.empty((P, 3, 3), dtype=torch.float32, device=device)
+    u = torch.empty((P, 3), dtype=plan.out_dtype, device=device)
+    g = torch.empty((P, 3, 3), dtype=plan.out_dtype, device=device)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -339,9 +340,9 @@ def run_ours(args):
     pk = peaks()
     dom = max(STAGES, key=lambda s: stages[s][0])
     dom_ms = stages[dom][0] / max(stages[dom][1], 1)
-    abytes = algorithmic_bytes(dom, N, P, "f32", order)
+    abytes = algorithmic_bytes(dom, N, P, hd, order)
     achieved = abytes / (dom_ms / 1e3) / 1e9
-    traffic = measured_traffic(dom, "f32", N, order)
+    traffic = measured_traffic(dom, hd, N, order)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": traffic, "algorithmic_bytes": abytes, "avg_launch_ms": dom_ms}
@@ -351,7 +352,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     fma_peak = sms * 128 * pk["sm_max_mhz"] * 1e6
     fma_rate = P * from_table1 / (g_ms / 1e3)
-    g_bytes = algorithmic_bytes("gather", N, P, "f32", order)
+    g_bytes = algorithmic_bytes("gather", N, P, hd, order)
     gather = {"avg_launch_ms": g_ms, "achieved_gbs": g_bytes / (g_ms / 1e3) / 1e9,
               "hbm_frac": g_bytes / (g_ms / 1e3) / 1e9 / pk["hbm_gbs"],
               "fma_per_particle_table1": from_table1, "fma_rate_tfma": fma_rate / 1e12,
@@ -363,7 +364,7 @@ def run_ours(args):
               "smem_gbs": P * 3 * order ** 3 * 4 / (g_ms / 1e3) / 1e9,
               "smem_peak_gbs_at_max_clock": sms * 128 * pk["sm_max_mhz"] * 1e6 / 1e9,
               "smem_frac_at_max_clock": P * 3 * order ** 3 * 4 / (g_ms / 1e3) / (sms * 128 * pk["sm_max_mhz"] * 1e6),
-              "traffic": measured_traffic("gather", "f32", N, order)}
+              "traffic": measured_traffic("gather", hd, N, order)}
     stages_ms = {s: {"total_ms": stages[s][0], "launches": stages[s][1],
                      "share": stages[s][0] / max(sum(v[0] for v in stages.values()), 1e-30)} for s in STAGES}
     # outputs at a fixed sample of particles, for the error against the oracle (computed after the run)
@@ -376,14 +377,14 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "scaling": "weak", "vs_baseline": None, "dtype": hd,
            "data": f"synthetic: Kolmogorov-spectrum field (seed {wl['field_seed']}), clustered particles "
                    f"(seed {wl['particle_seed']} + rank); no dataset",
-           "config": config_block(wl, "f32", world), "roofline": roofline, "gather": gather,
+           "config": config_block(wl, hd, world), "roofline": roofline, "gather": gather,
            "stages_ms": stages_ms, "gpu_launches": launches, "clocks": clocks, "nonfinite_positions": nonfinite}
 
     # ---- other coefficient forms and the end-to-end number (rank 0 only at N = 1)
-    if world == 1 and not args.quick:
+    if world == 1 and not args.quick and hd == "f32":
         forms = {"f32": {"particles_per_s": value, "ms_per_step": ms_total / args.steps}}
         ks = max(3, min(args.steps, 20))
         ms_bf, st_bf, _, sampled["bf16"] = run_form(B, wl, F, x, "bf16", ks, 2, device, sample=sample_t)
@@ -471,6 +472,21 @@ def run_adjoint(B, device, steps=10, warmup=3):
     plan.set_timing(False)
     names = ["bin", "scan", "scatter", "spread", "grad_x", "adj_fft"]
     stages = {s: st[s][0] / max(st[s][1], 1) for s in names}
+    # the same steps with the deterministic (fixed-point) spread
+    plan.set_deterministic(True)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_det = e0.elapsed_time(e1) / steps
+    st_det = plan.stage_times()
+    plan.set_timing(False)
+    plan.set_deterministic(False)
     rec = 16
     coef_b, spec_b = 3 * N ** 3 * 4, 3 * N * N * (N // 2 + 1) * 8
     hp = ((N // 2 + 1) + 7) // 8 * 8
@@ -485,6 +501,9 @@ def run_adjoint(B, device, steps=10, warmup=3):
            "particles_per_s": P / (ms / 1e3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
            "step": "g_coeffs zeroed, bin+sort, spread onto coefficients, position gradients, transposed transform",
            "stages_ms": stages,
+           "deterministic": {"ms_per_step": ms_det, "particles_per_s": P / (ms_det / 1e3),
+                             "spread_ms": st_det["spread"][0] / max(st_det["spread"][1], 1),
+                             "how": "bspline_plan_set_deterministic: fixed-point sums, bit-identical per call"},
            "hbm_frac": {s: abytes[s] / (stages[s] / 1e3) / 1e9 / pk["hbm_gbs"] for s in abytes if stages[s] > 0}}
     del uh, coef, x, gu, gg, g_coef, g_uh, g_x
     plan.close()
@@ -1100,6 +1119,24 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_part(args) -> dict:
+    """One secondary block alone on cuda:0 (for ncu captures of its kernels)."""
+    import torch
+    from paper_1201_4060_gb300 import _build, synth
+    _build.build()
+    from paper_1201_4060_gb300 import bspline as B
+    device = torch.device("cuda", 0)
+    if args.part == "adjoint":
+        return run_adjoint(B, device, steps=args.steps, warmup=args.warmup)
+    if args.part == "batch":
+        return run_batch(B, device, steps=args.steps, warmup=args.warmup)
+    if args.part == "orders":
+        return run_orders(B, device)[0]
+    wl = workload()
+    F = synth.kolmogorov_field(wl["N"], seed=wl["field_seed"])
+    return run_transform(B, wl, F, device)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1107,6 +1144,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no other forms, no e2e)")
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f64"], default="f32",
+                    help="coefficient type of the timed step (f32 is the benchmark; others for profiling captures)")
+    ap.add_argument("--part", choices=["adjoint", "batch", "orders", "transform"], default=None,
+                    help="run one secondary block alone and print it (profiling captures; not a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--samples", type=int, default=4096, help=argparse.SUPPRESS)
@@ -1132,6 +1173,9 @@ def main():
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.part:
+        print(json.dumps(run_part(args)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -209,12 +209,29 @@ int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const dou
  * x is required when P > 0 and g_coeffs or g_x is given.  Non-finite positions
  * contribute nothing to g_coeffs and are counted in the status word.
  * FP32 plans accumulate g_coeffs with atomics: the summation order, and so
- * the last bits, vary between calls.  Uses the plan's particle and transform
+ * the last bits, vary between calls, unless bspline_plan_set_deterministic
+ * turned on exact fixed-point sums.  Uses the plan's particle and transform
  * workspaces.  BSPLINE_ERR_INVALID_ARG for a missing required pointer, a bad
  * alignment or P outside [0, 2^31). */
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
                            const void* g_u, const void* g_grad, void* g_coeffs, void* g_u_hat,
                            double* g_x);
+
+/* Deterministic adjoint (FP32 and BF16 plans; FP64 plans: NOT_IMPLEMENTED).
+ * By default bspline_spread_adjoint adds the particles' contributions to
+ * g_coeffs with floating-point atomics, so the order of the additions, and
+ * the last bits of g_coeffs and g_u_hat, vary between calls.  With
+ * enable = 1 each contribution is computed in FP32 as before, rounded once to
+ * a 64-bit fixed-point integer at the scale 2^e, e = 61 - ceil(log2(G (1 +
+ * 3 N/L) P)) with G the largest |g_u| or |g_grad| over the particles (no
+ * node's sum can then leave the integer range), summed exactly with integer
+ * atomics and converted back once per node: the result is bit-identical from
+ * call to call, and each contribution carries an absolute rounding of at
+ * most 2^-(e+1) instead of an FP32 rounding per addition.  Costs a
+ * [3][N][N][N] int64 accumulator in the plan (allocated on first use) and a
+ * slower spread.  Cotangents must be finite in this mode.  Position gradients
+ * and the transform are deterministic in both modes. */
+int bspline_plan_set_deterministic(bspline_plan_t plan, int enable);
 
 /* Device workspace bspline_interp needs for P positions. */
 int bspline_workspace_bytes(bspline_plan_t plan, int64_t P, size_t* bytes);

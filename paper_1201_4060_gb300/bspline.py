@@ -49,7 +49,8 @@ def _load() -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    # BSPLINE_LIBRARY selects another build of the same ABI (the BSPLINE_CHECKS=1 variant)
+    path = os.environ.get("BSPLINE_LIBRARY") or _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with paper_1201_4060_gb300._build.build()")
     lib = ctypes.CDLL(path)
@@ -78,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "bspline_plan_set_timing": (i32, [vp, i32]),
         "bspline_plan_set_test_hooks": (i32, [vp, i32]),
         "bspline_plan_set_gather_split": (i32, [vp, ctypes.c_uint]),
+        "bspline_plan_set_deterministic": (i32, [vp, i32]),
         "bspline_plan_autotune": (i32, [vp, vp, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_uint),
                                         ctypes.POINTER(ctypes.c_double)]),
         "bspline_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]),
@@ -427,6 +429,12 @@ class Plan:
         if rc not in (OK, ERR_NONFINITE_INPUT):
             raise BSplineError(rc, "bspline_status")
         return n
+
+    def set_deterministic(self, enable: bool) -> None:
+        """Exact fixed-point sums in the adjoint spread: bit-identical results call to call
+        (bspline_plan_set_deterministic)."""
+        _check(_load().bspline_plan_set_deterministic(self.handle, 1 if enable else 0),
+               "bspline_plan_set_deterministic")
 
     def set_gather_split(self, direct_below: int) -> None:
         """Bricks with fewer particles than this use the direct gather (bspline_plan_set_gather_split)."""

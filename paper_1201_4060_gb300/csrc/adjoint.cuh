@@ -82,6 +82,48 @@ __device__ __forceinline__ bool item_range(const Ws<TR>& w, unsigned NB, unsigne
     return *beg < *end;
 }
 
+// The n particles of an item [beg, beg + n) ordered rank-major, bank-minor by
+// the bank (element index mod 32) of their stencil origin in a tile of row
+// stride EZ and plane stride EY * EZ, into s_order (as in the gather): a warp
+// taking 32 consecutive particles of that order touches each bank at most
+// once per rank it spans.  Ends with a barrier.
+template <int EY, int EZ, int NT, typename TR>
+__device__ __forceinline__ void bank_order(const Ws<TR>& w, unsigned beg, unsigned n, int x0, int y0, int z0,
+                                           unsigned* s_bucket, unsigned short* s_order) {
+    constexpr int KT = (kChunk + NT - 1) / NT;
+    unsigned packed[KT];
+    if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const unsigned i = threadIdx.x + k * NT;
+        if (i < n) {
+            const unsigned cp = w.s_rec[beg + i].cell;
+            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
+            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
+            const int oz = (int)(cp & 1023u) - z0;
+            const unsigned r = (unsigned)((ox * EY + oy) * EZ + oz) & 31u;
+            packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const unsigned i = threadIdx.x + k * NT;
+        if (i < n) {
+            const unsigned r = packed[k] & 31u, rk = packed[k] >> 5;
+            unsigned pos = 0;
+#pragma unroll 8
+            for (unsigned q = 0; q < 32; ++q) {
+                const unsigned bq = s_bucket[q];
+                pos += min(bq, rk) + ((q < r && bq > rk) ? 1u : 0u);
+            }
+            s_order[pos] = (unsigned short)i;
+        }
+    }
+    __syncthreads();
+}
+
 // Accumulation tile of the spread: the brick plus halo, [c][x][y][z], unpadded.
 template <int ORD, typename A> constexpr size_t acc_bytes() {
     using S = Shape<A, ORD>;
@@ -93,7 +135,7 @@ template <int ORD, typename A> constexpr size_t acc_bytes() {
 template <int ORD, typename TR, typename A, bool GRAD>
 __global__ void __launch_bounds__(kAdjThreads)
 spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A* __restrict__ g_grad,
-              A* __restrict__ g_coef, A dscale) {
+              A* __restrict__ g_coef, A dscale, unsigned long long* __restrict__ status) {
     using S = Shape<A, ORD>;
     constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ, BZ = S::BZ;
     constexpr int E3 = EX * EY * EZ;                    // one component
@@ -152,6 +194,10 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
         const size_t idx = rc.idx;
+        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
+                             (long long)idx < w.P,
+                         status + kStatusBounds))
+            continue;
         A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
         bspline_weights<ORD, A>((A)rc.t[0], wx, dwx);
         bspline_weights<ORD, A>((A)rc.t[1], wy, dwy);
@@ -225,6 +271,139 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
             }
         }
     }
+}
+
+// ---- Deterministic spread (plan option, FP32 accumulation types): every
+// node's sum is formed in 64-bit fixed point, which integer atomics add
+// exactly, so the order in which particles and work items arrive no longer
+// changes a bit.  Each contribution is computed in FP32 as in spread_kernel
+// and rounded once to an integer at the scale 2^e; e is chosen from a bound
+// on all contributions so that no node's sum can leave 2^61:
+//   |contribution| <= G (1 + 3 N/L),  G = max |g_u|, |g_grad| over particles
+// (|w| <= 1 and |w'| <= 1 for a cardinal B-spline), at most P per node, so
+// e = 61 - ceil(log2(G (1 + 3 N/L) P)).  The sums then go through one FP64
+// multiply by 2^-e and one FP32 add into g_coef.
+
+// G: atomic maximum over the cotangents' magnitudes (non-negative floats order as their bits).
+template <bool GRAD>
+__global__ void cotangent_bound_kernel(const float* __restrict__ g_u, const float* __restrict__ g_grad,
+                                       long long P, unsigned* __restrict__ bound) {
+    float m = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        if (g_u) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) m = fmaxf(m, fabsf(g_u[3 * i + c]));
+        }
+        if (GRAD) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) m = fmaxf(m, fabsf(g_grad[9 * i + k]));
+        }
+    }
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(bound, __float_as_uint(m));
+}
+
+// The scale exponent e of the fixed point (the same in every thread: it depends on G, N/L and P only).
+__device__ __forceinline__ int det_exponent(const unsigned* bound, float dscale, long long P) {
+    const float T = __uint_as_float(*bound) * (1.f + 3.f * dscale) * (float)P;
+    int ex = 0;
+    if (T > 0.f) frexpf(T, &ex);                        // T < 2^ex
+    return min(100, 61 - ex);
+}
+
+__device__ __forceinline__ void red_shared_s64(long long* p, long long v) {
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v) : "memory");
+}
+
+// As spread_kernel (FP32), the tile in fixed point and the tile added to acc_g with 64-bit integer atomics.
+template <int ORD, typename TR, bool GRAD>
+__global__ void __launch_bounds__(kAdjThreads)
+spread_det_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, const float* __restrict__ g_grad,
+                  long long* __restrict__ acc_g, float dscale, const unsigned* __restrict__ bound,
+                  unsigned long long* __restrict__ status) {
+    using S = Shape<float, ORD>;
+    constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ;
+    constexpr int E3 = EX * EY * EZ;
+    const unsigned NB = bg.NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    long long* acc = reinterpret_cast<long long*>(smem_raw);
+    unsigned brick, beg, end;
+    if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
+    int x0, y0, z0;
+    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
+    const float sc = ldexpf(1.f, det_exponent(bound, dscale, w.P));
+    const unsigned n = end - beg;
+    __shared__ unsigned s_bucket[32];
+    __shared__ unsigned short s_order[kChunk];
+    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) acc[e] = 0;
+    bank_order<EY, EZ, kAdjThreads>(w, beg, n, x0, y0, z0, s_bucket, s_order);   // ends with a barrier
+    for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
+        const Rec<TR> rc = w.s_rec[beg + s_order[q]];
+        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+        const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+        const int oz = (int)(rc.cell & 1023u) - z0;
+        const size_t idx = rc.idx;
+        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
+                             (long long)idx < w.P,
+                         status + kStatusBounds))
+            continue;
+        float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+        bspline_weights<ORD, float>(rc.t[0], wx, dwx);
+        bspline_weights<ORD, float>(rc.t[1], wy, dwy);
+        bspline_weights<ORD, float>(rc.t[2], wz, dwz);
+        long long* base = acc + (ox * EY + oy) * EZ + oz;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            const float gu = g_u ? g_u[3 * idx + c] : 0.f;
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+            if (GRAD) {
+                g0 = g_grad[9 * idx + 3 * c + 0] * dscale;
+                g1 = g_grad[9 * idx + 3 * c + 1] * dscale;
+                g2 = g_grad[9 * idx + 3 * c + 2] * dscale;
+            }
+            long long* tc = base + c * E3;
+#pragma unroll
+            for (int jx = 0; jx < ORD; ++jx) {
+                const float q0 = GRAD ? fmaf(g0, dwx[jx], gu * wx[jx]) : gu * wx[jx];
+                const float q1 = g1 * wx[jx], q2 = g2 * wx[jx];
+#pragma unroll
+                for (int jy = 0; jy < ORD; ++jy) {
+                    const float p0 = GRAD ? fmaf(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
+                    const float p1 = q2 * wy[jy];
+                    long long* line = tc + (jx * EY + jy) * EZ;
+#pragma unroll
+                    for (int jz = 0; jz < ORD; ++jz) {
+                        const float v = GRAD ? fmaf(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz];
+                        red_shared_s64(line + jz, __float2ll_rn(v * sc));
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) {
+        const long long v = acc[e];
+        if (v != 0) {
+            const int c = e / E3, r = e - c * E3;
+            const int ix = r / (EY * EZ), iy = (r / EZ) % EY, iz = r % EZ;
+            atomicAdd(reinterpret_cast<unsigned long long*>(
+                          &acc_g[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N +
+                                 wrap_index(z0 + iz, N)]),
+                      (unsigned long long)v);
+        }
+    }
+}
+
+// g_coef += acc_g 2^-e, one thread per node (the one rounding of each node's exact sum).
+static __global__ void det_finish_kernel(const long long* __restrict__ acc_g, float* __restrict__ g_coef, long long n,
+                                  float dscale, long long P, const unsigned* __restrict__ bound) {
+    const double inv = ldexp(1.0, -det_exponent(bound, dscale, P));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g_coef[i] += (float)((double)acc_g[i] * inv);
 }
 
 // Position gradient: one thread per particle of the work item, coefficients
@@ -302,6 +481,10 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
         const size_t idx = rc.idx;
+        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
+                             (long long)idx < w.P,
+                         status + kStatusBounds))
+            continue;
         A wx[ORD], dwx[ORD], d2wx[ORD], wy[ORD], dwy[ORD], d2wy[ORD], wz[ORD], dwz[ORD], d2wz[ORD];
         bspline_weights2<ORD, A>((A)rc.t[0], wx, dwx, d2wx);
         bspline_weights2<ORD, A>((A)rc.t[1], wy, dwy, d2wy);
@@ -375,12 +558,38 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
     using A = typename TileT<CT>::T;
     const A dscale = (A)((double)p->N / p->L);
     int rc;
+    if constexpr (sizeof(A) == 4) {
+        if (g_coef && p->deterministic) {
+            // fixed-point accumulator [3][N][N][N] int64, then the bound word
+            const long long nodes = 3LL * p->N * p->N * p->N;
+            long long* acc_g = reinterpret_cast<long long*>(p->det.ptr);
+            unsigned* bound = reinterpret_cast<unsigned*>(acc_g + nodes);
+            cudaError_t e = cudaMemsetAsync(acc_g, 0, sizeof(long long) * nodes + 16, p->stream);
+            if (e != cudaSuccess) return set_cuda_error(e);
+            const long long want = (w.P + 255) / 256;
+            const unsigned blocks = (unsigned)std::max(1LL, std::min(want, 8LL * p->sms));
+            if (g_grad)
+                cotangent_bound_kernel<true><<<blocks, 256, 0, p->stream>>>((const float*)g_u, (const float*)g_grad,
+                                                                            w.P, bound);
+            else
+                cotangent_bound_kernel<false><<<blocks, 256, 0, p->stream>>>((const float*)g_u, nullptr, w.P, bound);
+            const size_t sm = sizeof(long long) * 3 * (size_t)Shape<float, ORD>::EX * Shape<float, ORD>::EY *
+                              Shape<float, ORD>::EZ;
+            auto k = g_grad ? spread_det_kernel<ORD, TR, true> : spread_det_kernel<ORD, TR, false>;
+            if ((rc = set_smem(k, sm))) return rc;
+            k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, g, w, (const float*)g_u, (const float*)g_grad,
+                                                                acc_g, (float)dscale, bound, p->d_status);
+            const unsigned fb = (unsigned)std::max(1LL, std::min((nodes + 255) / 256, 16LL * p->sms));
+            det_finish_kernel<<<fb, 256, 0, p->stream>>>(acc_g, (float*)g_coef, nodes, (float)dscale, w.P, bound);
+            g_coef = nullptr;                               // done
+        }
+    }
     if (g_coef) {
         const size_t sm = acc_bytes<ORD, A>();
         auto k = g_grad ? spread_kernel<ORD, TR, A, true> : spread_kernel<ORD, TR, A, false>;
         if ((rc = set_smem(k, sm))) return rc;
         k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, g, w, (const A*)g_u, (const A*)g_grad,
-                                                            (A*)g_coef, dscale);
+                                                            (A*)g_coef, dscale, p->d_status);
     }
     if (g_x) {
         const size_t sm = tile_bytes<ORD, CT>() + 128;   // room to align the tile to 128 bytes

@@ -229,6 +229,7 @@ void free_plan(bspline_plan_s* p) {
     if (p->d_status) cudaFree(p->d_status);
     p->work.release();
     p->pws.release();
+    p->det.release();
     if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
@@ -463,6 +464,13 @@ int bspline_status(bspline_plan_t plan, int64_t* nonfinite) {
     if (h[kStatusParticleTimeout] || h[kStatusTransformTimeout]) return BSPLINE_ERR_TIMEOUT;
     if (h[kStatusBounds]) return BSPLINE_ERR_BOUNDS;
     return h[kStatusNonfinite] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
+}
+
+int bspline_plan_set_deterministic(bspline_plan_t plan, int enable) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (enable && plan->dtype == BSPLINE_F64) return BSPLINE_ERR_NOT_IMPLEMENTED;
+    plan->deterministic = enable ? 1 : 0;
+    return BSPLINE_OK;
 }
 
 int bspline_plan_set_gather_split(bspline_plan_t plan, unsigned direct_below) {

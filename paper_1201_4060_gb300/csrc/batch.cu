@@ -124,8 +124,8 @@ int build_queue(bspline_batch_s* b, int by, unsigned chunk_len) {
         item_pre[i + 1] = item_pre[i] + (P > 0 ? grids[i].NB + (unsigned)((P + chunk_len - 1) / chunk_len) : 0u);
         counts += grids[i].NB + 2;
     }
-    const size_t off_status = 0;
-    const size_t off_ctr = 16;
+    const size_t off_status = 0;                        // the status words of a plan, kStatusWords of them
+    const size_t off_ctr = sizeof(unsigned long long) * kStatusWords;
     const size_t off_counts = off_ctr + sizeof(unsigned) * (2 + 3 * (size_t)F);
     const size_t zero = off_counts + sizeof(unsigned) * counts;
     const size_t off_desc = align256(zero);
@@ -532,13 +532,14 @@ int bspline_batch_status(bspline_batch_t b, int64_t* nonfinite) {
     if (!b->queue_used) return BSPLINE_OK;
     Guard g(b->device);
     if (!g.ok) return BSPLINE_ERR_CUDA;
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[kStatusWords] = {};
     cudaError_t e = cudaStreamSynchronize(b->last_stream);
     if (e == cudaSuccess) e = cudaMemcpy(h, b->q.status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(e);
-    if (nonfinite) *nonfinite = (int64_t)h[0];
-    if (h[1]) return BSPLINE_ERR_TIMEOUT;
-    return h[0] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
+    if (nonfinite) *nonfinite = (int64_t)h[kStatusNonfinite];
+    if (h[kStatusParticleTimeout]) return BSPLINE_ERR_TIMEOUT;
+    if (h[kStatusBounds]) return BSPLINE_ERR_BOUNDS;
+    return h[kStatusNonfinite] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
 }
 
 int bspline_batch_destroy(bspline_batch_t b) {

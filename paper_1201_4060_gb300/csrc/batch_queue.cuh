@@ -42,7 +42,8 @@ struct FieldDesc {
 // Queue of one launch.  ctr (zeroed before every launch): [0] ticket counter,
 // [1] time-out word, then per field the finished count tasks, the finished
 // scan, and the finished placement tasks.  status (zeroed before every
-// launch): [0] non-finite positions of all fields, [1] a wait ran out.
+// launch; laid out as a plan's status words): [0] non-finite positions of all
+// fields, [1] a wait ran out, [2] index checks that failed (checks builds).
 struct Queue {
     const FieldDesc* fields;
     const unsigned* task_pre;    // [F + 1] prefix over fields of the count (= placement) tasks
@@ -75,7 +76,7 @@ __device__ __forceinline__ bool q_wait(const unsigned* flag, unsigned target, un
         if (q_ld_acquire(err) != 0u) return false;
         if (++it > kQueueWaitLimit) {
             atomicExch(err, 1u);
-            atomicOr(&status[1], 1ULL);
+            atomicOr(&status[kStatusParticleTimeout], 1ULL);
             return false;
         }
         __nanosleep(200);
@@ -116,7 +117,7 @@ __device__ __forceinline__ void q_count(const FieldDesc& f, long long p0, long l
         if (valid) {
             Rec<float> r;
             k = gather_impl::locate_particle<float>(f.x, p, f.N, f.scale, ORD, f.bg, &r);
-            if (k == NB) atomicAdd(&status[0], 1ULL);
+            if (k == NB) atomicAdd(&status[kStatusNonfinite], 1ULL);
         }
         const unsigned active = __ballot_sync(0xffffffffu, valid);
         if (valid) {
@@ -130,7 +131,8 @@ __device__ __forceinline__ void q_count(const FieldDesc& f, long long p0, long l
 // Placement task: locate again and write each record to its brick's next slot; NaN outputs for
 // non-finite positions.
 template <int ORD, bool GRAD>
-__device__ __forceinline__ void q_place(const FieldDesc& f, long long p0, long long p1) {
+__device__ __forceinline__ void q_place(const FieldDesc& f, long long p0, long long p1,
+                                        unsigned long long* status) {
     const unsigned NB = f.bg.NB;
     const int lane = threadIdx.x & 31;
     for (long long pw = p0 + (threadIdx.x & ~31u); pw < p1; pw += blockDim.x) {
@@ -157,7 +159,7 @@ __device__ __forceinline__ void q_place(const FieldDesc& f, long long p0, long l
             const unsigned d = base + (unsigned)__popc(peers & ((1u << lane) - 1u));
             r.idx = (unsigned)p;
             r.pad[0] = r.pad[1] = r.pad[2] = 0u;
-            f.w.s_rec[d] = r;
+            if (BS_CHECK_OK(d < f.w.offset[k] + f.w.count[k], status + kStatusBounds)) f.w.s_rec[d] = r;
         }
     }
 }
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(gather_impl::kGatherThreads, 2) batch_queue_ke
             const long long p0 = (long long)j * q.part_per_task;
             const long long p1 = min(f.P, p0 + (long long)q.part_per_task);
             if (phase == 0) q_count<ORD>(f, p0, p1, q.status);
-            else q_place<ORD, GRAD>(f, p0, p1);
+            else q_place<ORD, GRAD>(f, p0, p1, q.status);
             __syncthreads();
             if (threadIdx.x == 0 && !(phase == 0 && q.drop_first_signal && fi == 0 && j == 0))
                 q_signal(phase == 0 ? &done_count[fi] : &done_place[fi]);

@@ -51,13 +51,30 @@ inline bool supported_grid(int N) {
 }
 
 // Device status words of a plan, read by bspline_status.  Particle calls
-// (interp, eval, the adjoint's particle side) clear words 0-1 when they start,
-// the transform clears word 2.
+// (interp, eval, the adjoint's particle side) clear words 0-2 when they start,
+// the transform clears word 3.
 constexpr int kStatusNonfinite = 0;          // non-finite positions of the last particle call
 constexpr int kStatusParticleTimeout = 1;    // a tile wait of the last particle call ran out
-constexpr int kStatusTransformTimeout = 2;   // a wait of the last transform ran out
-constexpr int kStatusBounds = 3;             // index checks that failed (BSPLINE_CHECKS builds)
+constexpr int kStatusBounds = 2;             // index checks that failed (BSPLINE_CHECKS builds)
+constexpr int kStatusTransformTimeout = 3;   // a wait of the last transform ran out
 constexpr int kStatusWords = 4;
+constexpr int kStatusParticleWords = 3;      // the words a particle call clears
+
+// Index checks of a BSPLINE_CHECKS=1 build (compiled with -DBSPLINE_CHECKS=1):
+// BS_CHECK_OK(cond, word) is true when cond holds; when it does not, the
+// failure is counted in *word (a device status word) and the caller skips the
+// access the condition guards.  In other builds it is the constant true and
+// cond is not evaluated.
+#ifndef BSPLINE_CHECKS
+#define BSPLINE_CHECKS 0
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ bool bs_check_count(bool ok, unsigned long long* word) {
+    if (!ok) atomicAdd(word, 1ULL);
+    return ok;
+}
+#endif
+#define BS_CHECK_OK(cond, word) (!BSPLINE_CHECKS || bs_check_count((cond), (word)))
 
 struct PendingTiming {
     int stage;
@@ -98,6 +115,8 @@ struct bspline_plan_s {
     int sms = 1;            // streaming multiprocessors of the plan's device
     int test_hooks = 0;     // BSPLINE_TEST_* flags
     unsigned direct_below = BSPLINE_GATHER_SPLIT_AUTO;   // gather split (bspline_plan_set_gather_split)
+    int deterministic = 0;  // bspline_plan_set_deterministic: fixed-point spread of the adjoint
+    bs::DeviceBuffer det;   // its accumulator [3][N][N][N] int64 and the cotangent bound
     // Buffers, second stream and events of bspline_run_host (and the second
     // stream of bspline_eval); the copy stream and its events feed the
     // host-to-device copies of bspline_run_host.

@@ -52,15 +52,16 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-int encode_coef_tmap(CUtensorMap* map, const void* coef, int N, int box_z, int box_y, int box_x) {
+int encode_coef_tmap(CUtensorMap* map, const void* coef, int N, int box_z, int box_y, int box_x, int elem_bytes) {
     const EncodeTiledFn fn = encode_tiled();
     if (!fn) return BSPLINE_ERR_CUDA;
-    const cuuint64_t n = (cuuint64_t)N;
-    const cuuint64_t dims[4] = {n, n, n, 3};                            // z, y, x, component
-    const cuuint64_t strides[3] = {n * 4, n * n * 4, n * n * n * 4};  // bytes, dims 1..3
+    const cuuint64_t n = (cuuint64_t)N, eb = (cuuint64_t)elem_bytes;
+    const cuuint64_t dims[4] = {n, n, n, 3};                               // z, y, x, component
+    const cuuint64_t strides[3] = {n * eb, n * n * eb, n * n * n * eb};  // bytes, dims 1..3
     const cuuint32_t box[4] = {(cuuint32_t)box_z, (cuuint32_t)box_y, (cuuint32_t)box_x, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(coef), dims, strides, box, estr,
+    const CUtensorMapDataType t = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUresult r = fn(map, t, 4, const_cast<void*>(coef), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? BSPLINE_OK : BSPLINE_ERR_CUDA;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
 template <typename TR, typename OT, bool SORTED = false, bool PERM = false>
 __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                                BrickGrid g, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
-                               int aggregate, int* __restrict__ perm = nullptr) {
+                               int aggregate, unsigned long long* __restrict__ status, int* __restrict__ perm = nullptr) {
     const unsigned NB = g.NB;
     if constexpr (SORTED) {
         if (*w.unsorted == 0u) return;
@@ -259,7 +260,8 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
         for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
             Rec<TR> r;
             const unsigned k = locate_particle<TR>(x, p, N, scale, order, g, &r);
-            perm[atomicAdd(&w.cursor[k], 1u)] = (int)p;
+            const unsigned d = atomicAdd(&w.cursor[k], 1u);
+            if (BS_CHECK_OK(d < (unsigned)P, status + kStatusBounds)) perm[d] = (int)p;
         }
         return;
     }
@@ -289,7 +291,7 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
         } else if (place) {
             d = atomicAdd(&w.cursor[k], 1u);
         }
-        if (place) {
+        if (place && BS_CHECK_OK(d < w.offset[k] + w.count[k], status + kStatusBounds)) {
             r.idx = (unsigned)p;
             if constexpr (sizeof(TR) == 4) r.pad[0] = r.pad[1] = r.pad[2] = 0u;
             w.s_rec[d] = r;                             // one whole 32-byte sector
@@ -355,8 +357,8 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     } restore{p, main_stream};
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
-        return set_cuda_error(e);                       // non-finite count and tile-wait flag
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * kStatusParticleWords, st)) != cudaSuccess)
+        return set_cuda_error(e);                       // non-finite count, tile-wait flag, checks
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     const bool presorted = (flags & BSPLINE_INTERP_SORTED) != 0;
     const double scale = (double)p->N / p->L;
@@ -385,8 +387,11 @@ int run_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        if (presorted) scatter_kernel<TR, AT, true><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, ou, og, agg);
-        else scatter_kernel<TR, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, ou, og, agg);
+        if (presorted)
+            scatter_kernel<TR, AT, true><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, ou, og, agg,
+                                                                    p->d_status);
+        else
+            scatter_kernel<TR, AT><<<sort_grid, 256, 0, st>>>(x, P, p->N, scale, p->order, g, w, ou, og, agg, p->d_status);
     }
     if (sort_stream) {
         if ((e = cudaEventRecord(sorted, sort_stream)) != cudaSuccess) return set_cuda_error(e);
@@ -418,14 +423,14 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
     cudaStream_t st = p->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
-        return set_cuda_error(e);                       // non-finite count and tile-wait flag
+    if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * kStatusParticleWords, st)) != cudaSuccess)
+        return set_cuda_error(e);                       // non-finite count, tile-wait flag, checks
     const bool grad = !(flags & BSPLINE_INTERP_NO_GRAD);
     bin_kernel<TR, false, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, status,
                                                                NB < kAggregateBricks, (AT*)nullptr, (AT*)nullptr);
     scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     scatter_kernel<TR, AT><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, (AT*)out_u, grad ? (AT*)out_grad : nullptr,
-                                                             NB < kAggregateBricks);
+                                                             NB < kAggregateBricks, status);
     int rc = dispatch_order<CT, AT, TR>(p, coeffs, w, g, out_u, out_grad, grad);
     if (rc) return rc;
     return set_cuda_error(cudaGetLastError());
@@ -463,8 +468,8 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     cudaStream_t st = p->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
-        return set_cuda_error(e);                       // non-finite count and tile-wait flag
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * kStatusParticleWords, st)) != cudaSuccess)
+        return set_cuda_error(e);                       // non-finite count, tile-wait flag, checks
     {
         StageTimer tm(p, BSPLINE_STAGE_BIN);
         bin_kernel<TR, false, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w,
@@ -477,9 +482,14 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, g_x, nullptr, NB < kAggregateBricks);
+        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, g_x, nullptr, NB < kAggregateBricks,
+                                                                     p->d_status);
     }
     const long long items = (long long)NB + (P + kChunk - 1) / kChunk;
+    if (g_coef && p->deterministic && sizeof(TR) == 4) {
+        // the fixed-point accumulator of the deterministic spread and its bound word
+        if ((rc = p->det.grow(sizeof(long long) * 3 * (size_t)p->N * p->N * p->N + 16))) return rc;
+    }
     if (g_coef) {
         StageTimer tm(p, BSPLINE_STAGE_SPREAD);
         rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, nullptr);
@@ -507,7 +517,7 @@ int run_sort_order(bspline_plan_s* p, const double* x, int64_t P, int* perm) {
     cudaStream_t st = p->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * 2, st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned long long) * kStatusParticleWords, st)) != cudaSuccess)
         return set_cuda_error(e);
     const double scale = (double)p->N / p->L;
     const int agg = NB < kAggregateBricks;
@@ -516,7 +526,7 @@ int run_sort_order(bspline_plan_s* p, const double* x, int64_t P, int* perm) {
     scan_kernel<false><<<1, 1024, 0, st>>>(w.count, w.offset, w.cursor, w.chunk, w.item, NB, 0u);
     scatter_kernel<TR, float, false, true><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, scale, p->order, g, w,
                                                                             (float*)nullptr, (float*)nullptr, agg,
-                                                                            perm);
+                                                                            p->d_status, perm);
     return set_cuda_error(cudaGetLastError());
 }
 

@@ -12,11 +12,11 @@
 namespace bs {
 namespace gather_impl {
 
-// Tensor map of the FP32 coefficient array [3][N][N][N] for TMA tile loads:
-// box (z, y, x, component) = (box_z, box_y, box_x, 1).  Defined in
-// particles.cu; BSPLINE_OK, or an error if the driver's encoder is missing
-// or refuses (the caller then stages with cp.async).
-int encode_coef_tmap(CUtensorMap* map, const void* coef, int N, int box_z, int box_y, int box_x);
+// Tensor map of the coefficient array [3][N][N][N] (FP32, or BF16 with
+// elem_bytes = 2) for TMA tile loads: box (z, y, x, component) = (box_z,
+// box_y, box_x, 1).  Defined in particles.cu; BSPLINE_OK, or an error if the
+// driver's encoder is missing or refuses (the caller then stages with cp.async).
+int encode_coef_tmap(CUtensorMap* map, const void* coef, int N, int box_z, int box_y, int box_x, int elem_bytes = 4);
 
 constexpr int kAnchorBits = 10;          // N <= 1024
 
@@ -427,75 +427,86 @@ __device__ __forceinline__ void stage_tile_bf16(float* tile, const __nv_bfloat16
     }
 }
 
-// BF16 coefficients, asynchronously: the raw BF16 tile (same element layout,
-// half the bytes) is copied with 16-byte cp.async into the upper half of the
-// FP32 tile's shared memory while the gather buckets its particles, then
-// widened in place by expand_bf16_tile.  Needs z rows of a multiple of 8
-// elements (16-byte copies that never straddle the periodic wrap: z0 is a
-// multiple of 16 and N of 8).
-template <int ORD, int BYO = 0> constexpr bool bf16_async() {
-    return Shape<__nv_bfloat16, ORD, BYO>::PZ % 8 == 0 && (3 * Shape<__nv_bfloat16, ORD, BYO>::TS) % 8 == 0;
-}
-template <int ORD, int BYO = 0>
-__device__ __forceinline__ void stage_tile_bf16_async(float* tile, const __nv_bfloat16* __restrict__ coef, int N,
-                                                      int x0, int y0, int z0) {
+// BF16 coefficients stay BF16 in shared memory, in two copies of the tile
+// ([c][x][y][z], rows of PZ elements, 16-byte aligned): copy A holds element
+// z of a row at z, copy B holds element z + 1 at z.  A stencil line of ORD
+// values starting at tile z = oz is then ceil(ORD / 2) aligned 32-bit words:
+// copy A from word oz / 2 if oz is even, copy B from word (oz - 1) / 2 if it
+// is odd.  Each word carries two consecutive values (the lower z in its low
+// half), widened to FP32 in registers, so the contraction reads half the
+// shared-memory bytes of an FP32 tile with the same FP32 arithmetic.
+template <int ORD, int BYO = 0> struct Bf16Pair {
     using S = Shape<__nv_bfloat16, ORD, BYO>;
-    static_assert(S::PZ % 8 == 0, "16-byte BF16 rows");
-    constexpr int E = 3 * S::TS;                      // elements of the tile
-    constexpr int CH = S::PZ / 8;                     // 16-byte chunks per row
-    constexpr int PER = S::EY * CH;
-    constexpr int NI = (PER + 31) / 32;
-    __nv_bfloat16* raw = reinterpret_cast<__nv_bfloat16*>(tile) + E;   // bytes [2E, 4E) of the tile
+    static constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ;
+    static constexpr int PZ = (EZ + 7) & ~7;            // elements per row: 16-byte rows
+    static constexpr int SYW = PZ / 2, SXW = EY * SYW;  // words per row, per x-plane
+    static constexpr int TSW = (EX * SXW + 31) & ~31;   // words per component
+    static constexpr int COPYW = 3 * TSW;               // words per copy
+    static constexpr int NWL = (ORD + 1) / 2;           // words per stencil line
+    static constexpr size_t bytes = 2 * sizeof(unsigned) * (size_t)COPYW;
+};
+
+// Copy A of a brick: 16-byte cp.async chunks of 8 values (z0 is a multiple of
+// 16 and N of 8, so no chunk straddles the periodic wrap); element by element
+// below N = 16.  The caller waits for the copies and synchronises.
+template <int ORD, int BYO>
+__device__ __forceinline__ void stage_bf16_copy_a(unsigned* words, const __nv_bfloat16* __restrict__ coef, int N,
+                                                  int x0, int y0, int z0) {
+    using T = Bf16Pair<ORD, BYO>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int goff[NI], soff[NI];
+    if (N >= 16) {
+        constexpr int CH = T::PZ / 8;                   // chunks per row
+        constexpr int PER = T::EY * CH;                 // chunks per (c, x) plane
+        constexpr int NI = (PER + 31) / 32;
+        int goff[NI], soff[NI];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-        const int f = lane + 32 * i;
-        const int iy = f / CH, ch = f - iy * CH;
-        goff[i] = f < PER ? wrap_index(y0 + iy, N) * N + wrap_index(z0 + 8 * ch, N) : -1;
-        soff[i] = iy * S::SY + 8 * ch;
-    }
-    for (int pl = warp; pl < 3 * S::EX; pl += nw) {
-        const int c = pl / S::EX, ix = pl - c * S::EX;
-        const __nv_bfloat16* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
-        __nv_bfloat16* dst = raw + (size_t)c * S::TS + (size_t)ix * S::SX;
+        for (int i = 0; i < NI; ++i) {
+            const int f = lane + 32 * i;
+            const int iy = f / CH, ch = f - iy * CH;
+            goff[i] = f < PER ? wrap_index(y0 + iy, N) * N + wrap_index(z0 + 8 * ch, N) : -1;
+            soff[i] = iy * T::SYW + 4 * ch;
+        }
+        for (int pl = warp; pl < 3 * T::EX; pl += nw) {
+            const int c = pl / T::EX, ix = pl - c * T::EX;
+            const __nv_bfloat16* plane = coef + ((size_t)c * N + wrap_index(x0 + ix, N)) * (size_t)N * N;
+            unsigned* dst = words + (size_t)c * T::TSW + (size_t)ix * T::SXW;
 #pragma unroll
-        for (int i = 0; i < NI; ++i)
-            if (goff[i] >= 0) cp_async16(dst + soff[i], plane + goff[i]);
+            for (int i = 0; i < NI; ++i)
+                if (goff[i] >= 0) cp_async16(dst + soff[i], plane + goff[i]);
+        }
+    } else {
+        __nv_bfloat16* e = reinterpret_cast<__nv_bfloat16*>(words);
+        for (int k = threadIdx.x; k < 3 * T::EX * T::EY * T::PZ; k += blockDim.x) {
+            const int z = k % T::PZ, r = k / T::PZ, iy = r % T::EY, ix = (r / T::EY) % T::EX, c = r / (T::EY * T::EX);
+            e[2 * ((size_t)c * T::TSW + (size_t)ix * T::SXW + (size_t)iy * T::SYW) + z] =
+                coef[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N + wrap_index(z0 + z, N)];
+        }
     }
 }
 
-// Widens the raw BF16 tile in place, in ascending chunks of 8 elements per
-// thread: FP32 element e goes to bytes [4e, 4e + 4) from BF16 bytes [2E + 2e,
-// 2E + 2e + 2).  A chunk's reads all finish (barrier) before its writes, and
-// a write never reaches BF16 data of a later chunk (4 (k+1) C <= 2E + 2 (k+1) C
-// while (k + 1) C <= E).  Ends with a barrier.
-template <int ORD, int BYO = 0>
-__device__ __forceinline__ void expand_bf16_tile(float* tile) {
-    using S = Shape<__nv_bfloat16, ORD, BYO>;
-    constexpr int E = 3 * S::TS;
-    static_assert(E % 8 == 0, "whole 16-byte chunks");
-    const uint4* raw = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(tile) + E);
-    const int C = 8 * (int)blockDim.x;
-    for (int k0 = 0; k0 < E; k0 += C) {
-        const int e = k0 + 8 * (int)threadIdx.x;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (e < E) v = raw[e / 8];
-        __syncthreads();
-        if (e < E) {
-            const unsigned w4[4] = {v.x, v.y, v.z, v.w};
-            float f[8];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                f[2 * q] = __uint_as_float(w4[q] << 16);     // bf16 -> fp32: the high half of the word
-                f[2 * q + 1] = __uint_as_float(w4[q] & 0xffff0000u);
-            }
-            *reinterpret_cast<float4*>(tile + e) = make_float4(f[0], f[1], f[2], f[3]);
-            *reinterpret_cast<float4*>(tile + e + 4) = make_float4(f[4], f[5], f[6], f[7]);
-        }
+// Copy B from copy A: word j = (A[2j + 1], A[2j + 2]), four words per
+// thread and step (16-byte accesses).  The upper value of a row's last word
+// comes from the next row (or is zero at the end of the copy): it is never
+// part of a stencil line.  Call after copy A is complete and visible; ends
+// with a barrier.
+template <int ORD, int BYO>
+__device__ __forceinline__ void build_bf16_copy_b(unsigned* words) {
+    using T = Bf16Pair<ORD, BYO>;
+    static_assert(T::COPYW % 4 == 0, "16-byte steps");
+    const uint4* a4 = reinterpret_cast<const uint4*>(words);
+    uint4* b4 = reinterpret_cast<uint4*>(words + T::COPYW);
+    for (int v = threadIdx.x; v < T::COPYW / 4; v += blockDim.x) {
+        const uint4 a = a4[v];
+        const unsigned nx = (4 * v + 4 < T::COPYW) ? words[4 * v + 4] : 0u;
+        b4[v] = make_uint4(__byte_perm(a.x, a.y, 0x5432), __byte_perm(a.y, a.z, 0x5432), __byte_perm(a.z, a.w, 0x5432),
+                           __byte_perm(a.w, nx, 0x5432));
     }
     __syncthreads();
 }
+
+
+__device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 
 // TMA staging of an FP32 brick away from the periodic seams: thread 0 arms the
 // mbarrier and issues one box (PZ, EY, EX, 1) per component; the boxes never
@@ -516,6 +527,25 @@ __device__ __forceinline__ bool stage_tile_tma(float* tile, const CUtensorMap* m
         if (use_tma != kTmaArmOnly) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) tma_load_4d(tile + c * S::TS, map, z0, y0, x0, c, bar);
+        }
+    }
+    return tma;
+}
+
+// TMA staging of copy A of a BF16 pair tile away from the periodic seams (as
+// stage_tile_tma: one box (PZ, EY, EX, 1) per component, into the component's
+// 128-byte aligned words); returns whether the brick was staged this way.
+template <int ORD, int BYO>
+__device__ __forceinline__ bool stage_bf16_tma(unsigned* words, const CUtensorMap* map, unsigned long long* bar,
+                                               int N, int x0, int y0, int z0, int use_tma) {
+    using T = Bf16Pair<ORD, BYO>;
+    const bool tma = use_tma && x0 + T::EX <= N && y0 + T::EY <= N && z0 + T::EZ <= N;
+    if (tma && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, 3u * T::PZ * T::EY * T::EX * 2u);
+        if (use_tma != kTmaArmOnly) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tma_load_4d(words + c * T::TSW, map, z0, y0, x0, c, bar);
         }
     }
     return tma;
@@ -689,6 +719,62 @@ __device__ __forceinline__ void row_x2(LDR ldr, const PairWeights<ORD>& pw, cons
     *s01 = y01.x + y01.y;
 }
 
+// row_x2 on a BF16 pair tile: line jy of the x-row starts at word row0 + jy
+// SYW; the same terms in the same order as row_x2 (pairs of y-lines, z
+// ascending), each value the exact FP32 value of its BF16 coefficient.
+template <int ORD, bool GRAD, int SYW>
+__device__ __forceinline__ void row_x2_words(const unsigned* __restrict__ row0, const PairWeights<ORD>& pw,
+                                             const float (&wy)[ORD], const float (&dwy)[ORD], const float (&wz)[ORD],
+                                             const float (&dwz)[ORD], float* s00, float* s10, float* s01) {
+    constexpr int NP = ORD / 2, NWL = (ORD + 1) / 2;
+    float2 y00 = make_float2(0.f, 0.f), y10 = y00, y01 = y00;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const unsigned* l0 = row0 + (2 * p) * SYW;
+        const unsigned* l1 = l0 + SYW;
+        float2 z0 = make_float2(0.f, 0.f), z1 = z0;
+#pragma unroll
+        for (int k = 0; k < NWL; ++k) {
+            const unsigned a = l0[k], b = l1[k];
+            const float2 v0 = make_float2(bf16_lo(a), bf16_lo(b));
+            z0 = __ffma2_rn(pw.wz2[2 * k], v0, z0);
+            if (GRAD) z1 = __ffma2_rn(pw.dwz2[2 * k], v0, z1);
+            if (2 * k + 1 < ORD) {
+                const float2 v1 = make_float2(bf16_hi(a), bf16_hi(b));
+                z0 = __ffma2_rn(pw.wz2[2 * k + 1], v1, z0);
+                if (GRAD) z1 = __ffma2_rn(pw.dwz2[2 * k + 1], v1, z1);
+            }
+        }
+        y00 = __ffma2_rn(pw.wyp[p], z0, y00);
+        if (GRAD) {
+            y10 = __ffma2_rn(pw.dwyp[p], z0, y10);
+            y01 = __ffma2_rn(pw.wyp[p], z1, y01);
+        }
+    }
+    if constexpr (ORD % 2 == 1) {                   // the unpaired last line
+        const unsigned* l = row0 + (ORD - 1) * SYW;
+        float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < NWL; ++k) {
+            const unsigned a = l[k];
+            z0 = fmaf(wz[2 * k], bf16_lo(a), z0);
+            if (GRAD) z1 = fmaf(dwz[2 * k], bf16_lo(a), z1);
+            if (2 * k + 1 < ORD) {
+                z0 = fmaf(wz[2 * k + 1], bf16_hi(a), z0);
+                if (GRAD) z1 = fmaf(dwz[2 * k + 1], bf16_hi(a), z1);
+            }
+        }
+        y00.x = fmaf(wy[ORD - 1], z0, y00.x);
+        if (GRAD) {
+            y10.x = fmaf(dwy[ORD - 1], z0, y10.x);
+            y01.x = fmaf(wy[ORD - 1], z1, y01.x);
+        }
+    }
+    *s00 = y00.x + y00.y;
+    *s10 = y10.x + y10.y;
+    *s01 = y01.x + y01.y;
+}
+
 // Accumulation of one x-row's sums into u and the gradient.
 template <bool GRAD>
 __device__ __forceinline__ void add_row(float wxj, float dwxj, float s00, float s10, float s01, float* u, float* gx,
@@ -753,11 +839,40 @@ __device__ __forceinline__ void eval_component_x2(const float* __restrict__ base
                            dwy, wz, dwz, dscale, out_u, out_grad);
 }
 
+// Components c0..c0+NC-1 of one particle from a BF16 pair tile (weights once);
+// base = the particle's first stencil word of component 0 in its copy.
+template <int ORD, bool GRAD, typename T, int NC>
+__device__ __forceinline__ void eval_bf16(const unsigned* __restrict__ base, int c0, float tx, float ty, float tz,
+                                          float dscale, float* __restrict__ out_u, float* __restrict__ out_grad) {
+    float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+    bspline_weights<ORD, float>(tx, wx, dwx);
+    bspline_weights<ORD, float>(ty, wy, dwy);
+    bspline_weights<ORD, float>(tz, wz, dwz);
+    const PairWeights<ORD> pw(wz, dwz, wy, dwy);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const unsigned* cb = base + (c0 + q) * T::TSW;
+        float u = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int jx = 0; jx < ORD; ++jx) {
+            float s00, s10, s01;
+            row_x2_words<ORD, GRAD, T::SYW>(cb + jx * T::SXW, pw, wy, dwy, wz, dwz, &s00, &s10, &s01);
+            add_row<GRAD>(wx[jx], dwx[jx], s00, s10, s01, &u, &gx, &gy, &gz);
+        }
+        out_u[q] = u;
+        if (GRAD) {
+            out_grad[3 * q + 0] = gx * dscale;
+            out_grad[3 * q + 1] = gy * dscale;
+            out_grad[3 * q + 2] = gz * dscale;
+        }
+    }
+}
+
 // FP64: one thread per particle (the FP64 pipe, not shared memory, bounds it).
 template <int ORD, typename TR, bool GRAD>
 __global__ void __launch_bounds__(128)
 gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, double* __restrict__ out_u,
-           double* __restrict__ out_grad, double dscale) {
+           double* __restrict__ out_grad, double dscale, unsigned long long* __restrict__ status) {
     using S = Shape<double, ORD>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* tile = reinterpret_cast<double*>(smem_raw);
@@ -775,6 +890,10 @@ gather_f64(const double* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, doubl
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
         const unsigned idx = rc.idx;
+        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
+                             (long long)idx < w.P,
+                         status + kStatusBounds))
+            continue;
         double u[3], gr[9];
         eval_particle<ORD, double, GRAD, S::SX, S::SY, S::TS>(tile + ox * S::SX + oy * S::SY + oz, (double)rc.t[0],
                                                                (double)rc.t[1], (double)rc.t[2], dscale, u, gr);
@@ -846,22 +965,36 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
     const unsigned end = w.offset[brick] + w.count[brick];
     int x0, y0, z0;
     brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
-    // BF16 tiles of orders 6-8 are copied raw and asynchronously (widened after the bucketing)
-    constexpr bool kRawBf16 = sizeof(CT) == 2 && bf16_async<ORD, BYO>();
-    const bool raw_bf16 = kRawBf16 && N >= 16;
-    // FP32 bricks away from the periodic seams by TMA, the others with cp.async
-    const bool tma = stage_tile_tma<ORD, CT, BYO>(tile, tmap, &s_mbar, N, x0, y0, z0, use_tma);
+    // BF16: the pair tile (copy A now, asynchronously; copy B after the bucketing)
+    constexpr bool kBf16 = sizeof(CT) == 2;
+    using T2 = Bf16Pair<ORD, BYO>;
+    unsigned* words = reinterpret_cast<unsigned*>(tile);
+    // bricks away from the periodic seams by TMA, the others with cp.async
+    bool tma;
+    if constexpr (kBf16) tma = stage_bf16_tma<ORD, BYO>(words, tmap, &s_mbar, N, x0, y0, z0, use_tma);
+    else tma = stage_tile_tma<ORD, CT, BYO>(tile, tmap, &s_mbar, N, x0, y0, z0, use_tma);
     if (tma) {
-    } else if constexpr (kRawBf16) {
-        if (raw_bf16)
-            stage_tile_bf16_async<ORD, BYO>(tile, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
-        else stage_brick<ORD, CT, BYO>(tile, coef, N, x0, y0, z0);
+    } else if constexpr (kBf16) {
+        stage_bf16_copy_a<ORD, BYO>(words, reinterpret_cast<const __nv_bfloat16*>(coef), N, x0, y0, z0);
     } else {
         stage_brick<ORD, CT, BYO>(tile, coef, N, x0, y0, z0);
     }
+    // shared-memory bank (word index mod 32) of a particle's first stencil value
+    auto bank_of = [&](int ox, int oy, int oz) -> unsigned {
+        if constexpr (kBf16)
+            return (unsigned)(((oz & 1) ? T2::COPYW : 0) + (ox * T2::EY + oy) * T2::SYW + (oz >> 1)) & 31u;
+        else
+            return (unsigned)(ox * S::SX + oy * S::SY + oz) & 31u;
+    };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec_out = ((reinterpret_cast<uintptr_t>(out_u) | (GRAD ? reinterpret_cast<uintptr_t>(out_grad) : 0u)) &
                           7u) == 0u;
+    // checks build: the stencil inside the staged tile, the output index inside the arrays
+    auto origin_ok = [&](int ox, int oy, int oz, unsigned idx) {
+        return BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
+                               (long long)idx < w.P,
+                           status + kStatusBounds);
+    };
     {
         const int n = (int)min(chunk_len, end - c0);
         if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
@@ -877,7 +1010,7 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
                 const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(cp & 1023u) - z0;
-                const unsigned r = (unsigned)(ox * S::SX + oy * S::SY + oz) & 31u;
+                const unsigned r = bank_of(ox, oy, oz);
                 packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
             }
         }
@@ -894,7 +1027,7 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
                     const unsigned bq = s_bucket[q];
                     pos += min(bq, rk) + ((q < r && bq > rk) ? 1u : 0u);
                 }
-                s_order[pos] = (unsigned short)i;
+                if (BS_CHECK_OK(pos < (unsigned)n, status + kStatusBounds)) s_order[pos] = (unsigned short)i;
             }
         }
         cp_async_wait_all();
@@ -903,9 +1036,7 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
             return;
         }
         __syncthreads();                                  // tile and order ready
-        if constexpr (kRawBf16) {
-            if (raw_bf16) expand_bf16_tile<ORD, BYO>(tile);
-        }
+        if constexpr (kBf16) build_bf16_copy_b<ORD, BYO>(words);
         // Warp jobs over that order.  Rank j holds #{banks with more than j
         // particles} particles, non-increasing in j.  While a rank holds at
         // least 16 particles it is one job (every load conflict-free); the
@@ -962,9 +1093,16 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(rc.cell & 1023u) - z0;
+                if (!origin_ok(ox, oy, oz, idx)) continue;
                 float u[3], g[9];
-                eval_particle_x2<ORD, GRAD, S::SX, S::SY, S::TS>(tile + ox * S::SX + oy * S::SY + oz, (float)rc.t[0],
-                                                                  (float)rc.t[1], (float)rc.t[2], dscale, u, g);
+                if constexpr (kBf16)
+                    eval_bf16<ORD, GRAD, T2, 3>(words + ((oz & 1) ? T2::COPYW : 0) + (ox * T2::EY + oy) * T2::SYW +
+                                                    (oz >> 1),
+                                                0, (float)rc.t[0], (float)rc.t[1], (float)rc.t[2], dscale, u, g);
+                else
+                    eval_particle_x2<ORD, GRAD, S::SX, S::SY, S::TS>(tile + ox * S::SX + oy * S::SY + oz,
+                                                                      (float)rc.t[0], (float)rc.t[1], (float)rc.t[2],
+                                                                      dscale, u, g);
                 if (vec_out) {
                     store_u3(out_u + 3 * (size_t)idx, idx & 1u, u);
                     if (GRAD) store_g9(out_grad + 9 * (size_t)idx, idx & 1u, g);
@@ -990,10 +1128,16 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
                 const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
                 const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
                 const int oz = (int)(rc.cell & 1023u) - z0;
+                if (!origin_ok(ox, oy, oz, idx)) continue;
                 float u, g[3];
-                eval_component_x2<ORD, GRAD, S::SX, S::SY>(tile + c * S::TS + ox * S::SX + oy * S::SY + oz,
-                                                           (float)rc.t[0], (float)rc.t[1], (float)rc.t[2], dscale,
-                                                           &u, g);
+                if constexpr (kBf16)
+                    eval_bf16<ORD, GRAD, T2, 1>(words + ((oz & 1) ? T2::COPYW : 0) + (ox * T2::EY + oy) * T2::SYW +
+                                                    (oz >> 1),
+                                                (int)c, (float)rc.t[0], (float)rc.t[1], (float)rc.t[2], dscale, &u, g);
+                else
+                    eval_component_x2<ORD, GRAD, S::SX, S::SY>(tile + c * S::TS + ox * S::SX + oy * S::SY + oz,
+                                                               (float)rc.t[0], (float)rc.t[1], (float)rc.t[2], dscale,
+                                                               &u, g);
                 out_u[3 * (size_t)idx + c] = u;
                 if (GRAD) {
 #pragma unroll
@@ -1028,7 +1172,7 @@ gather_f32(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w, float* __
 template <int ORD, typename CT, typename TR, bool GRAD>
 __global__ void __launch_bounds__(256, 2)
 gather_direct(const CT* __restrict__ coef, int N, unsigned NB, Ws<TR> w, float* __restrict__ out_u,
-              float* __restrict__ out_grad, float dscale) {
+              float* __restrict__ out_grad, float dscale, unsigned long long* __restrict__ status) {
     const unsigned beg = w.offset[NB + 2], end = w.offset[NB];
     const size_t NN = (size_t)N * N;
     for (unsigned i = beg + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
@@ -1036,6 +1180,7 @@ gather_direct(const CT* __restrict__ coef, int N, unsigned NB, Ws<TR> w, float* 
         const int ax = (int)(rc.cell >> (2 * kAnchorBits));
         const int ay = (int)((rc.cell >> kAnchorBits) & 1023u);
         const int az = (int)(rc.cell & 1023u);
+        if (!BS_CHECK_OK(ax < N && ay < N && az < N && (long long)rc.idx < w.P, status + kStatusBounds)) continue;
         float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
         bspline_weights<ORD, float>((float)rc.t[0], wx, dwx);
         bspline_weights<ORD, float>((float)rc.t[1], wy, dwy);
@@ -1089,18 +1234,22 @@ int run_gather(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, voi
         auto k = grad ? gather_f64<ORD, TR, true> : gather_f64<ORD, TR, false>;
         if ((rc = set_smem(k, sm))) return rc;
         k<<<NB, 128, sm, p->stream>>>(reinterpret_cast<const double*>(coeffs), p->N, g, w, (double*)out_u,
-                                      grad ? (double*)out_grad : nullptr, dscale);
+                                      grad ? (double*)out_grad : nullptr, dscale, p->d_status);
     } else {
         auto k = grad ? gather_f32<ORD, CT, TR, true> : gather_f32<ORD, CT, TR, false>;
-        const size_t sm_aligned = sm + 128;              // room to align the tile to 128 bytes
+        // room to align the tile to 128 bytes; BF16: the two copies of the pair tile
+        const size_t sm_aligned = (sizeof(CT) == 2 ? Bf16Pair<ORD>::bytes : sm) + 128;
         if ((rc = set_smem(k, sm_aligned))) return rc;
         // FP32 coefficients: a TMA tensor map for the interior bricks (cp.async if it cannot be made)
         using S = Shape<CT, ORD>;
         CUtensorMap tmap;
         std::memset(&tmap, 0, sizeof tmap);
         int use_tma = 0;
-        if (sizeof(CT) == 4 && p->N >= 16 && !(p->test_hooks & BSPLINE_TEST_NO_TMA))
-            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? kTmaOn : 0;
+        if (p->N >= 16 && !(p->test_hooks & BSPLINE_TEST_NO_TMA)) {
+            const int box_z = sizeof(CT) == 2 ? Bf16Pair<ORD>::PZ : S::PZ;
+            use_tma = encode_coef_tmap(&tmap, coeffs, p->N, box_z, S::EY, S::EX, (int)sizeof(CT)) == BSPLINE_OK
+                          ? kTmaOn : 0;
+        }
         if (use_tma && (p->test_hooks & BSPLINE_TEST_SKIP_TMA_ISSUE)) use_tma = kTmaArmOnly;
         // work items: at most one partial chunk per brick plus P / kChunk full ones
         const long long items = (long long)NB + (w.P + kChunk - 1) / kChunk;
@@ -1127,7 +1276,7 @@ int run_gather_direct(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid
         const long long want = (w.P + 255) / 256;
         const unsigned blocks = (unsigned)std::max(1LL, std::min(want, 32LL * p->sms));
         k<<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const CT*>(coeffs), p->N, NB, w, (float*)out_u,
-                                         grad ? (float*)out_grad : nullptr, dscale);
+                                         grad ? (float*)out_grad : nullptr, dscale, p->d_status);
         return BSPLINE_OK;
     }
 }

@@ -111,6 +111,44 @@ def test_spread_f32(B, order, dtype):
     assert normwise(gc.cpu().numpy(), O.spread(x, gu, gg, N, order)) < TOL32_SPREAD
 
 
+@pytest.mark.parametrize("order,dtype,with_grad", [(4, "f32", True), (6, "bf16", True), (2, "f32", False),
+                                                    (8, "f32", True)])
+def test_deterministic_spread_bit_identical_and_oracle(B, order, dtype, with_grad):
+    """bspline_plan_set_deterministic: exact fixed-point sums give bit-identical g_coeffs and g_u_hat on
+    repeated calls (and on a different launch order of the same work), within the FP32 spread's
+    tolerance of the oracle; accumulation into a nonzero g_coeffs adds the same sums."""
+    N, P = 32, 30000
+    x = synth.clustered_particles(P, seed=40 + order)
+    plan = B.Plan(N, order, dtype)
+    plan.set_deterministic(True)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=order + 300, with_grad=with_grad)
+    xt = _dev(x, torch.float64)
+    h1, _, a1 = plan.spread_adjoint(xt, gu_t, gg_t)
+    h2, _, a2 = plan.spread_adjoint(xt, gu_t, gg_t)
+    assert torch.equal(a1, a2) and torch.equal(h1, h2)
+    # the same particles in another order: other sorted slots, other atomics order, same sums
+    perm = torch.randperm(P, generator=torch.Generator().manual_seed(1)).cuda()
+    h3, _, a3 = plan.spread_adjoint(xt[perm].contiguous(), gu_t[perm].contiguous(),
+                                    gg_t[perm].contiguous() if with_grad else None)
+    assert torch.equal(a1, a3) and torch.equal(h1, h3)
+    ref = O.spread(x, gu, gg, N, order)
+    assert normwise(a1.cpu().numpy(), ref) < TOL32_SPREAD
+    base = torch.full_like(a1, 0.25)
+    _, _, a4 = plan.spread_adjoint(xt, gu_t, gg_t, g_coef=base.clone(), u_hat_grad=False)
+    assert torch.equal(a4, base + a1)
+    # the default mode agrees within the FP32 tolerance
+    plan.set_deterministic(False)
+    _, _, a5 = plan.spread_adjoint(xt, gu_t, gg_t, u_hat_grad=False)
+    assert normwise(a5.cpu().numpy(), a1.cpu().numpy()) < TOL32_SPREAD
+
+
+def test_deterministic_mode_refused_for_f64(B):
+    plan = B.Plan(16, 4, "f64")
+    with pytest.raises(B.BSplineError) as exc:
+        plan.set_deterministic(True)
+    assert exc.value.code == B.ERR_NOT_IMPLEMENTED
+
+
 def test_spread_accumulates_and_optional_cotangents(B):
     N, order, P = 16, 4, 500
     x = _dev(synth.uniform_particles(P, seed=3), torch.float64)

@@ -496,13 +496,15 @@ def test_direct_and_staged_gathers_agree_bit_for_bit(B, dtype, N, order):
     assert normwise(outs[0][0], ru) < tol["u"] and normwise(outs[0][1], rg) < tol["grad"]
 
 
-@pytest.mark.parametrize("N,order", [(64, 6), (96, 4), (64, 8), (128, 3)])
-def test_tma_and_cp_async_staging_agree_bit_for_bit(B, N, order):
-    """FP32 bricks away from the periodic seams are staged by TMA tensor copies, the others (and all of
-    them with BSPLINE_TEST_NO_TMA) by cp.async: the same tile, so the same bits."""
+@pytest.mark.parametrize("N,order,dtype", [(64, 6, "f32"), (96, 4, "f32"), (64, 8, "f32"), (128, 3, "f32"),
+                                           (64, 6, "bf16"), (96, 5, "bf16"), (64, 8, "bf16")])
+def test_tma_and_cp_async_staging_agree_bit_for_bit(B, N, order, dtype):
+    """Bricks away from the periodic seams are staged by TMA tensor copies (FP32 tiles; the first copy
+    of a BF16 pair tile), the others (and all of them with BSPLINE_TEST_NO_TMA) by cp.async: the same
+    tile, so the same bits."""
     half = synth.kolmogorov_field(N, seed=70 + order).dense()
     x = torch.from_numpy(synth.clustered_particles(30000, seed=71)).cuda()
-    plan = B.Plan(N, order, "f32")
+    plan = B.Plan(N, order, dtype)
     coef = plan.coeffs(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
     plan.set_gather_split(0)                              # every brick staged
     u_t, g_t = plan.interp(coef, x)
@@ -512,7 +514,8 @@ def test_tma_and_cp_async_staging_agree_bit_for_bit(B, N, order):
     assert plan.status() == 0
     assert torch.equal(u_t, u_c) and torch.equal(g_t, g_c)
     ru, rg = O.interpolate(rounded_input(half, "f32"), x.cpu().numpy(), order)
-    assert normwise(u_t.cpu().numpy(), ru) < TOL32["u"] and normwise(g_t.cpu().numpy(), rg) < TOL32["grad"]
+    tol = TOL32 if dtype == "f32" else TOL16
+    assert normwise(u_t.cpu().numpy(), ru) < tol["u"] and normwise(g_t.cpu().numpy(), rg) < tol["grad"]
 
 
 def brick_keys(x, N, order, dtype):
