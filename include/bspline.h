@@ -360,7 +360,9 @@ int bspline_interp_noalloc(const void* coeffs, int N, int order, bspline_dtype d
  * structure for many small fields (grid size, order and dtype may differ per
  * field), whose short kernels would otherwise leave the GPU idle.
  * When every field has an FP32 plan of one order and u and grad u are wanted
- * for every field with particles, the particle side of all fields runs as one
+ * for every field with particles, the fields of one grid size and prefilter
+ * are transformed together (one launch of each transform kernel per group, in
+ * workspace the batch owns), and the particle side of all fields runs as one
  * persistent kernel after the transforms: a device work queue of count, scan,
  * placement and gather tasks (the steps of bspline_interp; Section 5 locate,
  * Sections 3-4 evaluation), taken in order by every CTA, each task waiting

@@ -2,13 +2,14 @@
 //
 // The paper evaluates one field at a time; many small fields (different grid
 // sizes and particle counts) leave most of the GPU idle between the short
-// kernels of each.  A batch records the coefficient transform of every field
-// into one graph, the fields round-robin over K concurrent streams (a plan's
-// fields stay on one stream, since they share its workspace).  The particle
-// side of every field then runs as ONE persistent kernel walking a device
-// work queue of count, scan, placement and gather tasks (batch_queue.cuh),
-// when the fields allow it (FP32 coefficients, one order, u and grad u);
-// otherwise each field's evaluation is recorded after its transform.  The
+// kernels of each.  When the fields allow it (FP32 coefficients, one order,
+// u and grad u), a batch records one transform launch pair per group of
+// fields of equal grid size (the groups round-robin over K concurrent
+// streams), then ONE persistent kernel for the particle side of every field,
+// walking a device work queue of count, scan, placement and gather tasks
+// (batch_queue.cuh).  Otherwise each field's transform and evaluation are
+// recorded, the fields round-robin over the K streams (a plan's fields stay
+// on one stream, since they share its workspace).  The
 // graph is replayed with one launch.  K, the queue's brick y extent and its
 // particles per gather item are chosen by timing (bspline_batch_autotune).
 #include <algorithm>
@@ -50,6 +51,15 @@ struct bspline_batch_s {
     size_t zero_bytes = 0;              // leading bytes of qbuf cleared before every launch
     bs::batch_impl::Queue q{};
     cudaStream_t last_stream = nullptr; // stream of the last launch (bspline_batch_status)
+    // transforms of the queue path: the fields grouped by grid size and prefilter, one launch pair per group
+    struct Group {
+        int plan;                       // a field whose plan supplies the tables
+        int nfields;
+        void** ptrs;                    // device: nfields u_hat pointers, then nfields coefficient pointers
+        void* work;                     // device: the group's transform workspace
+    };
+    std::vector<Group> groups;
+    bs::DeviceBuffer tbuf;
 };
 
 namespace {
@@ -181,6 +191,41 @@ int build_queue(bspline_batch_s* b, int by, unsigned chunk_len) {
     return BSPLINE_OK;
 }
 
+// Group the fields by grid size and prefilter (order and dtype are the batch's), lay out each group's
+// pointer arrays and transform workspace in tbuf, and upload the pointers.
+int build_groups(bspline_batch_s* b) {
+    std::map<std::pair<int, int>, std::vector<int>> by;
+    for (int i = 0; i < b->n; ++i) by[{b->plans[i]->N, b->plans[i]->prefilter}].push_back(i);
+    b->groups.clear();
+    size_t off = 0;
+    std::vector<size_t> offs;
+    for (auto& kv : by) {
+        const std::vector<int>& f = kv.second;
+        offs.push_back(off);
+        off = align256(off + sizeof(void*) * 2 * f.size());
+        offs.push_back(off);
+        off = align256(off + coeffs_fields_workspace_bytes(b->plans[f[0]], (int)f.size()));
+    }
+    int rc = b->tbuf.grow(off);
+    if (rc) return rc;
+    char* base = static_cast<char*>(b->tbuf.ptr);
+    size_t gi = 0;
+    for (auto& kv : by) {
+        const std::vector<int>& f = kv.second;
+        std::vector<void*> ptrs(2 * f.size());
+        for (size_t j = 0; j < f.size(); ++j) {
+            ptrs[j] = const_cast<void*>(b->u_hat[f[j]]);
+            ptrs[f.size() + j] = b->coeffs[f[j]];
+        }
+        void** dptr = reinterpret_cast<void**>(base + offs[2 * gi]);
+        cudaError_t e = cudaMemcpy(dptr, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        b->groups.push_back({f[0], (int)f.size(), dptr, base + offs[2 * gi + 1]});
+        ++gi;
+    }
+    return BSPLINE_OK;
+}
+
 int launch_queue(int order, int by, const batch_impl::Queue& q, int sms, cudaStream_t st) {
     using namespace batch_impl;
     switch (order) {
@@ -238,15 +283,16 @@ int capture(bspline_batch_s* b, int k) {
     if (use_queue) {
         if (!batch_impl::queue_brick_y_ok(order, by)) return BSPLINE_ERR_INVALID_ARG;
         if ((rc = build_queue(b, by, (unsigned)b->item_particles))) return rc;
+        if ((rc = build_groups(b))) return rc;
     }
     int sms = 1;
     cudaError_t e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e0 != cudaSuccess) return set_cuda_error(e0);
     // workspaces are allocated now: no allocation may happen inside the capture
-    for (int i = 0; i < b->n; ++i) {
+    for (int i = 0; i < b->n && !use_queue; ++i) {
         bspline_plan_t p = b->plans[i];
         if ((rc = p->work.grow(coeffs_workspace_bytes(p)))) return rc;
-        if (!use_queue && (rc = p->pws.grow(interp_workspace_bytes(p, b->P[i])))) return rc;
+        if ((rc = p->pws.grow(interp_workspace_bytes(p, b->P[i])))) return rc;
     }
     std::vector<cudaStream_t> saved(b->n);
     std::vector<bool> timing(b->n);
@@ -261,11 +307,20 @@ int capture(bspline_batch_s* b, int k) {
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
     for (int s = 0; s < k && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->side[s], b->fork, 0);
     rc = set_cuda_error(e);
-    for (int i = 0; i < b->n && rc == BSPLINE_OK; ++i) {
+    if (use_queue) {
+        // one transform launch pair per group of equal grid size, the groups round-robin over the streams
+        unsigned* terr = reinterpret_cast<unsigned*>(b->q.status + kStatusTransformTimeout);
+        for (size_t g = 0; g < b->groups.size() && rc == BSPLINE_OK; ++g) {
+            const auto& G = b->groups[g];
+            rc = launch_coeffs_fields(b->plans[G.plan], G.nfields, G.ptrs, G.ptrs + G.nfields, G.work, terr,
+                                      b->side[g % (size_t)k]);
+        }
+    }
+    for (int i = 0; i < b->n && rc == BSPLINE_OK && !use_queue; ++i) {
         bspline_plan_t p = b->plans[i];
         p->stream = b->side[lane[p] % k];
         rc = bspline_coeffs(p, b->u_hat[i], b->coeffs[i]);
-        if (rc == BSPLINE_OK && !use_queue)
+        if (rc == BSPLINE_OK)
             rc = bspline_interp(p, b->coeffs[i], b->x[i], b->P[i], b->out_u[i], b->out_grad[i],
                                 b->out_grad[i] ? 0 : BSPLINE_INTERP_NO_GRAD);
     }
@@ -373,9 +428,17 @@ int bspline_batch_create(bspline_batch_t* out, int nfields, const bspline_plan_t
 int bspline_batch_capture(bspline_batch_t b, int streams, const void* const* u_hat, void* const* coeffs,
                           const double* const* x, const int64_t* P, void* const* out_u, void* const* out_grad) {
     if (!b || streams < 1 || !u_hat || !coeffs || !x || !P || !out_u) return BSPLINE_ERR_INVALID_ARG;
-    for (int i = 0; i < b->n; ++i)
+    for (int i = 0; i < b->n; ++i) {
         if (P[i] < 0 || P[i] > 0x7fffffffLL || !u_hat[i] || !coeffs[i] || (P[i] > 0 && (!x[i] || !out_u[i])))
             return BSPLINE_ERR_INVALID_ARG;
+        // the checks of bspline_coeffs: 16-byte aligned, coefficients not overlapping the spectrum
+        size_t cb = 0, ub = 0;
+        bspline_coeffs_bytes(b->plans[i], &cb);
+        bspline_uhat_bytes(b->plans[i], &ub);
+        const char* a = static_cast<const char*>(u_hat[i]);
+        const char* c = static_cast<const char*>(coeffs[i]);
+        if ((uintptr_t)a % 16 || (uintptr_t)c % 16 || (a < c + cb && c < a + ub)) return BSPLINE_ERR_INVALID_ARG;
+    }
     Guard g(b->device);
     if (!g.ok) return BSPLINE_ERR_CUDA;
     b->u_hat.assign(u_hat, u_hat + b->n);
@@ -537,7 +600,7 @@ int bspline_batch_status(bspline_batch_t b, int64_t* nonfinite) {
     if (e == cudaSuccess) e = cudaMemcpy(h, b->q.status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_cuda_error(e);
     if (nonfinite) *nonfinite = (int64_t)h[kStatusNonfinite];
-    if (h[kStatusParticleTimeout]) return BSPLINE_ERR_TIMEOUT;
+    if (h[kStatusParticleTimeout] || h[kStatusTransformTimeout]) return BSPLINE_ERR_TIMEOUT;
     if (h[kStatusBounds]) return BSPLINE_ERR_BOUNDS;
     return h[kStatusNonfinite] ? BSPLINE_ERR_NONFINITE_INPUT : BSPLINE_OK;
 }
@@ -547,6 +610,7 @@ int bspline_batch_destroy(bspline_batch_t b) {
     Guard g(b->device);
     drop_graph(b);
     b->qbuf.release();
+    b->tbuf.release();
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);

@@ -33,10 +33,14 @@ using namespace fftc;
 // ---------------------------------------------------------------- pass X
 // Lines along kx (input stride N*H complex); batch index b = ky*H + kz is
 // contiguous in the input.  Output: [3][N(x)][N(ky)][HP] with kz fastest.
+// Several fields of one grid size in one launch (batches): in_fields[f] is
+// field f's half spectrum, its x-transformed spectrum goes to out + f 3 N N HP,
+// and the grid holds 3 * tiles CTAs per field.  in_fields = nullptr: one field.
 template <typename R, int N, int NL>
 __global__ void __launch_bounds__(threads_for<N, NL>())
 fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __restrict__ out,
-                const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw, int comp0) {
+                const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw, int comp0,
+                const typename Cx<R>::T* const* __restrict__ in_fields) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     static_assert(T % NL == 0, "each thread stays on one line");
@@ -47,8 +51,16 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
     V* tws = reinterpret_cast<V*>(smem_raw);
     V* s = tws + N;
     const int t = threadIdx.x;
-    const int comp = comp0 + (int)(blockIdx.x / TILES);
-    const long long b0 = (blockIdx.x % TILES) * NL;
+    unsigned bx = blockIdx.x;
+    if (in_fields) {
+        constexpr unsigned per = 3u * (unsigned)TILES;
+        const unsigned f = bx / per;
+        bx -= f * per;
+        in = in_fields[f];
+        out += (long long)f * 3 * N * N * HP;
+    }
+    const int comp = comp0 + (int)(bx / TILES);
+    const long long b0 = (bx % TILES) * NL;
     const int valid = (int)std::min<long long>(NL, NH - b0);
     for (int m = t; m < N; m += T) tws[m] = tw[m];
     // this thread's line: batch index b0 + bl = ky H + kz; prefilter c(ky) c(kz) of the line
@@ -92,8 +104,9 @@ template <> __device__ __forceinline__ void store_pair<__nv_bfloat16, float2>(__
 // ---------------------------------------------------------------- passes Y + Z fused
 // One persistent kernel does the ky transform and the kz c2r of every
 // (component, x) plane, handing each plane from one to the other through a
-// ring of plane buffers small enough to stay in L2 (at most kRingMax x N x HP
-// complex), so the intermediate spectrum never makes a round trip through HBM.  Work items are taken in order from a global
+// ring of plane buffers small enough to stay in L2 (kRingMax planes, or up
+// to 32 MB of them for small planes: fields_ring_slots), so the intermediate
+// spectrum never makes a round trip through HBM.  Work items are taken in order from a global
 // counter: per plane, ceil(H / NL) "Y" items (NL kz columns, all ky) then
 // N / NR "Z" items (NR rows y, all kz).  A Z item waits until all Y items of
 // its plane have been stored; a Y item waits until the Z items that last used
@@ -220,7 +233,7 @@ template <typename R, typename OutT, int N, int NL, int NLY>
 __global__ void __launch_bounds__(threads_for<N, NL>(), yz_min_blocks<R, N, NL>())
 fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
              const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int lag, int ring_slots,
-             int drop_signals, long long plane0, long long planes) {
+             int drop_signals, long long plane0, long long planes, OutT* const* __restrict__ out_fields) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
@@ -345,7 +358,15 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
                 const V O = cmul(csub(a, bb), tws[k]);
                 return mk<V>(E.x - O.y, E.y + O.x);
             };
-            OutT* dst = out + (pl * N + y0) * (long long)N;
+            // planes of several fields (batches): field pl / 3N writes its own coefficients
+            OutT* ob = out;
+            long long lpl = pl;
+            if (out_fields) {
+                const long long f = pl / (3LL * N);
+                ob = out_fields[f];
+                lpl = pl - f * 3LL * N;
+            }
+            OutT* dst = ob + (lpl * N + y0) * (long long)N;
             auto st = [&](int m, int b, V z) { store_pair<OutT, V>(dst + (long long)b * N + 2 * m, z); };
             if constexpr (radix_for(M) == M) {
                 stage_single<V, M, NR, T>(ld, st);
@@ -359,10 +380,20 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
     }
 }
 
+// Ring slots of a transform over F fields of grid N: one launch keeps about 2 grid / (items per plane)
+// planes in flight, far more than kRingMax for small planes, so the ring grows up to 32 MB of planes
+// (L2-resident); at 512^3 FP32 it stays at kRingMax.
+template <typename V> long long fields_ring_slots(int N, int F) {
+    const long long plane = (long long)sizeof(V) * N * row_pitch(N);
+    const long long fit = (32LL << 20) / plane;
+    return std::max<long long>(kRingMax, std::min<long long>(3LL * N * F, fit));
+}
+
 // Workspace of the transform: the x-transformed spectrum, the plane ring and the counters.
 template <typename V> size_t transform_workspace(int N) {
     const size_t HP = row_pitch(N);
-    return sizeof(V) * (3ull * N * N * HP + (size_t)kRingMax * N * HP) + sizeof(unsigned) * (1 + 6ull * N);
+    return sizeof(V) * (3ull * N * N * HP + (size_t)fields_ring_slots<V>(N, 1) * N * HP) +
+           sizeof(unsigned) * (1 + 6ull * N);
 }
 
 // Y-item columns in units of tile_lines.
@@ -395,7 +426,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) 
         const long long tiles = ((long long)N * H + NLX - 1) / NLX;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);
         k<<<(unsigned)((c1 - c0) * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c,
-                                                                             tw, c0);
+                                                                             tw, c0, nullptr);
     }
     {
         auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
@@ -411,20 +442,94 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) 
         const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
         // planes in progress at once ~ 2 grid / items-per-plane (each CTA runs one item and has claimed
         // the next); consumers trail by that plus a margin
-        const int lag = (int)std::min<long long>(std::min<long long>(kRingMax / 2, planes),
+        const long long slots = fields_ring_slots<V>(N, 1);
+        const int lag = (int)std::min<long long>(std::min<long long>(slots / 2, planes),
                                                  (2 * grid + ipp - 1) / ipp + 2);
         const int ring_slots = 2 * lag;
         V* ring = w + 3LL * N * N * HP;
-        unsigned* ctr = reinterpret_cast<unsigned*>(ring + (long long)kRingMax * N * HP);
+        unsigned* ctr = reinterpret_cast<unsigned*>(ring + slots * N * HP);
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 2 * planes), st);
         if (e != cudaSuccess) return set_cuda_error(e);
         StageTimer tm(p, BSPLINE_STAGE_FFT_YZ);
         k<<<(unsigned)grid, T, sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), ring, tw, ctr,
                                          reinterpret_cast<unsigned*>(p->d_status + kStatusTransformTimeout), lag, ring_slots,
                                          (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0,
-                                         (long long)c0 * N, planes);
+                                         (long long)c0 * N, planes, nullptr);
     }
     return set_cuda_error(cudaGetLastError());
+}
+
+// F fields of one grid size, order and prefilter (the tables of p) in one launch of each kernel:
+// in_fields / out_fields are device arrays of F pointers; w is the group's workspace
+// (fields_workspace<V>(N, F) bytes); a wait that runs out sets *error.
+template <typename V> size_t fields_workspace(int N, int F) {
+    const size_t HP = row_pitch(N);
+    return sizeof(V) * (3ull * N * N * HP * (size_t)F + (size_t)fields_ring_slots<V>(N, F) * N * HP) +
+           sizeof(unsigned) * (1 + 6ull * N * (size_t)F);
+}
+
+template <typename R, typename OutT, int N>
+int run_fft_fields(const bspline_plan_s* p, int F, const void* const* in_fields, void* const* out_fields, void* work,
+                   unsigned* error, cudaStream_t st) {
+    using V = typename Cx<R>::T;
+    constexpr int NL = tile_lines<R>();
+    constexpr int T = threads_for<N, NL>();
+    constexpr int H = N / 2 + 1, HP = row_pitch(N);
+    const R* c = nullptr;
+    const V* tw = nullptr;
+    if constexpr (sizeof(R) == 8) {
+        c = p->d_c64;
+        tw = p->d_tw64;
+    } else {
+        c = p->d_c32;
+        tw = p->d_tw32;
+    }
+    V* w = reinterpret_cast<V*>(work);
+    int rc;
+    {
+        constexpr int NLX = 2 * NL;
+        auto k = fft_x_prefilter<R, N, NLX>;
+        const size_t sm = sizeof(V) * (N + (size_t)N * NLX);
+        if ((rc = set_smem(k, sm))) return rc;
+        const long long tiles = ((long long)N * H + NLX - 1) / NLX;
+        k<<<(unsigned)(3LL * F * tiles), threads_for<N, NLX>(), sm, st>>>(
+            nullptr, w, c, tw, 0, reinterpret_cast<const V* const*>(in_fields));
+    }
+    {
+        auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
+        constexpr int NR = z_rows<R, N, NL>();
+        const size_t sm = sizeof(V) * yz_smem_elems<R, N, NL, kYCols * NL>();
+        if ((rc = set_smem(k, sm))) return rc;
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T, sm);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        const int ipp = (H + kYCols * NL - 1) / (kYCols * NL) + N / NR;
+        const long long planes = 3LL * N * F;
+        const long long items = planes * ipp;
+        const long long grid = std::min<long long>(items, (long long)std::max(per_sm, 1) * p->sms);
+        const long long slots = fields_ring_slots<V>(N, F);
+        const int lag = (int)std::min<long long>(std::min<long long>(slots / 2, planes),
+                                                 (2 * grid + ipp - 1) / ipp + 2);
+        V* ring = w + 3LL * N * N * HP * F;
+        unsigned* ctr = reinterpret_cast<unsigned*>(ring + slots * N * HP);
+        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 2 * planes), st);
+        if (e != cudaSuccess) return set_cuda_error(e);
+        k<<<(unsigned)grid, T, sm, st>>>(w, nullptr, ring, tw, ctr, error, lag, 2 * lag, 0, 0LL, planes,
+                                         reinterpret_cast<OutT* const*>(out_fields));
+    }
+    return set_cuda_error(cudaGetLastError());
+}
+
+template <int N>
+int run_n_fields(const bspline_plan_s* p, int F, const void* const* in_fields, void* const* out_fields, void* work,
+                 unsigned* error, cudaStream_t st) {
+    switch (p->dtype) {
+        case BSPLINE_F64: return run_fft_fields<double, double, N>(p, F, in_fields, out_fields, work, error, st);
+        case BSPLINE_F32: return run_fft_fields<float, float, N>(p, F, in_fields, out_fields, work, error, st);
+        case BSPLINE_BF16:
+            return run_fft_fields<float, __nv_bfloat16, N>(p, F, in_fields, out_fields, work, error, st);
+    }
+    return BSPLINE_ERR_INVALID_ARG;
 }
 
 template <int N> int run_n(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) {
@@ -468,5 +573,29 @@ int launch_coeffs_range(bspline_plan_s* p, const void* u_hat, void* coeffs, int 
 }
 
 int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs) { return launch_coeffs_range(p, u_hat, coeffs, 0, 3); }
+
+size_t coeffs_fields_workspace_bytes(const bspline_plan_s* p, int F) {
+    return p->dtype == BSPLINE_F64 ? fields_workspace<double2>(p->N, F) : fields_workspace<float2>(p->N, F);
+}
+
+int launch_coeffs_fields(const bspline_plan_s* p, int F, const void* const* in_fields, void* const* out_fields,
+                         void* work, unsigned* error, cudaStream_t st) {
+    switch (p->N) {
+        case 8: return run_n_fields<8>(p, F, in_fields, out_fields, work, error, st);
+        case 16: return run_n_fields<16>(p, F, in_fields, out_fields, work, error, st);
+        case 32: return run_n_fields<32>(p, F, in_fields, out_fields, work, error, st);
+        case 64: return run_n_fields<64>(p, F, in_fields, out_fields, work, error, st);
+        case 128: return run_n_fields<128>(p, F, in_fields, out_fields, work, error, st);
+        case 256: return run_n_fields<256>(p, F, in_fields, out_fields, work, error, st);
+        case 512: return run_n_fields<512>(p, F, in_fields, out_fields, work, error, st);
+        case 1024: return run_n_fields<1024>(p, F, in_fields, out_fields, work, error, st);
+        case 48: return run_n_fields<48>(p, F, in_fields, out_fields, work, error, st);
+        case 96: return run_n_fields<96>(p, F, in_fields, out_fields, work, error, st);
+        case 192: return run_n_fields<192>(p, F, in_fields, out_fields, work, error, st);
+        case 384: return run_n_fields<384>(p, F, in_fields, out_fields, work, error, st);
+        case 768: return run_n_fields<768>(p, F, in_fields, out_fields, work, error, st);
+    }
+    return BSPLINE_ERR_UNSUPPORTED_N;
+}
 
 }  // namespace bs

@@ -150,6 +150,13 @@ int launch_coeffs(bspline_plan_s* p, const void* u_hat, void* coeffs);
 // Transform of components c0..c1-1 only (launch_coeffs = 0..3).
 int launch_coeffs_range(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1);
 
+// Transform of F fields with p's grid size, order, dtype and prefilter, one launch per kernel:
+// in_fields / out_fields are device arrays of F u_hat / coefficient pointers, work holds
+// coeffs_fields_workspace_bytes(p, F) bytes; a wait that runs out sets *error.
+size_t coeffs_fields_workspace_bytes(const bspline_plan_s* p, int F);
+int launch_coeffs_fields(const bspline_plan_s* p, int F, const void* const* in_fields, void* const* out_fields,
+                         void* work, unsigned* error, cudaStream_t st);
+
 // Particles: bin, sort and evaluate u and grad u.
 size_t interp_workspace_bytes(const bspline_plan_s* p, int64_t P);
 int launch_interp(bspline_plan_s* p, const void* coeffs, const double* x, int64_t P, void* out_u,
