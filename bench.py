@@ -345,7 +345,11 @@ def run_ours(args):
     traffic = measured_traffic(dom, hd, N, order)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic, "algorithmic_bytes": abytes, "avg_launch_ms": dom_ms}
+                "traffic": traffic, "algorithmic_bytes": abytes, "avg_launch_ms": dom_ms,
+                "traffic_source": ("profiles/traffic.txt: DRAM bytes of one launch of this kernel on this workload "
+                                   "from a one-pass ncu capture, taken on the same kernel source (hash "
+                                   f"{kernel_source_sha(dom)}); not measured in this run" if traffic is not None
+                                   else "none for the current kernel source")}
     # the gather's arithmetic: Table 1 multiply-adds per particle against the FP32 FMA pipe
     from_table1 = 6 * order ** 3 + 15 * order ** 2 + 12 * order
     g_ms = stages["gather"][0] / max(stages["gather"][1], 1)
