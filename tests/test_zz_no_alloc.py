@@ -74,6 +74,32 @@ def test_noalloc_matches_plan_path_on_consecutive_calls(B):
         plan.close()
 
 
+def test_noalloc_call_changes_no_device_allocation(B):
+    """After a first call (which loads the library's kernels and its fixed array), a call leaves the
+    device's free memory and torch's allocated bytes exactly as they were."""
+    N, order = 32, 4
+    x = torch.from_numpy(synth.uniform_particles(20000, seed=12)).cuda()
+    plan, coef, u_ref, g_ref = plan_path(B, N, order, "f32", 2.0 * math.pi, x, 35)
+    u = torch.empty_like(u_ref)
+    g = torch.empty_like(g_ref)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        rc = B.bspline_interp_noalloc(coef.data_ptr(), N, order, B.F32, 2.0 * math.pi, x.data_ptr(), x.shape[0],
+                                      u.data_ptr(), g.data_ptr(), 0, stream)
+        assert rc == B.OK
+        torch.cuda.synchronize()
+
+    call()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    assert normwise(u, u_ref) <= TOL["f32"][0] and normwise(g, g_ref) <= TOL["f32"][1]
+    plan.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(B):
     buf = torch.zeros(1 << 12, dtype=torch.float64, device="cuda")
     p = buf.data_ptr()
