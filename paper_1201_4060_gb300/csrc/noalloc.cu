@@ -87,7 +87,7 @@ extern "C" int bspline_interp_noalloc(const void* coeffs, int N, int order, bspl
     int rc = scratch_for_device(dev, &base);
     if (rc == BSPLINE_OK) {
         auto* status = reinterpret_cast<unsigned long long*>(base);
-        p.d_status = status;                       // words 0-1 are cleared by every call (non-finite, tile wait)
+        p.d_status = status;                       // words 0-2 are cleared by every call (non-finite, tile wait, bounds)
         void* ws = static_cast<unsigned char*>(base) + kStatusBytes;
         rc = bs::launch_interp_ws(&p, ws, status, coeffs, x, P, out_u, out_grad, flags);
     }
