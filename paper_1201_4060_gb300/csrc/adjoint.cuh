@@ -421,7 +421,7 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
     const unsigned NB = bg.NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
-    A* tile = reinterpret_cast<A*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    A* tile = reinterpret_cast<A*>(smem_raw + ((0u - smem_u32(smem_raw)) & 127u));   // 128-byte aligned
     __shared__ __align__(8) unsigned long long s_mbar;
     unsigned brick, beg, end;
     if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;

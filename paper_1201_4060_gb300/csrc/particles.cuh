@@ -955,8 +955,10 @@ __device__ __forceinline__ void gather_f32_item(unsigned item, unsigned chunk_le
     using S = Shape<CT, ORD, BYO>;
     constexpr int NW = kGatherThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack)
-    float* tile = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // the tile 128-byte aligned (TMA destinations; the launch adds 128 bytes of slack), offset from the
+    // shared array itself so that its loads stay shared-memory loads (an address rebuilt from an integer
+    // would be a generic one)
+    float* tile = reinterpret_cast<float*>(smem_raw + ((0u - smem_u32(smem_raw)) & 127u));
     __shared__ unsigned s_bucket[32];
     __shared__ unsigned short s_order[kChunk];
     __shared__ __align__(8) unsigned long long s_mbar;
