@@ -476,9 +476,13 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
     }
     __syncthreads();
     const A s2 = dscale * dscale;
+    // a thread's next record is requested while its current particle is evaluated
+    auto record = [&](unsigned q) { return w.s_rec[beg + (kBucket ? (unsigned)s_order[q] : q)]; };
+    Rec<TR> rc_next;
+    if (threadIdx.x < n) rc_next = record(threadIdx.x);
     for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
-        const unsigned i = beg + (kBucket ? (unsigned)s_order[q] : q);
-        const Rec<TR> rc = w.s_rec[i];
+        const Rec<TR> rc = rc_next;
+        if (q + kAdjThreads < n) rc_next = record(q + kAdjThreads);
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
@@ -487,6 +491,14 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
                              (long long)idx < w.P,
                          status + kStatusBounds))
             continue;
+        // the particle's cotangents, requested before the contractions that they multiply
+        A gu[3], gg[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gu[c] = g_u ? g_u[3 * idx + c] : A(0);
+        if (HESS) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) gg[e] = g_grad[9 * idx + e];
+        }
         A wx[ORD], dwx[ORD], d2wx[ORD], wy[ORD], dwy[ORD], d2wy[ORD], wz[ORD], dwz[ORD], d2wz[ORD];
         bspline_weights2<ORD, A>((A)rc.t[0], wx, dwx, d2wx);
         bspline_weights2<ORD, A>((A)rc.t[1], wy, dwy, d2wy);
@@ -533,14 +545,15 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
                     t011 = fma(wx[jx], y11, t011);
                 }
             }
-            const A gu = g_u ? g_u[3 * idx + c] * dscale : A(0);
-            gx = fma(gu, t100, gx);
-            gy = fma(gu, t010, gy);
-            gz = fma(gu, t001, gz);
+            // this component's cotangents (selects: c is a rolled loop counter)
+            const A guc = (c == 0 ? gu[0] : (c == 1 ? gu[1] : gu[2])) * dscale;
+            gx = fma(guc, t100, gx);
+            gy = fma(guc, t010, gy);
+            gz = fma(guc, t001, gz);
             if (HESS) {
-                const A g0 = g_grad[9 * idx + 3 * c + 0] * s2;
-                const A g1 = g_grad[9 * idx + 3 * c + 1] * s2;
-                const A g2 = g_grad[9 * idx + 3 * c + 2] * s2;
+                const A g0 = (c == 0 ? gg[0] : (c == 1 ? gg[3] : gg[6])) * s2;
+                const A g1 = (c == 0 ? gg[1] : (c == 1 ? gg[4] : gg[7])) * s2;
+                const A g2 = (c == 0 ? gg[2] : (c == 1 ? gg[5] : gg[8])) * s2;
                 gx += g0 * t200 + g1 * t110 + g2 * t101;
                 gy += g0 * t110 + g1 * t020 + g2 * t011;
                 gz += g0 * t101 + g1 * t011 + g2 * t002;
