@@ -189,9 +189,13 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
         }
         __syncthreads();
     }
+    // a thread's next record is requested while its current particle is spread
+    auto record = [&](unsigned q) { return w.s_rec[beg + (kBucket ? (unsigned)s_order[q] : q)]; };
+    Rec<TR> rc_next;
+    if (threadIdx.x < n) rc_next = record(threadIdx.x);
     for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
-        const unsigned i = beg + (kBucket ? (unsigned)s_order[q] : q);
-        const Rec<TR> rc = w.s_rec[i];
+        const Rec<TR> rc = rc_next;
+        if (q + kAdjThreads < n) rc_next = record(q + kAdjThreads);
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
@@ -200,6 +204,15 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
                              (long long)idx < w.P,
                          status + kStatusBounds))
             continue;
+        // the particle's cotangents, all requested before the shared-memory reductions (loads cannot move
+        // across them)
+        A cu[3], cg[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cu[c] = g_u ? g_u[3 * idx + c] : A(0);
+        if (GRAD) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) cg[e] = g_grad[9 * idx + e];
+        }
         A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
         bspline_weights<ORD, A>((A)rc.t[0], wx, dwx);
         bspline_weights<ORD, A>((A)rc.t[1], wy, dwy);
@@ -207,12 +220,12 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A*
         A* base = acc + (ox * EY + oy) * EZ + oz;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const A gu = g_u ? g_u[3 * idx + c] : A(0);
+            const A gu = cu[c];
             A g0 = A(0), g1 = A(0), g2 = A(0);
             if (GRAD) {
-                g0 = g_grad[9 * idx + 3 * c + 0] * dscale;
-                g1 = g_grad[9 * idx + 3 * c + 1] * dscale;
-                g2 = g_grad[9 * idx + 3 * c + 2] * dscale;
+                g0 = cg[3 * c + 0] * dscale;
+                g1 = cg[3 * c + 1] * dscale;
+                g2 = cg[3 * c + 2] * dscale;
             }
             A* tc = base + c * E3;
 #pragma unroll
@@ -343,8 +356,11 @@ spread_det_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, 
     __shared__ unsigned short s_order[kChunk];
     for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) acc[e] = 0;
     bank_order<EY, EZ, kAdjThreads>(w, beg, n, x0, y0, z0, s_bucket, s_order);   // ends with a barrier
+    Rec<TR> rc_next;                                    // the thread's next record, requested ahead
+    if (threadIdx.x < n) rc_next = w.s_rec[beg + s_order[threadIdx.x]];
     for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
-        const Rec<TR> rc = w.s_rec[beg + s_order[q]];
+        const Rec<TR> rc = rc_next;
+        if (q + kAdjThreads < n) rc_next = w.s_rec[beg + s_order[q + kAdjThreads]];
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
@@ -353,6 +369,14 @@ spread_det_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, 
                              (long long)idx < w.P,
                          status + kStatusBounds))
             continue;
+        // the particle's cotangents, all requested before the reductions (loads cannot move across them)
+        float cu[3], cg[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cu[c] = g_u ? g_u[3 * idx + c] : 0.f;
+        if (GRAD) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) cg[e] = g_grad[9 * idx + e];
+        }
         float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
         bspline_weights<ORD, float>(rc.t[0], wx, dwx);
         bspline_weights<ORD, float>(rc.t[1], wy, dwy);
@@ -360,12 +384,13 @@ spread_det_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, 
         long long* base = acc + (ox * EY + oy) * EZ + oz;
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
-            const float gu = g_u ? g_u[3 * idx + c] : 0.f;
+            // this component's cotangents (selects: c is a rolled loop counter)
+            const float gu = c == 0 ? cu[0] : (c == 1 ? cu[1] : cu[2]);
             float g0 = 0.f, g1 = 0.f, g2 = 0.f;
             if (GRAD) {
-                g0 = g_grad[9 * idx + 3 * c + 0] * dscale;
-                g1 = g_grad[9 * idx + 3 * c + 1] * dscale;
-                g2 = g_grad[9 * idx + 3 * c + 2] * dscale;
+                g0 = (c == 0 ? cg[0] : (c == 1 ? cg[3] : cg[6])) * dscale;
+                g1 = (c == 0 ? cg[1] : (c == 1 ? cg[4] : cg[7])) * dscale;
+                g2 = (c == 0 ? cg[2] : (c == 1 ? cg[5] : cg[8])) * dscale;
             }
             long long* tc = base + c * E3;
 #pragma unroll
