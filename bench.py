@@ -223,11 +223,14 @@ def dense_field_on_gpu(F, dtype_torch, device):
     return uh
 
 
-def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True, sample=None):
-    """Time `steps` whole-path steps with one plan of coefficient type dtype; returns (ms/step, stage dict,
-    non-finite count, outputs at the sampled particle indices (host FP64 arrays) or None)."""
+def run_form(B, wl, F, x, dtype, steps, warmup, device, timed_stages=True, sample=None, band=0):
+    """Time `steps` whole-path steps with one plan of coefficient type dtype (band > 0: the plan is told
+    that modes beyond |k_i| <= band are zero); returns (ms/step, stage dict, non-finite count, outputs at
+    the sampled particle indices (host FP64 arrays) or None)."""
     import torch
     plan = B.Plan(wl["N"], wl["order"], dtype)
+    if band:
+        plan.set_band(band)
     uh = dense_field_on_gpu(F, plan.uhat_dtype, device)
     coef = plan.empty_coeffs()
     P = x.shape[0]
@@ -409,6 +412,7 @@ def run_ours(args):
             forms["f32"]["e_prec_below_e_trunc"] = errs["e_prec_below_e_trunc"]
         out["forms"] = forms
         out["e2e"] = run_e2e(B, wl, F, xs, device, steps=24)
+        out["band"] = run_band(B, wl, F, x, xs, device, ks, sample_t, sampled["f32"])
         orders, o_sampled, o_idx = run_orders(B, device)
         if not args.no_cpu_baseline:
             oe = orders_errors(o_sampled, o_idx)
@@ -749,7 +753,25 @@ def run_batch(B, device, steps=10, warmup=3):
     return out
 
 
-def run_e2e(B, wl, F, xs, device, steps):
+def run_band(B, wl, F, x, xs, device, steps, sample_t, full_sampled):
+    """The same workload on plans told that the field is band-limited (bspline_plan_set_band with the
+    generator's |k| <= N/3, the 2/3-rule dealiasing of pseudo-spectral codes): the transform skips the
+    zero modes and bspline_run_host copies only the band box.  The outputs must be the full path's bits;
+    reported beside the headline, which takes every mode of the spectrum."""
+    import numpy as np
+    N, P = wl["N"], wl["P"]
+    K = N // 3
+    ms, st, _, samp = run_form(B, wl, F, x, "f32", steps, 2, device, sample=sample_t, band=K)
+    same = bool(np.array_equal(samp[0], full_sampled[0]) and np.array_equal(samp[1], full_sampled[1]))
+    return {"kmax": K, "input": f"modes with |kx|, |ky|, kz <= {K} (the field generator's band, |k| <= N/3)",
+            "particles_per_s": P / (ms / 1e3), "ms_per_step": ms,
+            "fft_x_ms": st["fft_x"][0] / max(st["fft_x"][1], 1), "fft_yz_ms": st["fft_yz"][0] / max(st["fft_yz"][1], 1),
+            "gather_ms": st["gather"][0] / max(st["gather"][1], 1),
+            "sampled_outputs_equal_full_path": same,
+            "e2e": run_e2e(B, wl, F, xs, device, steps=24, band=K)}
+
+
+def run_e2e(B, wl, F, xs, device, steps, band=0):
     """Same metric through the host-buffer API: every step copies u_hat and the positions from pinned
     host memory to the device and u and grad u back, all inside the timed region.  Steps alternate
     between two plans on two streams (bspline_run_host_async, then bspline_wait before a plan is
@@ -761,6 +783,9 @@ def run_e2e(B, wl, F, xs, device, steps):
     import torch
     N, order, P = wl["N"], wl["order"], wl["P"]
     plans = [B.Plan(N, order, "f32") for _ in range(2)]
+    for p in plans:
+        if band:
+            p.set_band(band)                             # only the band box of u_hat crosses the host link
     streams = [torch.cuda.Stream(device) for _ in range(2)]
     uh = torch.from_numpy(F.dense(np.complex64)).pin_memory()
     xh = torch.from_numpy(xs).pin_memory()
@@ -786,7 +811,7 @@ def run_e2e(B, wl, F, xs, device, steps):
     t = statistics.median(seqs)
     for p in plans:
         p.close()
-    h2d = uh.numel() * 8 + xh.numel() * 8
+    h2d = (3 * (2 * band + 1) ** 2 * (band + 1) if band else uh.numel()) * 8 + xh.numel() * 8
     d2h = outs[0][0].numel() * 4 + outs[0][1].numel() * 4
     del uh, xh, outs
     torch.cuda.empty_cache()

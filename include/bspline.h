@@ -104,6 +104,20 @@ int bspline_plan_set_length(bspline_plan_t plan, double L);
 /* Prefilter choice (default BSPLINE_PREFILTER_INTERP). */
 int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind);
 
+/* Band-limited input (no counterpart in the paper, which transforms the full
+ * spectrum; pseudo-spectral fields are dealiased, e.g. by the 2/3 rule, and
+ * hold no mode beyond a known wavenumber).  kmax > 0 declares that every mode
+ * of u_hat with |kx| > kmax, |ky| > kmax or kz > kmax (signed wavenumbers,
+ * kz >= 0 in the half spectrum) is zero: bspline_coeffs, bspline_eval and
+ * bspline_run_host then neither read those modes nor transform the lines that
+ * hold nothing else, and bspline_run_host copies only the box |kx|, |ky|, kz <=
+ * kmax from the host.  The coefficients are bit for bit those of the full
+ * transform of u_hat with those modes zero (whatever u_hat holds there).
+ * kmax = 0 (the default) turns it off.  Errors: INVALID_ARG for kmax < 0 or
+ * 2 kmax >= N (the band must leave out the Nyquist planes).  The adjoint
+ * transform of bspline_spread_adjoint always produces the full spectrum. */
+int bspline_plan_set_band(bspline_plan_t plan, int kmax);
+
 /* The prefilter c(k) that a plan of this N, order and kind applies along each
  * axis (Section 7: Eq. B_spline_multiplication for INTERP, Eq. B_spline_coeff
  * for L2), computed on the host in FP64 exactly as bspline_plan computes it.

@@ -59,6 +59,7 @@ def _load() -> ctypes.CDLL:
         "bspline_plan": (i32, [ctypes.POINTER(vp), i32, i32, i32]),
         "bspline_plan_set_length": (i32, [vp, ctypes.c_double]),
         "bspline_plan_set_prefilter": (i32, [vp, i32]),
+        "bspline_plan_set_band": (i32, [vp, i32]),
         "bspline_prefilter_values": (i32, [i32, i32, i32, ctypes.POINTER(ctypes.c_double)]),
         "bspline_plan_set_stream": (i32, [vp, vp]),
         "bspline_coeffs_bytes": (i32, [vp, ctypes.POINTER(sz)]),
@@ -435,6 +436,10 @@ class Plan:
         (bspline_plan_set_deterministic)."""
         _check(_load().bspline_plan_set_deterministic(self.handle, 1 if enable else 0),
                "bspline_plan_set_deterministic")
+
+    def set_band(self, kmax: int) -> None:
+        """Modes with |kx|, |ky| or kz beyond kmax are zero (bspline_plan_set_band; 0 = off)."""
+        _check(_load().bspline_plan_set_band(self.handle, int(kmax)), "bspline_plan_set_band")
 
     def set_gather_split(self, direct_below: int) -> None:
         """Bricks with fewer particles than this use the direct gather (bspline_plan_set_gather_split)."""

@@ -338,6 +338,13 @@ int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind) {
     return upload_prefilter(plan);
 }
 
+int bspline_plan_set_band(bspline_plan_t plan, int kmax) {
+    if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
+    if (kmax < 0 || (kmax > 0 && 2 * kmax >= plan->N)) return BSPLINE_ERR_INVALID_ARG;
+    plan->band = kmax;
+    return BSPLINE_OK;
+}
+
 int bspline_plan_set_stream(bspline_plan_t plan, void* stream) {
     if (!valid_plan(plan)) return BSPLINE_ERR_INVALID_ARG;
     plan->stream = (cudaStream_t)stream;
@@ -573,6 +580,30 @@ int bspline_plan_set_test_hooks(bspline_plan_t plan, int hooks) {
 // each component as soon as it has arrived; the gather waits for the sort
 // and the last component, then the results are copied back on the plan's
 // stream.  Returns once all of it is queued.
+// With a band (bspline_plan_set_band) only the box |kx|, |ky|, kz <= band of each
+// component crosses the host link: four pitched 3D copies (kx and ky each in
+// [0, band] and [N - band, N)), rows of band + 1 modes; the transform reads
+// nothing else.
+static cudaError_t copy_band_h2d(const bspline_plan_s* p, void* dst, const void* src, int comp, size_t elem,
+                                 cudaStream_t s) {
+    const int N = p->N, H = N / 2 + 1, K = p->band;
+    const int first[2] = {0, N - K}, count[2] = {K + 1, K};
+    for (int a = 0; a < 2; ++a) {                       // kx range
+        for (int b = 0; b < 2; ++b) {                   // ky range
+            cudaMemcpy3DParms m = {};
+            m.srcPtr = make_cudaPitchedPtr(const_cast<void*>(src), H * elem, H * elem, (size_t)N);
+            m.dstPtr = make_cudaPitchedPtr(dst, H * elem, H * elem, (size_t)N);
+            m.srcPos = make_cudaPos(0, (size_t)first[b], (size_t)comp * N + (size_t)first[a]);
+            m.dstPos = m.srcPos;
+            m.extent = make_cudaExtent((size_t)(K + 1) * elem, (size_t)count[b], (size_t)count[a]);
+            m.kind = cudaMemcpyHostToDevice;
+            const cudaError_t e = cudaMemcpy3DAsync(&m, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 int bspline_run_host_async(bspline_plan_t plan, const void* u_hat_host, const double* x_host, int64_t P,
                            void* u_host, void* grad_host) {
     if (!valid_plan(plan) || !u_hat_host || !u_host || (P > 0 && !x_host)) return BSPLINE_ERR_INVALID_ARG;
@@ -597,9 +628,11 @@ int bspline_run_host_async(bspline_plan_t plan, const void* u_hat_host, const do
         e = cudaMemcpyAsync(plan->host_x.ptr, x_host, sizeof(double) * 3 * P, cudaMemcpyHostToDevice, cp);
     if (e == cudaSuccess) e = cudaEventRecord(plan->ev_copied[0], cp);
     const size_t comp = uhat_bytes_of(plan) / 3;
+    const size_t elem = plan->dtype == BSPLINE_F64 ? 16 : 8;   // one complex mode
     for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-        e = cudaMemcpyAsync((char*)plan->host_uhat.ptr + c * comp, (const char*)u_hat_host + c * comp, comp,
-                            cudaMemcpyHostToDevice, cp);
+        if (plan->band) e = copy_band_h2d(plan, plan->host_uhat.ptr, u_hat_host, c, elem, cp);
+        else e = cudaMemcpyAsync((char*)plan->host_uhat.ptr + c * comp, (const char*)u_hat_host + c * comp, comp,
+                                 cudaMemcpyHostToDevice, cp);
         if (e == cudaSuccess) e = cudaEventRecord(plan->ev_copied[1 + c], cp);
     }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, plan->ev_copied[0], 0);

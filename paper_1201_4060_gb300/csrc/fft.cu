@@ -36,11 +36,14 @@ using namespace fftc;
 // Several fields of one grid size in one launch (batches): in_fields[f] is
 // field f's half spectrum, its x-transformed spectrum goes to out + f 3 N N HP,
 // and the grid holds 3 * tiles CTAs per field.  in_fields = nullptr: one field.
+// band > 0 (bspline_plan_set_band): modes with |kx|, |ky| or kz beyond band are
+// zero; they are not read, and the columns (ky, kz) outside the band are not
+// transformed or stored (the ky/kz pass never reads them).
 template <typename R, int N, int NL>
 __global__ void __launch_bounds__(threads_for<N, NL>())
 fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __restrict__ out,
                 const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw, int comp0,
-                const typename Cx<R>::T* const* __restrict__ in_fields) {
+                const typename Cx<R>::T* const* __restrict__ in_fields, int band) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     static_assert(T % NL == 0, "each thread stays on one line");
@@ -62,6 +65,16 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
     const int comp = comp0 + (int)(bx / TILES);
     const long long b0 = (bx % TILES) * NL;
     const int valid = (int)std::min<long long>(NL, NH - b0);
+    auto col_in_band = [&](int b) {                      // column b0 + b = ky H + kz inside the band
+        const long long bb = b0 + b;
+        const int ky = (int)(bb / H), kz = (int)(bb % H);
+        return kz <= band && (ky <= band || ky >= N - band);
+    };
+    if (band) {                                          // a tile with no column in the band has nothing to do
+        bool any = false;
+        for (int b = 0; b < valid; ++b) any = any || col_in_band(b);
+        if (!any) return;
+    }
     for (int m = t; m < N; m += T) tws[m] = tw[m];
     // this thread's line: batch index b0 + bl = ky H + kz; prefilter c(ky) c(kz) of the line
     const int bl = t % NL;
@@ -70,14 +83,16 @@ fft_x_prefilter(const typename Cx<R>::T* __restrict__ in, typename Cx<R>::T* __r
     const R cyz = (bl < valid) ? c[ky] * c[kz] : R(0);
     const V* src = in + (long long)comp * N * NH + b0;
     V* dst = out + (long long)comp * N * N * HP + (long long)ky * HP + kz;
+    // this thread's line (every thread stays on its column bl: the b below is always bl)
+    const bool col = bl < valid && (!band || col_in_band(bl));
     auto ld = [&](int q, int b) -> V {                   // prefilter c(kx) c(ky) c(kz) on load
-        if (b >= valid) return mk<V>(R(0), R(0));
+        if (!col || (band && q > band && q < N - band)) return mk<V>(R(0), R(0));
         const V a = src[(long long)q * NH + b];
         const R f = __ldg(&c[q]) * cyz;
         return mk<V>(a.x * f, a.y * f);
     };
     auto st = [&](int q, int b, V v) {
-        if (b < valid) dst[(long long)q * N * HP] = v;
+        if (col) dst[(long long)q * N * HP] = v;
     };
     if constexpr (radix_for(N) == N) {
         stage_single<V, N, NL, T>(ld, st);
@@ -233,7 +248,7 @@ template <typename R, typename OutT, int N, int NL, int NLY>
 __global__ void __launch_bounds__(threads_for<N, NL>(), yz_min_blocks<R, N, NL>())
 fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, typename Cx<R>::T* ring,
              const typename Cx<R>::T* __restrict__ tw, unsigned* ctr, unsigned* error, int lag, int ring_slots,
-             int drop_signals, long long plane0, long long planes, OutT* const* __restrict__ out_fields) {
+             int drop_signals, long long plane0, long long planes, OutT* const* __restrict__ out_fields, int band) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
@@ -309,14 +324,20 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
         item_to_plane<TPZ, ZPP>(item, planes, lag, &lp, &r);
         const long long pl = plane0 + lp;
         V* slot = ring + (lp % ring_slots) * (long long)N * HP;
-        if (r < TPZ) {
-            // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot
+        if (r < TPZ && band && r * NLY > band) {
+            // ---- Y item beyond the band: its columns are zero, and the Z items never read them
+            if (t == 0) prefetch_flag();
+            __syncthreads();
+            if (t == 0 && !drop_signals) signal_release(&done_y[lp]);
+        } else if (r < TPZ) {
+            // ---- Y item: columns kz0..kz0+NL-1, all ky; into the ring slot (rows ky beyond the band: zero)
             const int kz0 = r * NLY;
             const int valid = std::min(NLY, H - kz0);
             const V* src = w + pl * N * HP + kz0;
             V* dst = slot + kz0;
             auto ld = [&](int q, int b) -> V {
-                return (b < valid) ? __ldcs(&src[(long long)q * HP + b]) : mk<V>(R(0), R(0));
+                return (b < valid && (!band || q <= band || q >= N - band)) ? __ldcs(&src[(long long)q * HP + b])
+                                                                              : mk<V>(R(0), R(0));
             };
             auto st = [&](int q, int b, V v) {
                 if (b < valid) dst[(long long)q * HP + b] = v;
@@ -339,8 +360,10 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             const int y0 = (r - TPZ) * NR;
             const unsigned char* src = reinterpret_cast<const unsigned char*>(slot + (long long)y0 * HP);
             unsigned char* dstb = reinterpret_cast<unsigned char*>(raw);
-            for (int j = t; j < NR * CHUNKS; j += T) {
-                const int row = j / CHUNKS, k = j - row * CHUNKS;
+            // with a band only the row's first band + 1 modes are staged (the others are read as zero)
+            const int nch = band ? std::min(CHUNKS, ((band + 1) * (int)sizeof(V) + 15) / 16) : CHUNKS;
+            for (int j = t; j < NR * nch; j += T) {
+                const int row = j / nch, k = j - row * nch;
                 cp_async16_l2(dstb + (size_t)row * RP * sizeof(V) + 16 * k, src + (size_t)row * HP * sizeof(V) + 16 * k);
             }
             cp_async_wait_all();
@@ -351,7 +374,9 @@ fft_yz_fused(const typename Cx<R>::T* __restrict__ w, OutT* __restrict__ out, ty
             }
             auto ld = [&](int k, int b) -> V {          // even/odd split of the half spectrum
                 const V* row = raw + b * RP;
-                const V a = row[k], c = row[M - k];     // k = 0: X[0] and X[M]
+                const V zero = mk<V>(R(0), R(0));       // modes beyond the band
+                const V a = (!band || k <= band) ? row[k] : zero;
+                const V c = (!band || M - k <= band) ? row[M - k] : zero;   // k = 0: X[0] and X[M]
                 if (k == 0) return mk<V>(a.x + c.x, a.x - c.x);
                 const V bb = mk<V>(c.x, -c.y);
                 const V E = cadd(a, bb);
@@ -426,7 +451,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) 
         const long long tiles = ((long long)N * H + NLX - 1) / NLX;
         StageTimer tm(p, BSPLINE_STAGE_FFT_X);
         k<<<(unsigned)((c1 - c0) * tiles), threads_for<N, NLX>(), sm, st>>>(reinterpret_cast<const V*>(u_hat), w, c,
-                                                                             tw, c0, nullptr);
+                                                                             tw, c0, nullptr, p->band);
     }
     {
         auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
@@ -454,7 +479,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) 
         k<<<(unsigned)grid, T, sm, st>>>(w, reinterpret_cast<OutT*>(coeffs), ring, tw, ctr,
                                          reinterpret_cast<unsigned*>(p->d_status + kStatusTransformTimeout), lag, ring_slots,
                                          (p->test_hooks & BSPLINE_TEST_DROP_TRANSFORM_SIGNALS) ? 1 : 0,
-                                         (long long)c0 * N, planes, nullptr);
+                                         (long long)c0 * N, planes, nullptr, p->band);
     }
     return set_cuda_error(cudaGetLastError());
 }
@@ -493,7 +518,7 @@ int run_fft_fields(const bspline_plan_s* p, int F, const void* const* in_fields,
         if ((rc = set_smem(k, sm))) return rc;
         const long long tiles = ((long long)N * H + NLX - 1) / NLX;
         k<<<(unsigned)(3LL * F * tiles), threads_for<N, NLX>(), sm, st>>>(
-            nullptr, w, c, tw, 0, reinterpret_cast<const V* const*>(in_fields));
+            nullptr, w, c, tw, 0, reinterpret_cast<const V* const*>(in_fields), 0);
     }
     {
         auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
@@ -515,7 +540,7 @@ int run_fft_fields(const bspline_plan_s* p, int F, const void* const* in_fields,
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 2 * planes), st);
         if (e != cudaSuccess) return set_cuda_error(e);
         k<<<(unsigned)grid, T, sm, st>>>(w, nullptr, ring, tw, ctr, error, lag, 2 * lag, 0, 0LL, planes,
-                                         reinterpret_cast<OutT* const*>(out_fields));
+                                         reinterpret_cast<OutT* const*>(out_fields), 0);
     }
     return set_cuda_error(cudaGetLastError());
 }

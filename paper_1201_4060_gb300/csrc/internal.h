@@ -116,6 +116,7 @@ struct bspline_plan_s {
     int test_hooks = 0;     // BSPLINE_TEST_* flags
     unsigned direct_below = BSPLINE_GATHER_SPLIT_AUTO;   // gather split (bspline_plan_set_gather_split)
     int deterministic = 0;  // bspline_plan_set_deterministic: fixed-point spread of the adjoint
+    int band = 0;           // bspline_plan_set_band: modes beyond |k_i| <= band taken as zero (0: none)
     bs::DeviceBuffer det;   // its accumulator [3][N][N][N] int64 and the cotangent bound
     // Buffers, second stream and events of bspline_run_host (and the second
     // stream of bspline_eval); the copy stream and its events feed the
