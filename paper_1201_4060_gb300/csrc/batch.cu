@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -191,11 +192,12 @@ int build_queue(bspline_batch_s* b, int by, unsigned chunk_len) {
     return BSPLINE_OK;
 }
 
-// Group the fields by grid size and prefilter (order and dtype are the batch's), lay out each group's
-// pointer arrays and transform workspace in tbuf, and upload the pointers.
+// Group the fields by grid size, prefilter and band (order and dtype are the batch's), lay out each
+// group's pointer arrays and transform workspace in tbuf, and upload the pointers.
 int build_groups(bspline_batch_s* b) {
-    std::map<std::pair<int, int>, std::vector<int>> by;
-    for (int i = 0; i < b->n; ++i) by[{b->plans[i]->N, b->plans[i]->prefilter}].push_back(i);
+    std::map<std::tuple<int, int, int>, std::vector<int>> by;
+    for (int i = 0; i < b->n; ++i)
+        by[std::make_tuple(b->plans[i]->N, b->plans[i]->prefilter, b->plans[i]->band)].push_back(i);
     b->groups.clear();
     size_t off = 0;
     std::vector<size_t> offs;

@@ -484,7 +484,7 @@ int run_fft(bspline_plan_s* p, const void* u_hat, void* coeffs, int c0, int c1) 
     return set_cuda_error(cudaGetLastError());
 }
 
-// F fields of one grid size, order and prefilter (the tables of p) in one launch of each kernel:
+// F fields of one grid size, order, prefilter and band (those of p) in one launch of each kernel:
 // in_fields / out_fields are device arrays of F pointers; w is the group's workspace
 // (fields_workspace<V>(N, F) bytes); a wait that runs out sets *error.
 template <typename V> size_t fields_workspace(int N, int F) {
@@ -518,7 +518,7 @@ int run_fft_fields(const bspline_plan_s* p, int F, const void* const* in_fields,
         if ((rc = set_smem(k, sm))) return rc;
         const long long tiles = ((long long)N * H + NLX - 1) / NLX;
         k<<<(unsigned)(3LL * F * tiles), threads_for<N, NLX>(), sm, st>>>(
-            nullptr, w, c, tw, 0, reinterpret_cast<const V* const*>(in_fields), 0);
+            nullptr, w, c, tw, 0, reinterpret_cast<const V* const*>(in_fields), p->band);
     }
     {
         auto k = fft_yz_fused<R, OutT, N, NL, kYCols * NL>;
@@ -540,7 +540,7 @@ int run_fft_fields(const bspline_plan_s* p, int F, const void* const* in_fields,
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (1 + 2 * planes), st);
         if (e != cudaSuccess) return set_cuda_error(e);
         k<<<(unsigned)grid, T, sm, st>>>(w, nullptr, ring, tw, ctr, error, lag, 2 * lag, 0, 0LL, planes,
-                                         reinterpret_cast<OutT* const*>(out_fields), 0);
+                                         reinterpret_cast<OutT* const*>(out_fields), p->band);
     }
     return set_cuda_error(cudaGetLastError());
 }

@@ -255,3 +255,34 @@ def test_batch_queue_autotune_and_its_cache(B, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     assert all(torch.equal(a, b) for a, b in zip(ref, ou))
     batch.close()
+
+
+def test_batch_band_limited_fields_equal_single_field_calls(B):
+    """Plans told that their fields are band-limited (bspline_plan_set_band, K = N/3 here and K = N/4 for a
+    second plan of one grid size: two transform groups of that size) run their transforms on the band in
+    the batch as in single-field calls: the same bits, and the full path's bits too."""
+    spec = [dict(N=48, field_seed=41, particle_seed=51, P=4000, K=16), dict(N=64, field_seed=42, particle_seed=52,
+            P=9000, K=21), dict(N=64, field_seed=43, particle_seed=53, P=3000, K=16)]
+    plans, uh, co, xs, ou, og = [], [], [], [], [], []
+    for f in spec:
+        plan = B.Plan(f["N"], 4, "f32")
+        plan.set_band(f["K"])
+        half = synth.kolmogorov_field(f["N"], seed=f["field_seed"], kmax=f["K"]).dense()
+        plans.append(plan)
+        uh.append(torch.from_numpy(half).to(plan.uhat_dtype).cuda())
+        co.append(plan.empty_coeffs())
+        xs.append(torch.from_numpy(synth.uniform_particles(f["P"], seed=f["particle_seed"])).cuda())
+        ou.append(torch.empty((f["P"], 3), dtype=torch.float32, device="cuda"))
+        og.append(torch.empty((f["P"], 3, 3), dtype=torch.float32, device="cuda"))
+    batch = B.Batch(plans)
+    batch.capture(uh, co, xs, ou, og, streams=2)
+    batch.launch()
+    assert batch.status() == (B.OK, 0)
+    for i, f in enumerate(spec):
+        c, u, g = _single_field(plans, uh, xs, i)
+        full = B.Plan(f["N"], 4, "f32")
+        cf = full.coeffs(uh[i])
+        torch.cuda.synchronize()
+        assert torch.equal(c, co[i]) and torch.equal(cf, co[i])
+        assert torch.equal(u, ou[i]) and torch.equal(g, og[i])
+    batch.close()
