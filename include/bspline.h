@@ -114,8 +114,11 @@ int bspline_plan_set_prefilter(bspline_plan_t plan, bspline_prefilter kind);
  * kmax from the host.  The coefficients are bit for bit those of the full
  * transform of u_hat with those modes zero (whatever u_hat holds there).
  * kmax = 0 (the default) turns it off.  Errors: INVALID_ARG for kmax < 0 or
- * 2 kmax >= N (the band must leave out the Nyquist planes).  The adjoint
- * transform of bspline_spread_adjoint always produces the full spectrum. */
+ * 2 kmax >= N (the band must leave out the Nyquist planes).  Since the forward
+ * path then ignores the modes outside the box, their gradient is zero: the
+ * g_u_hat of bspline_spread_adjoint holds zeros there and, inside the box,
+ * the full adjoint's bits (the transposed transform skips the ky lines beyond
+ * the band). */
 int bspline_plan_set_band(bspline_plan_t plan, int kmax);
 
 /* The prefilter c(k) that a plan of this N, order and kind applies along each

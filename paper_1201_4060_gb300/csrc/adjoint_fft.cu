@@ -70,7 +70,7 @@ fft_z_r2c(const R* __restrict__ g, typename Cx<R>::T* __restrict__ out, const ty
 // One (component, x) plane, NL columns kz0.., all y: forward c2c along y in place.
 template <typename R, int N, int NL>
 __global__ void __launch_bounds__(threads_for<N, NL>())
-fft_y_fwd(typename Cx<R>::T* __restrict__ w, const typename Cx<R>::T* __restrict__ tw) {
+fft_y_fwd(typename Cx<R>::T* __restrict__ w, const typename Cx<R>::T* __restrict__ tw, int band) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int H = N / 2 + 1, HP = row_pitch(N);
@@ -81,6 +81,7 @@ fft_y_fwd(typename Cx<R>::T* __restrict__ w, const typename Cx<R>::T* __restrict
     const int t = threadIdx.x;
     const long long pl = blockIdx.x / TPZ;
     const int kz0 = (int)(blockIdx.x % TPZ) * NL;
+    if (band && kz0 > band) return;                      // columns the band's last pass writes as zero
     const int valid = min(NL, H - kz0);
     V* base = w + pl * N * HP + kz0;
     load_tile<V, N, NL, T, NL>(s, base, HP, valid);
@@ -100,7 +101,7 @@ fft_y_fwd(typename Cx<R>::T* __restrict__ w, const typename Cx<R>::T* __restrict
 template <typename R, int N, int NL>
 __global__ void __launch_bounds__(threads_for<N, NL>())
 fft_x_fwd_prefilter(const typename Cx<R>::T* __restrict__ w, typename Cx<R>::T* __restrict__ out,
-                    const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw) {
+                    const R* __restrict__ c, const typename Cx<R>::T* __restrict__ tw, int band) {
     using V = typename Cx<R>::T;
     constexpr int T = threads_for<N, NL>();
     constexpr int M = N / 2, H = M + 1, HP = row_pitch(N);
@@ -113,6 +114,16 @@ fft_x_fwd_prefilter(const typename Cx<R>::T* __restrict__ w, typename Cx<R>::T* 
     const int rem = (int)(blockIdx.x % ((long long)N * TPZ));
     const int ky = rem / TPZ, kz0 = (rem % TPZ) * NL;
     const int valid = min(NL, H - kz0);
+    // a band (bspline_plan_set_band): the forward path ignores every mode outside |kx|, |ky|, kz <= band,
+    // so their gradient is zero; columns wholly outside it are written as zeros without a transform
+    V* dst = out + (long long)comp * N * N * H;
+    if (band && (kz0 > band || (ky > band && ky < N - band))) {
+        for (int e = t; e < N * NL; e += T) {
+            const int kx = e / NL, b = e % NL;
+            if (b < valid) dst[((long long)kx * N + ky) * H + kz0 + b] = mk<V>(R(0), R(0));
+        }
+        return;
+    }
     load_tile<V, N, NL, T, NL>(s, w + (long long)comp * N * N * HP + (long long)ky * HP + kz0, (long long)N * HP,
                                valid);
     for (int m = t; m < N; m += T) tws[m] = tw[m];
@@ -120,14 +131,14 @@ fft_x_fwd_prefilter(const typename Cx<R>::T* __restrict__ w, typename Cx<R>::T* 
     __syncthreads();
     fft_smem<V, N, NL, T, NL>(s, tws, 1);
     const R cy = __ldg(&c[ky]);
-    V* dst = out + (long long)comp * N * N * H;
     for (int e = t; e < N * NL; e += T) {
         const int kx = e / NL, b = e % NL;
         if (b < valid) {
             const int kz = kz0 + b;
             const R f = __ldg(&c[kx]) * cy * __ldg(&c[kz]) * ((kz == 0 || kz == M) ? R(1) : R(2));
             const V a = s[((N - kx) % N) * NL + b];
-            dst[((long long)kx * N + ky) * H + kz] = mk<V>(a.x * f, a.y * f);
+            const bool in = !band || (kz <= band && (kx <= band || kx >= N - band));
+            dst[((long long)kx * N + ky) * H + kz] = in ? mk<V>(a.x * f, a.y * f) : mk<V>(R(0), R(0));
         }
     }
 }
@@ -164,14 +175,14 @@ int run_adjoint_fft(bspline_plan_s* p, const void* g_coef, void* g_u_hat) {
         auto k = fft_y_fwd<R, N, NL>;
         const size_t sm = sizeof(V) * (N + (size_t)N * NL);
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<(unsigned)(3LL * N * TPZ), T, sm, st>>>(w, tw);
+        k<<<(unsigned)(3LL * N * TPZ), T, sm, st>>>(w, tw, p->band);
     }
     {
         constexpr int T = threads_for<N, NL>();
         auto k = fft_x_fwd_prefilter<R, N, NL>;
         const size_t sm = sizeof(V) * (N + (size_t)N * NL);
         if ((rc = set_smem(k, sm))) return rc;
-        k<<<(unsigned)(3LL * N * TPZ), T, sm, st>>>(w, reinterpret_cast<V*>(g_u_hat), c, tw);
+        k<<<(unsigned)(3LL * N * TPZ), T, sm, st>>>(w, reinterpret_cast<V*>(g_u_hat), c, tw, p->band);
     }
     return set_cuda_error(cudaGetLastError());
 }

@@ -89,6 +89,24 @@ def test_band_eval_and_host_path_equal_the_full_path(B, N, K, dtype):
     assert band.status() == 0
 
 
+@pytest.mark.parametrize("N,K,dtype", [(48, 16, "f64"), (64, 21, "f32"), (32, 1, "f32")])
+def test_band_adjoint_is_the_full_adjoint_inside_and_zero_outside(B, N, K, dtype):
+    """The banded forward path ignores the modes outside the band, so the gradient there is zero; inside,
+    the transposed transform gives the full one's bits."""
+    rng = np.random.default_rng(N + K)
+    full = B.Plan(N, 4, dtype)
+    band = B.Plan(N, 4, dtype)
+    band.set_band(K)
+    g = torch.from_numpy(rng.standard_normal((3, N, N, N))).to(full.out_dtype).cuda()
+    x = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    gf, _, _ = full.spread_adjoint(x, g_coef=g.clone())
+    gb, _, _ = band.spread_adjoint(x, g_coef=g.clone())
+    torch.cuda.synchronize()
+    out = torch.from_numpy(outside_band(N, K)).cuda()
+    expect = torch.where(out[None], torch.zeros_like(gf), gf)
+    assert torch.equal(gb, expect)
+
+
 def test_band_off_and_argument_checks(B):
     plan = B.Plan(32, 4, "f32")
     for bad in (-1, 16, 40):
