@@ -225,9 +225,15 @@ int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const dou
  *           coeffs (as written by bspline_coeffs); NaN for non-finite positions.
  * x is required when P > 0 and g_coeffs or g_x is given.  Non-finite positions
  * contribute nothing to g_coeffs and are counted in the status word.
- * FP32 plans accumulate g_coeffs with atomics: the summation order, and so
- * the last bits, vary between calls, unless bspline_plan_set_deterministic
- * turned on exact fixed-point sums.  Uses the plan's particle and transform
+ * FP32 and BF16 plans sum each work item's contributions exactly in
+ * two-word fixed point at scales taken from the item's largest cotangent
+ * (each contribution rounded once, about 40 bits below that bound), convert
+ * each node's sum to FP32 once and add the items into g_coeffs with FP32
+ * atomics: the order of those additions, and so the last bits, vary between
+ * calls, unless bspline_plan_set_deterministic turned on exact sums over all
+ * items.  Items holding a non-finite cotangent are summed with FP32 atomics,
+ * so NaN and infinities reach the nodes of those particles' stencils.
+ * FP64 plans sum with FP64 atomics.  Uses the plan's particle and transform
  * workspaces.  BSPLINE_ERR_INVALID_ARG for a missing required pointer, a bad
  * alignment or P outside [0, 2^31). */
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,
@@ -235,19 +241,22 @@ int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double
                            double* g_x);
 
 /* Deterministic adjoint (FP32 and BF16 plans; FP64 plans: NOT_IMPLEMENTED).
- * By default bspline_spread_adjoint adds the particles' contributions to
- * g_coeffs with floating-point atomics, so the order of the additions, and
- * the last bits of g_coeffs and g_u_hat, vary between calls.  With
- * enable = 1 each contribution is computed in FP32 as before, rounded once to
- * a 64-bit fixed-point integer at the scale 2^e, e = 61 - ceil(log2(G (1 +
- * 3 N/L) P)) with G the largest |g_u| or |g_grad| over the particles (no
- * node's sum can then leave the integer range), summed exactly with integer
- * atomics and converted back once per node: the result is bit-identical from
- * call to call, and each contribution carries an absolute rounding of at
- * most 2^-(e+1) instead of an FP32 rounding per addition.  Costs a
- * [3][N][N][N] int64 accumulator in the plan (allocated on first use) and a
- * slower spread.  Cotangents must be finite in this mode.  Position gradients
- * and the transform are deterministic in both modes. */
+ * By default bspline_spread_adjoint adds the work items' sums to g_coeffs
+ * with floating-point atomics, so the order of the additions, and the last
+ * bits of g_coeffs and g_u_hat, vary between calls.  With enable = 1 each
+ * contribution is computed in FP32 as before and rounded once to an integer
+ * at the scale 2^e, one scale for the whole call:
+ * e = min(36 - ceil(log2 Gb), 61 - ceil(log2(P Gb)), 118) with
+ * Gb = G (1 + 3 N/L) (Gb = G without g_grad) and G the largest |g_u| or
+ * |g_grad| over the particles, so that no node's sum can leave the 64-bit
+ * range; the integers are summed exactly (integer atomics into a 64-bit
+ * accumulator) and converted back once per node: the result is
+ * bit-identical from call to call, and each contribution carries an
+ * absolute rounding of at most 2^-(e+1).  Costs a [3][N][N][N] int64
+ * accumulator in the plan (allocated on first use), a pass over the
+ * cotangents and a pass over the accumulator.  A non-finite cotangent makes
+ * the call fall back to FP32 atomics (not bit-identical then).  Position
+ * gradients and the transform are deterministic in both modes. */
 int bspline_plan_set_deterministic(bspline_plan_t plan, int enable);
 
 /* Device workspace bspline_interp needs for P positions. */

@@ -9,8 +9,9 @@
 //                             + (N/L) (g_grad[c][0] w'_x w_y w_z + g_grad[c][1] w_x w'_y w_z
 //                                      + g_grad[c][2] w_x w_y w'_z)
 //            accumulated per work item in a shared-memory tile of the brick
-//            (shared-memory atomics), then added to g_coef with global
-//            atomics (periodic wrap); per node 1 multiply + 1 FMA after the
+//            (shared-memory atomics; FP32 types in two-word fixed point),
+//            then added to g_coef with global atomics (periodic wrap); per
+//            node 1 multiply + 1 FMA after the
 //            factorisation  w_z (w_y q0 + w'_y q1) + w'_z (w_y q2),
 //            q0 = g_u w_x + s g0 w'_x, q1 = s g1 w_x, q2 = s g2 w_x;
 //   g_x:     the derivative of sum_c g_u[c] u_c + sum_{c,e} g_grad[c][e] du_c/dx_e
@@ -82,35 +83,303 @@ __device__ __forceinline__ bool item_range(const Ws<TR>& w, unsigned NB, unsigne
     return *beg < *end;
 }
 
-// The n particles of an item [beg, beg + n) ordered rank-major, bank-minor by
-// the bank (element index mod 32) of their stencil origin in a tile of row
-// stride EZ and plane stride EY * EZ, into s_order (as in the gather): a warp
-// taking 32 consecutive particles of that order touches each bank at most
-// once per rank it spans.  Ends with a barrier.
-template <int EY, int EZ, int NT, typename TR>
-__device__ __forceinline__ void bank_order(const Ws<TR>& w, unsigned beg, unsigned n, int x0, int y0, int z0,
-                                           unsigned* s_bucket, unsigned short* s_order) {
-    constexpr int KT = (kChunk + NT - 1) / NT;
-    unsigned packed[KT];
-    if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
+// Accumulation tile of the FP64 spread: the brick plus halo, [c][x][y][z], unpadded.
+template <int ORD> constexpr size_t acc_bytes() {
+    using S = Shape<double, ORD>;
+    return sizeof(double) * 3 * (size_t)S::EX * S::EY * S::EZ;
+}
+
+// FP64 spread, one CTA per work item: its particles' cotangents into a shared
+// tile (FP64 shared-memory atomics, particles in their sorted order), then the
+// tile added to g_coef with global atomics.  Compiled for three CTAs per SM.
+template <int ORD, typename TR, bool GRAD>
+__global__ void __launch_bounds__(kAdjThreads, 3)
+spread_kernel(int N, BrickGrid bg, Ws<TR> w, const double* __restrict__ g_u, const double* __restrict__ g_grad,
+              double* __restrict__ g_coef, double dscale, unsigned long long* __restrict__ status) {
+    using S = Shape<double, ORD>;
+    constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ;
+    constexpr int E3 = EX * EY * EZ;                    // one component
+    const unsigned NB = bg.NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* acc = reinterpret_cast<double*>(smem_raw);
+    unsigned brick, beg, end;
+    if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
+    int x0, y0, z0;
+    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
+    const unsigned n = end - beg;
+    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) acc[e] = 0.0;
     __syncthreads();
+    Rec<TR> rc_next;                                    // a thread's next record, requested ahead
+    if (threadIdx.x < n) rc_next = w.s_rec[beg + threadIdx.x];
+    for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
+        const Rec<TR> rc = rc_next;
+        if (q + kAdjThreads < n) rc_next = w.s_rec[beg + q + kAdjThreads];
+        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+        const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
+        const int oz = (int)(rc.cell & 1023u) - z0;
+        const size_t idx = rc.idx;
+        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
+                             (long long)idx < w.P,
+                         status + kStatusBounds))
+            continue;
+        // the particle's cotangents, all requested before the reductions
+        double cu[3], cg[9];
 #pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        const unsigned i = threadIdx.x + k * NT;
-        if (i < n) {
-            const unsigned cp = w.s_rec[beg + i].cell;
-            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
-            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
-            const int oz = (int)(cp & 1023u) - z0;
-            const unsigned r = (unsigned)((ox * EY + oy) * EZ + oz) & 31u;
-            packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
+        for (int c = 0; c < 3; ++c) cu[c] = g_u ? g_u[3 * idx + c] : 0.0;
+        if (GRAD) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) cg[e] = g_grad[9 * idx + e];
+        }
+        double wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
+        bspline_weights<ORD, double>((double)rc.t[0], wx, dwx);
+        bspline_weights<ORD, double>((double)rc.t[1], wy, dwy);
+        bspline_weights<ORD, double>((double)rc.t[2], wz, dwz);
+        double* base = acc + (ox * EY + oy) * EZ + oz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double gu = cu[c];
+            double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+            if (GRAD) {
+                g0 = cg[3 * c + 0] * dscale;
+                g1 = cg[3 * c + 1] * dscale;
+                g2 = cg[3 * c + 2] * dscale;
+            }
+            double* tc = base + c * E3;
+#pragma unroll
+            for (int jx = 0; jx < ORD; ++jx) {
+                const double q0 = GRAD ? fma(g0, dwx[jx], gu * wx[jx]) : gu * wx[jx];
+                const double q1 = g1 * wx[jx], q2 = g2 * wx[jx];
+#pragma unroll
+                for (int jy = 0; jy < ORD; ++jy) {
+                    const double p0 = GRAD ? fma(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
+                    const double p1 = q2 * wy[jy];
+                    double* line = tc + (jx * EY + jy) * EZ;
+#pragma unroll
+                    for (int jz = 0; jz < ORD; ++jz) atomicAdd(line + jz, GRAD ? fma(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz]);
+                }
+            }
         }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) {
+        const double v = acc[e];
+        if (v != 0.0) {
+            const int c = e / E3, r = e - c * E3;
+            const int ix = r / (EY * EZ), iy = (r / EZ) % EY, iz = r % EZ;
+            atomicAdd(&g_coef[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N +
+                              wrap_index(z0 + iz, N)],
+                      v);
+        }
+    }
+}
+
+// ---- FP32 spread in two-word fixed point.  Shared-memory reductions of 32-bit
+// integers cost next to nothing beside the rest of the spread, those of FP32
+// values (and of 64-bit integers) several times more: on the adjoint workload
+// 0.67 ms with 32-bit integer reductions, 1.08 ms with FP32 ones, 2.0 ms with
+// 64-bit ones.  So each contribution v is split at the scales 2^e1 and
+// 2^(e1 + e2) into
+//     hi = rint(v 2^e1),  lo = rint((v 2^e1 - hi) 2^e2),   hi 2^e2 + lo = rint(v 2^(e1 + e2)),
+// both added with 32-bit integer reductions into a tile of two words a node;
+// the node's sum  sum hi 2^-e1 + sum lo 2^-(e1 + e2)  is exact up to half a
+// unit of 2^-(e1 + e2) per contribution.  The scales come from a bound on the
+// contributions: with G the largest cotangent magnitude and |w|, |w'| <= 1 for
+// a cardinal B-spline, |v| <= Gb = G (1 + 3 N/L); rint is FP32 addition of
+// 1.5 2^23, exact while |x| < 2^22, and no node's sums of at most n terms may
+// leave 2^30.  Per work item (G and n of the item's particles):
+//     e1 = min(21 - ceil(log2 Gb), 29 - ceil(log2 (n Gb)), 100),  e2 = min(22, 30 - ceil(log2 (n + 1))),
+// about 40 bits below the largest contribution, then one conversion to FP32
+// and FP32 atomics into g_coef.  Deterministic mode (one scale for every
+// item, so that the rounding of a contribution does not depend on which item
+// it falls in; G over all particles, n <= 2048, P particles in all):
+//     e1 = min(18 - ceil(log2 Gb), Ef),  e2 = Ef - e1,  Ef = min(36 - ceil(log2 Gb), 61 - ceil(log2 (P Gb)), 118),
+// and each node's hi 2^e2 + lo goes to a 64-bit fixed-point accumulator with
+// integer atomics: every contribution is rounded once, rint(v 2^Ef), and all
+// sums are exact, so neither particle order nor atomics order changes a bit;
+// one FP64 multiply by 2^-Ef and one FP32 add take the sums into g_coef.
+// Non-finite cotangents fall back to FP32 reductions (NaN and infinities reach
+// g_coef).  The two-word tile is split along x into XP parts, one CTA each,
+// so that two CTAs share an SM.
+template <int ORD> struct FxShape {
+    using S = Shape<float, ORD>;
+    static constexpr int BX = S::BX, BY = S::BY, BZ = S::BZ;
+    static constexpr int XP = ORD <= 5 ? 2 : 4;         // x parts of a brick
+    static constexpr int XW = BX / XP;                   // origins of one part in x
+    static constexpr int EX = XW + ORD - 1, EY = S::EY, EZ = S::EZ;
+    static constexpr int E3 = EX * EY * EZ;              // nodes of one component
+};
+static_assert(FxShape<2>::BX % FxShape<2>::XP == 0 && FxShape<8>::BX % FxShape<8>::XP == 0, "x parts");
+constexpr int kFxThreads = 384;
+
+template <int ORD> constexpr size_t fx_tile_bytes() { return sizeof(unsigned) * 6 * (size_t)FxShape<ORD>::E3; }
+
+constexpr float kRintMagic = 12582912.0f;               // 1.5 2^23
+constexpr unsigned kRintMagicBits = 0x4B400000u;
+
+__device__ __forceinline__ void red_shared_u32(unsigned* p, unsigned v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_f32(float* p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+}
+
+// The split scales; fixed = false for a non-finite bound.
+struct FxScale {
+    bool fixed;
+    int e1, e2;
+};
+
+// gbits: the bits of G (non-negative floats order as their bits, NaN above infinity); n: terms a node can sum.
+__device__ __forceinline__ FxScale fx_item_scale(unsigned gbits, float bound_factor, unsigned n) {
+    const float Gb = __uint_as_float(gbits) * bound_factor;
+    FxScale s{gbits < 0x7F800000u && Gb * (float)n < INFINITY, 0, 0};
+    if (s.fixed && gbits) {
+        int kG, kT;
+        frexpf(Gb, &kG);                                // Gb < 2^kG
+        frexpf(Gb * (float)n, &kT);
+        s.e1 = min(min(21 - kG, 29 - kT), 100);
+        s.e2 = min(22, 30 - (32 - __clz(n)));
+    }
+    return s;
+}
+
+__device__ __forceinline__ FxScale fx_det_scale(unsigned gbits, float bound_factor, long long P) {
+    const float Gb = __uint_as_float(gbits) * bound_factor;
+    FxScale s{gbits < 0x7F800000u && Gb * (float)P < INFINITY, 0, 0};
+    if (s.fixed && gbits) {
+        int kG, kP;
+        frexpf(Gb, &kG);
+        frexpf(Gb * (float)P, &kP);
+        const int ef = min(min(36 - kG, 61 - kP), 118);
+        s.e1 = min(18 - kG, ef);
+        s.e2 = ef - s.e1;
+    }
+    return s;
+}
+
+// G over all particles (deterministic mode), as bits.
+template <bool GRAD>
+__global__ void cotangent_bound_kernel(const float* __restrict__ g_u, const float* __restrict__ g_grad,
+                                       long long P, unsigned* __restrict__ bound) {
+    unsigned m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        if (g_u) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) m = max(m, __float_as_uint(fabsf(g_u[3 * i + c])));
+        }
+        if (GRAD) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) m = max(m, __float_as_uint(fabsf(g_grad[9 * i + k])));
+        }
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(bound, m);
+}
+
+// The contributions of one particle to its 3 n^3 nodes (factorised as in spread_kernel), each handed to add(node, v).
+template <int ORD, bool GRAD, typename Add>
+__device__ __forceinline__ void spread_particle(const float (&cu)[3], const float (&cg)[9], float dscale,
+                                                const float (&wx)[ORD], const float (&dwx)[ORD],
+                                                const float (&wy)[ORD], const float (&dwy)[ORD],
+                                                const float (&wz)[ORD], const float (&dwz)[ORD], int base,
+                                                int E3, int EY, int EZ, Add add) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float gu = cu[c];
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (GRAD) {
+            g0 = cg[3 * c + 0] * dscale;
+            g1 = cg[3 * c + 1] * dscale;
+            g2 = cg[3 * c + 2] * dscale;
+        }
+#pragma unroll
+        for (int jx = 0; jx < ORD; ++jx) {
+            const float q0 = GRAD ? fmaf(g0, dwx[jx], gu * wx[jx]) : gu * wx[jx];
+            const float q1 = g1 * wx[jx], q2 = g2 * wx[jx];
+#pragma unroll
+            for (int jy = 0; jy < ORD; ++jy) {
+                const float p0 = GRAD ? fmaf(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
+                const float p1 = q2 * wy[jy];
+                const int line = base + c * E3 + (jx * EY + jy) * EZ;
+#pragma unroll
+                for (int jz = 0; jz < ORD; ++jz) add(line + jz, GRAD ? fmaf(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz]);
+            }
+        }
+    }
+}
+
+// One CTA per (work item, x part).  DET: the deterministic mode's scales (bound = G over all particles) and
+// the tile added to acc_g; otherwise the item's own scales and the tile added to g_coef.
+template <int ORD, typename TR, bool GRAD, bool DET>
+__global__ void __launch_bounds__(kFxThreads, 2)
+spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, const float* __restrict__ g_grad,
+                 float* __restrict__ g_coef, long long* __restrict__ acc_g, const unsigned* __restrict__ bound,
+                 float dscale, float bound_factor, unsigned long long* __restrict__ status) {
+    using F = FxShape<ORD>;
+    constexpr int EX = F::EX, EY = F::EY, EZ = F::EZ, E3 = F::E3, BZ = F::BZ, XW = F::XW;
+    const unsigned NB = bg.NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned* hi = reinterpret_cast<unsigned*>(smem_raw);     // [3][EX][EY][EZ], then lo the same
+    unsigned* lo = hi + 3 * E3;
+    unsigned brick, beg, end;
+    if (!item_range(w, NB, blockIdx.x / F::XP, &brick, &beg, &end)) return;
+    const int part = (int)(blockIdx.x % F::XP);
+    int x0, y0, z0;
+    brick_origin<F::BX, F::BY, F::BZ>(brick, bg, &x0, &y0, &z0);
+    __shared__ unsigned s_bucket[32];
+    __shared__ unsigned short s_order[kChunk];
+    __shared__ unsigned s_gmax;
+    const unsigned n = end - beg;
+    for (int e = threadIdx.x; e < 6 * E3; e += kFxThreads) hi[e] = 0u;
+    if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_gmax = 0;
+    __syncthreads();
+    // this part's particles, bucketed by the bank of their stencil origin in the part's tile (rank-major,
+    // bank-minor, as in the gather), and the largest magnitude of their cotangents
+    constexpr int KT = (kChunk + kFxThreads - 1) / kFxThreads;
+    unsigned packed[KT];
+    unsigned gbits = 0;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        const unsigned i = threadIdx.x + k * NT;
+        const unsigned i = threadIdx.x + k * kFxThreads;
+        packed[k] = ~0u;
         if (i < n) {
+            const Rec<TR>& rc = w.s_rec[beg + i];
+            const unsigned cp = rc.cell;
+            const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
+            const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
+            const int oz = (int)(cp & 1023u) - z0;
+            const long long idx = rc.idx;
+            const bool ok = ox >= 0 && ox < F::BX && oy >= 0 && oy < F::BY && oz >= 0 && oz < F::BZ && idx < w.P;
+            if (part == 0) (void)BS_CHECK_OK(ok, status + kStatusBounds);
+            if (ok && ox / XW == part) {
+                const unsigned r = (unsigned)(((ox - part * XW) * EY + oy) * EZ + oz) & 31u;
+                packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
+                if (!DET) {
+                    if (g_u) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) gbits = max(gbits, __float_as_uint(fabsf(g_u[3 * idx + c])));
+                    }
+                    if (GRAD) {
+#pragma unroll
+                        for (int e = 0; e < 9; ++e)
+                            gbits = max(gbits, __float_as_uint(fabsf(g_grad[9 * idx + e])));
+                    }
+                }
+            }
+        }
+    }
+    if (!DET) {
+        gbits = __reduce_max_sync(0xffffffffu, gbits);
+        if ((threadIdx.x & 31) == 0 && gbits) atomicMax(&s_gmax, gbits);
+    }
+    __syncthreads();
+    unsigned np = 0;                                    // particles of this part
+#pragma unroll 8
+    for (unsigned q = 0; q < 32; ++q) np += s_bucket[q];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        if (packed[k] != ~0u) {
             const unsigned r = packed[k] & 31u, rk = packed[k] >> 5;
             unsigned pos = 0;
 #pragma unroll 8
@@ -118,317 +387,100 @@ __device__ __forceinline__ void bank_order(const Ws<TR>& w, unsigned beg, unsign
                 const unsigned bq = s_bucket[q];
                 pos += min(bq, rk) + ((q < r && bq > rk) ? 1u : 0u);
             }
-            s_order[pos] = (unsigned short)i;
+            s_order[pos] = (unsigned short)(threadIdx.x + k * kFxThreads);
         }
     }
+    const unsigned gmax = DET ? *bound : s_gmax;
     __syncthreads();
-}
-
-// Accumulation tile of the spread: the brick plus halo, [c][x][y][z], unpadded.
-template <int ORD, typename A> constexpr size_t acc_bytes() {
-    using S = Shape<A, ORD>;
-    return sizeof(A) * 3 * (size_t)S::EX * S::EY * S::EZ;
-}
-
-// One CTA per work item: spread its particles' cotangents into a shared tile,
-// then add the tile to g_coef.  The accumulation tile allows three CTAs per SM;
-// compiled for three (more registers between the shared-memory atomics):
-// 1.13 -> 1.10 ms at 256^3, cubic, 2^22 particles.
-template <int ORD, typename TR, typename A, bool GRAD>
-__global__ void __launch_bounds__(kAdjThreads, 3)
-spread_kernel(int N, BrickGrid bg, Ws<TR> w, const A* __restrict__ g_u, const A* __restrict__ g_grad,
-              A* __restrict__ g_coef, A dscale, unsigned long long* __restrict__ status) {
-    using S = Shape<A, ORD>;
-    constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ, BZ = S::BZ;
-    constexpr int E3 = EX * EY * EZ;                    // one component
-    const unsigned NB = bg.NB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    A* acc = reinterpret_cast<A*>(smem_raw);
-    unsigned brick, beg, end;
-    if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
-    int x0, y0, z0;
-    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
-    __shared__ unsigned s_bucket[32];
-    __shared__ unsigned short s_order[kChunk];
-    const unsigned n = end - beg;
-    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) acc[e] = A(0);
-    if (threadIdx.x < 32) s_bucket[threadIdx.x] = 0;
-    __syncthreads();
-    // FP32: particles ordered rank-major, bank-minor by the bank of their stencil origin (as in the
-    // gather), so a warp's shared-memory atomics hit distinct banks; FP64 keeps the sorted order
-    constexpr bool kBucket = sizeof(A) == 4;
-    if constexpr (kBucket) {
-        constexpr int KT = (kChunk + kAdjThreads - 1) / kAdjThreads;
-        unsigned packed[KT];
-#pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            const unsigned i = threadIdx.x + k * kAdjThreads;
-            if (i < n) {
-                const unsigned cp = w.s_rec[beg + i].cell;
-                const int ox = (int)(cp >> (2 * kAnchorBits)) - x0;
-                const int oy = (int)((cp >> kAnchorBits) & 1023u) - y0;
-                const int oz = (int)(cp & 1023u) - z0;
-                const unsigned r = (unsigned)((ox * EY + oy) * EZ + oz) & 31u;
-                packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            const unsigned i = threadIdx.x + k * kAdjThreads;
-            if (i < n) {
-                const unsigned r = packed[k] & 31u, rk = packed[k] >> 5;
-                unsigned pos = 0;
-#pragma unroll 8
-                for (unsigned q = 0; q < 32; ++q) {
-                    const unsigned bq = s_bucket[q];
-                    pos += min(bq, rk) + ((q < r && bq > rk) ? 1u : 0u);
-                }
-                s_order[pos] = (unsigned short)i;
-            }
-        }
-        __syncthreads();
-    }
-    // a thread's next record is requested while its current particle is spread
-    auto record = [&](unsigned q) { return w.s_rec[beg + (kBucket ? (unsigned)s_order[q] : q)]; };
-    Rec<TR> rc_next;
-    if (threadIdx.x < n) rc_next = record(threadIdx.x);
-    for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
-        const Rec<TR> rc = rc_next;
-        if (q + kAdjThreads < n) rc_next = record(q + kAdjThreads);
-        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
+    if (gmax == 0 || np == 0) return;                   // every contribution is zero
+    const FxScale sc = DET ? fx_det_scale(gmax, bound_factor, w.P) : fx_item_scale(gmax, bound_factor, np);
+    const float s1 = ldexpf(1.f, sc.e1), s2 = ldexpf(1.f, sc.e2);
+    const int xs = part * XW;
+    auto particle = [&](const Rec<TR>& rc, auto add) {
+        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0 - xs;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
         const size_t idx = rc.idx;
-        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
-                             (long long)idx < w.P,
-                         status + kStatusBounds))
-            continue;
-        // the particle's cotangents, all requested before the shared-memory reductions (loads cannot move
-        // across them)
-        A cu[3], cg[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) cu[c] = g_u ? g_u[3 * idx + c] : A(0);
-        if (GRAD) {
-#pragma unroll
-            for (int e = 0; e < 9; ++e) cg[e] = g_grad[9 * idx + e];
-        }
-        A wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
-        bspline_weights<ORD, A>((A)rc.t[0], wx, dwx);
-        bspline_weights<ORD, A>((A)rc.t[1], wy, dwy);
-        bspline_weights<ORD, A>((A)rc.t[2], wz, dwz);
-        A* base = acc + (ox * EY + oy) * EZ + oz;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const A gu = cu[c];
-            A g0 = A(0), g1 = A(0), g2 = A(0);
-            if (GRAD) {
-                g0 = cg[3 * c + 0] * dscale;
-                g1 = cg[3 * c + 1] * dscale;
-                g2 = cg[3 * c + 2] * dscale;
-            }
-            A* tc = base + c * E3;
-#pragma unroll
-            for (int jx = 0; jx < ORD; ++jx) {
-                const A q0 = GRAD ? fma(g0, dwx[jx], gu * wx[jx]) : gu * wx[jx];
-                const A q1 = g1 * wx[jx], q2 = g2 * wx[jx];
-#pragma unroll
-                for (int jy = 0; jy < ORD; ++jy) {
-                    const A p0 = GRAD ? fma(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
-                    const A p1 = q2 * wy[jy];
-                    A* line = tc + (jx * EY + jy) * EZ;
-#pragma unroll
-                    for (int jz = 0; jz < ORD; ++jz) {
-                        const A v = GRAD ? fma(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz];
-                        if constexpr (sizeof(A) == 4) {   // reduction without a return value
-                            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(
-                                             (unsigned)__cvta_generic_to_shared(line + jz)),
-                                         "f"((float)v)
-                                         : "memory");
-                        } else {
-                            atomicAdd(line + jz, v);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if constexpr (sizeof(A) == 4) {
-        // per tile row: the brick's B nodes as B/4 aligned 16-byte vector atomics
-        // (z0 and N are multiples of 4, so 4 consecutive z stay inside one period),
-        // then the EZ - BZ halo nodes one by one
-        constexpr int U = BZ / 4 + (EZ - BZ);
-        for (int e = threadIdx.x; e < 3 * EX * EY * U; e += kAdjThreads) {
-            const int row = e / U, k = e - row * U;
-            const int c = row / (EX * EY), ix = (row / EY) % EX, iy = row % EY;
-            const A* src = acc + (size_t)row * EZ;
-            A* dst = g_coef + (((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N;
-            if (k < BZ / 4) {
-                const float4 v = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
-                if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
-                    atomicAdd(reinterpret_cast<float4*>(dst + wrap_index(z0 + 4 * k, N)), v);
-            } else {
-                const int iz = BZ + (k - BZ / 4);
-                const A v = src[iz];
-                if (v != A(0)) atomicAdd(dst + wrap_index(z0 + iz, N), v);
-            }
-        }
-    } else {
-        for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) {
-            const A v = acc[e];
-            if (v != A(0)) {
-                const int c = e / E3, r = e - c * E3;
-                const int ix = r / (EY * EZ), iy = (r / EZ) % EY, iz = r % EZ;
-                atomicAdd(&g_coef[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N +
-                                  wrap_index(z0 + iz, N)],
-                          v);
-            }
-        }
-    }
-}
-
-// ---- Deterministic spread (plan option, FP32 accumulation types): every
-// node's sum is formed in 64-bit fixed point, which integer atomics add
-// exactly, so the order in which particles and work items arrive no longer
-// changes a bit.  Each contribution is computed in FP32 as in spread_kernel
-// and rounded once to an integer at the scale 2^e; e is chosen from a bound
-// on all contributions so that no node's sum can leave 2^61:
-//   |contribution| <= G (1 + 3 N/L),  G = max |g_u|, |g_grad| over particles
-// (|w| <= 1 and |w'| <= 1 for a cardinal B-spline), at most P per node, so
-// e = 61 - ceil(log2(G (1 + 3 N/L) P)).  The sums then go through one FP64
-// multiply by 2^-e and one FP32 add into g_coef.
-
-// G: atomic maximum over the cotangents' magnitudes (non-negative floats order as their bits).
-template <bool GRAD>
-__global__ void cotangent_bound_kernel(const float* __restrict__ g_u, const float* __restrict__ g_grad,
-                                       long long P, unsigned* __restrict__ bound) {
-    float m = 0.f;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
-        if (g_u) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) m = fmaxf(m, fabsf(g_u[3 * i + c]));
-        }
-        if (GRAD) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) m = fmaxf(m, fabsf(g_grad[9 * i + k]));
-        }
-    }
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(bound, __float_as_uint(m));
-}
-
-// The scale exponent e of the fixed point (the same in every thread: it depends on G, N/L and P only).
-__device__ __forceinline__ int det_exponent(const unsigned* bound, float dscale, long long P) {
-    const float T = __uint_as_float(*bound) * (1.f + 3.f * dscale) * (float)P;
-    int ex = 0;
-    if (T > 0.f) frexpf(T, &ex);                        // T < 2^ex
-    return min(100, 61 - ex);
-}
-
-__device__ __forceinline__ void red_shared_s64(long long* p, long long v) {
-    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v) : "memory");
-}
-
-// As spread_kernel (FP32), the tile in fixed point and the tile added to acc_g with 64-bit integer atomics.
-template <int ORD, typename TR, bool GRAD>
-__global__ void __launch_bounds__(kAdjThreads)
-spread_det_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, const float* __restrict__ g_grad,
-                  long long* __restrict__ acc_g, float dscale, const unsigned* __restrict__ bound,
-                  unsigned long long* __restrict__ status) {
-    using S = Shape<float, ORD>;
-    constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ;
-    constexpr int E3 = EX * EY * EZ;
-    const unsigned NB = bg.NB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    long long* acc = reinterpret_cast<long long*>(smem_raw);
-    unsigned brick, beg, end;
-    if (!item_range(w, NB, blockIdx.x, &brick, &beg, &end)) return;
-    int x0, y0, z0;
-    brick_origin<S::BX, S::BY, S::BZ>(brick, bg, &x0, &y0, &z0);
-    const float sc = ldexpf(1.f, det_exponent(bound, dscale, w.P));
-    const unsigned n = end - beg;
-    __shared__ unsigned s_bucket[32];
-    __shared__ unsigned short s_order[kChunk];
-    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) acc[e] = 0;
-    bank_order<EY, EZ, kAdjThreads>(w, beg, n, x0, y0, z0, s_bucket, s_order);   // ends with a barrier
-    Rec<TR> rc_next;                                    // the thread's next record, requested ahead
-    if (threadIdx.x < n) rc_next = w.s_rec[beg + s_order[threadIdx.x]];
-    for (unsigned q = threadIdx.x; q < n; q += kAdjThreads) {
-        const Rec<TR> rc = rc_next;
-        if (q + kAdjThreads < n) rc_next = w.s_rec[beg + s_order[q + kAdjThreads]];
-        const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0;
-        const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
-        const int oz = (int)(rc.cell & 1023u) - z0;
-        const size_t idx = rc.idx;
-        if (!BS_CHECK_OK(ox >= 0 && ox < S::BX && oy >= 0 && oy < S::BY && oz >= 0 && oz < S::BZ &&
-                             (long long)idx < w.P,
-                         status + kStatusBounds))
-            continue;
         // the particle's cotangents, all requested before the reductions (loads cannot move across them)
         float cu[3], cg[9];
 #pragma unroll
         for (int c = 0; c < 3; ++c) cu[c] = g_u ? g_u[3 * idx + c] : 0.f;
-        if (GRAD) {
 #pragma unroll
-            for (int e = 0; e < 9; ++e) cg[e] = g_grad[9 * idx + e];
-        }
+        for (int e = 0; e < 9; ++e) cg[e] = GRAD ? g_grad[9 * idx + e] : 0.f;
         float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
-        bspline_weights<ORD, float>(rc.t[0], wx, dwx);
-        bspline_weights<ORD, float>(rc.t[1], wy, dwy);
-        bspline_weights<ORD, float>(rc.t[2], wz, dwz);
-        long long* base = acc + (ox * EY + oy) * EZ + oz;
-#pragma unroll 1
-        for (int c = 0; c < 3; ++c) {
-            // this component's cotangents (selects: c is a rolled loop counter)
-            const float gu = c == 0 ? cu[0] : (c == 1 ? cu[1] : cu[2]);
-            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-            if (GRAD) {
-                g0 = (c == 0 ? cg[0] : (c == 1 ? cg[3] : cg[6])) * dscale;
-                g1 = (c == 0 ? cg[1] : (c == 1 ? cg[4] : cg[7])) * dscale;
-                g2 = (c == 0 ? cg[2] : (c == 1 ? cg[5] : cg[8])) * dscale;
-            }
-            long long* tc = base + c * E3;
-#pragma unroll
-            for (int jx = 0; jx < ORD; ++jx) {
-                const float q0 = GRAD ? fmaf(g0, dwx[jx], gu * wx[jx]) : gu * wx[jx];
-                const float q1 = g1 * wx[jx], q2 = g2 * wx[jx];
-#pragma unroll
-                for (int jy = 0; jy < ORD; ++jy) {
-                    const float p0 = GRAD ? fmaf(q1, dwy[jy], q0 * wy[jy]) : q0 * wy[jy];
-                    const float p1 = q2 * wy[jy];
-                    long long* line = tc + (jx * EY + jy) * EZ;
-#pragma unroll
-                    for (int jz = 0; jz < ORD; ++jz) {
-                        const float v = GRAD ? fmaf(p1, dwz[jz], p0 * wz[jz]) : p0 * wz[jz];
-                        red_shared_s64(line + jz, __float2ll_rn(v * sc));
-                    }
-                }
-            }
+        bspline_weights<ORD, float>((float)rc.t[0], wx, dwx);
+        bspline_weights<ORD, float>((float)rc.t[1], wy, dwy);
+        bspline_weights<ORD, float>((float)rc.t[2], wz, dwz);
+        spread_particle<ORD, GRAD>(cu, cg, dscale, wx, dwx, wy, dwy, wz, dwz, (ox * EY + oy) * EZ + oz, E3, EY, EZ,
+                                   add);
+    };
+    // a thread's next record is requested while its current particle is spread
+    auto loop = [&](auto add) {
+        Rec<TR> rc_next;
+        if (threadIdx.x < np) rc_next = w.s_rec[beg + s_order[threadIdx.x]];
+        for (unsigned q = threadIdx.x; q < np; q += kFxThreads) {
+            const Rec<TR> rc = rc_next;
+            if (q + kFxThreads < np) rc_next = w.s_rec[beg + s_order[q + kFxThreads]];
+            particle(rc, add);
         }
+    };
+    if (sc.fixed) {
+        loop([&](int node, float v) {
+            const float h = fmaf(v, s1, kRintMagic);
+            const float r = fmaf(v, s1, -(h - kRintMagic));  // exact: v 2^e1 - hi
+            const float l = fmaf(r, s2, kRintMagic);
+            red_shared_u32(hi + node, __float_as_uint(h) - kRintMagicBits);
+            red_shared_u32(lo + node, __float_as_uint(l) - kRintMagicBits);
+        });
+    } else {
+        float* acc = reinterpret_cast<float*>(hi);
+        loop([&](int node, float v) { red_shared_f32(acc + node, v); });
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 3 * E3; e += kAdjThreads) {
-        const long long v = acc[e];
-        if (v != 0) {
-            const int c = e / E3, r = e - c * E3;
-            const int ix = r / (EY * EZ), iy = (r / EZ) % EY, iz = r % EZ;
-            atomicAdd(reinterpret_cast<unsigned long long*>(
-                          &acc_g[(((size_t)c * N + wrap_index(x0 + ix, N)) * N + wrap_index(y0 + iy, N)) * N +
-                                 wrap_index(z0 + iz, N)]),
-                      (unsigned long long)v);
+    auto dst_row = [&](int row, auto* base) {
+        const int c = row / (EX * EY), ix = (row / EY) % EX, iy = row % EY;
+        return base + (((size_t)c * N + wrap_index(x0 + xs + ix, N)) * N + wrap_index(y0 + iy, N)) * N;
+    };
+    if (DET && sc.fixed) {
+        // the exact sums, rint(v 2^Ef) each, into the 64-bit accumulator
+        for (int e = threadIdx.x; e < 3 * E3; e += kFxThreads) {
+            const long long f = ((long long)(int)hi[e] << sc.e2) + (int)lo[e];
+            if (f != 0) {
+                const int row = e / EZ, iz = e - row * EZ;
+                atomicAdd(reinterpret_cast<unsigned long long*>(dst_row(row, acc_g) + wrap_index(z0 + iz, N)),
+                          (unsigned long long)f);
+            }
+        }
+        return;
+    }
+    // into g_coef: per tile row the brick's BZ nodes as BZ/4 aligned 16-byte vector atomics (z0 and N are
+    // multiples of 4, so 4 consecutive z stay inside one period), then the EZ - BZ halo nodes one by one
+    const float inv1 = ldexpf(1.f, -sc.e1), inv12 = ldexpf(1.f, -(sc.e1 + sc.e2));
+    auto value = [&](int node) {
+        return sc.fixed ? fmaf((float)(int)hi[node], inv1, (float)(int)lo[node] * inv12) : __uint_as_float(hi[node]);
+    };
+    constexpr int U = BZ / 4 + (EZ - BZ);
+    for (int e = threadIdx.x; e < 3 * EX * EY * U; e += kFxThreads) {
+        const int row = e / U, k = e - row * U;
+        float* dst = dst_row(row, g_coef);
+        if (k < BZ / 4) {
+            const int nd = row * EZ + 4 * k;
+            const float4 v = make_float4(value(nd), value(nd + 1), value(nd + 2), value(nd + 3));
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+                atomicAdd(reinterpret_cast<float4*>(dst + wrap_index(z0 + 4 * k, N)), v);
+        } else {
+            const int iz = BZ + (k - BZ / 4);
+            const float v = value(row * EZ + iz);
+            if (v != 0.f) atomicAdd(dst + wrap_index(z0 + iz, N), v);
         }
     }
 }
 
-// g_coef += acc_g 2^-e, one thread per node (the one rounding of each node's exact sum).
+// g_coef += acc_g 2^-Ef, one thread per node (the one rounding of each node's exact sum).
 static __global__ void det_finish_kernel(const long long* __restrict__ acc_g, float* __restrict__ g_coef, long long n,
-                                  float dscale, long long P, const unsigned* __restrict__ bound) {
-    const double inv = ldexp(1.0, -det_exponent(bound, dscale, P));
+                                         float bound_factor, long long P, const unsigned* __restrict__ bound) {
+    const FxScale sc = fx_det_scale(*bound, bound_factor, P);
+    const double inv = ldexp(1.0, -(sc.e1 + sc.e2));
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         g_coef[i] += (float)((double)acc_g[i] * inv);
 }
@@ -599,37 +651,50 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
     const A dscale = (A)((double)p->N / p->L);
     int rc;
     if constexpr (sizeof(A) == 4) {
-        if (g_coef && p->deterministic) {
-            // fixed-point accumulator [3][N][N][N] int64, then the bound word
-            const long long nodes = 3LL * p->N * p->N * p->N;
-            long long* acc_g = reinterpret_cast<long long*>(p->det.ptr);
-            unsigned* bound = reinterpret_cast<unsigned*>(acc_g + nodes);
-            cudaError_t e = cudaMemsetAsync(acc_g, 0, sizeof(long long) * nodes + 16, p->stream);
-            if (e != cudaSuccess) return set_cuda_error(e);
-            const long long want = (w.P + 255) / 256;
-            const unsigned blocks = (unsigned)std::max(1LL, std::min(want, 8LL * p->sms));
-            if (g_grad)
-                cotangent_bound_kernel<true><<<blocks, 256, 0, p->stream>>>((const float*)g_u, (const float*)g_grad,
-                                                                            w.P, bound);
-            else
-                cotangent_bound_kernel<false><<<blocks, 256, 0, p->stream>>>((const float*)g_u, nullptr, w.P, bound);
-            const size_t sm = sizeof(long long) * 3 * (size_t)Shape<float, ORD>::EX * Shape<float, ORD>::EY *
-                              Shape<float, ORD>::EZ;
-            auto k = g_grad ? spread_det_kernel<ORD, TR, true> : spread_det_kernel<ORD, TR, false>;
-            if ((rc = set_smem(k, sm))) return rc;
-            k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, g, w, (const float*)g_u, (const float*)g_grad,
-                                                                acc_g, (float)dscale, bound, p->d_status);
-            const unsigned fb = (unsigned)std::max(1LL, std::min((nodes + 255) / 256, 16LL * p->sms));
-            det_finish_kernel<<<fb, 256, 0, p->stream>>>(acc_g, (float*)g_coef, nodes, (float)dscale, w.P, bound);
+        if (g_coef) {
+            const size_t sm = fx_tile_bytes<ORD>();
+            const unsigned grid = (unsigned)(items * FxShape<ORD>::XP);
+            const float factor = g_grad ? 1.f + 3.f * (float)dscale : 1.f;   // |contribution| <= G factor
+            if (p->deterministic) {
+                // fixed-point accumulator [3][N][N][N] int64, then the bound word
+                const long long nodes = 3LL * p->N * p->N * p->N;
+                long long* acc_g = reinterpret_cast<long long*>(p->det.ptr);
+                unsigned* bound = reinterpret_cast<unsigned*>(acc_g + nodes);
+                cudaError_t e = cudaMemsetAsync(acc_g, 0, sizeof(long long) * nodes + 16, p->stream);
+                if (e != cudaSuccess) return set_cuda_error(e);
+                const long long want = (w.P + 255) / 256;
+                const unsigned blocks = (unsigned)std::max(1LL, std::min(want, 8LL * p->sms));
+                if (g_grad)
+                    cotangent_bound_kernel<true><<<blocks, 256, 0, p->stream>>>((const float*)g_u,
+                                                                                (const float*)g_grad, w.P, bound);
+                else
+                    cotangent_bound_kernel<false><<<blocks, 256, 0, p->stream>>>((const float*)g_u, nullptr, w.P,
+                                                                                 bound);
+                auto k = g_grad ? spread_fx_kernel<ORD, TR, true, true> : spread_fx_kernel<ORD, TR, false, true>;
+                if ((rc = set_smem(k, sm))) return rc;
+                k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, (const float*)g_u, (const float*)g_grad,
+                                                       (float*)g_coef, acc_g, bound, (float)dscale, factor,
+                                                       p->d_status);
+                const unsigned fb = (unsigned)std::max(1LL, std::min((nodes + 255) / 256, 16LL * p->sms));
+                det_finish_kernel<<<fb, 256, 0, p->stream>>>(acc_g, (float*)g_coef, nodes, factor, w.P, bound);
+            } else {
+                auto k = g_grad ? spread_fx_kernel<ORD, TR, true, false> : spread_fx_kernel<ORD, TR, false, false>;
+                if ((rc = set_smem(k, sm))) return rc;
+                k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, (const float*)g_u, (const float*)g_grad,
+                                                       (float*)g_coef, nullptr, nullptr, (float)dscale, factor,
+                                                       p->d_status);
+            }
             g_coef = nullptr;                               // done
         }
     }
-    if (g_coef) {
-        const size_t sm = acc_bytes<ORD, A>();
-        auto k = g_grad ? spread_kernel<ORD, TR, A, true> : spread_kernel<ORD, TR, A, false>;
-        if ((rc = set_smem(k, sm))) return rc;
-        k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, g, w, (const A*)g_u, (const A*)g_grad,
-                                                            (A*)g_coef, dscale, p->d_status);
+    if constexpr (sizeof(A) == 8) {
+        if (g_coef) {
+            const size_t sm = acc_bytes<ORD>();
+            auto k = g_grad ? spread_kernel<ORD, TR, true> : spread_kernel<ORD, TR, false>;
+            if ((rc = set_smem(k, sm))) return rc;
+            k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>(p->N, g, w, (const double*)g_u, (const double*)g_grad,
+                                                                (double*)g_coef, (double)dscale, p->d_status);
+        }
     }
     if (g_x) {
         const size_t sm = tile_bytes<ORD, CT>() + 128;   // room to align the tile to 128 bytes

@@ -111,6 +111,50 @@ def test_spread_f32(B, order, dtype):
     assert normwise(gc.cpu().numpy(), O.spread(x, gu, gg, N, order)) < TOL32_SPREAD
 
 
+@pytest.mark.parametrize("order", [2, 4, 5, 6, 8])
+def test_spread_f32_dense_cell_and_scale(B, order):
+    """FP32 spreads sum each work item in two-word fixed point at scales taken from the item's largest
+    cotangent: every particle in one cell (items of 2048 particles, every node summing up to 2048 terms)
+    stays within the FP32 tolerance of the oracle, and cotangents scaled by 2^40 or 2^-40 give the
+    scaled sums (the scales follow the cotangents)."""
+    N, P = 32, 12000
+    rng = np.random.default_rng(order)
+    h = L / N
+    x = np.concatenate([(np.array([7, 20, 9]) + 0.5) * h + 0.2 * h * rng.standard_normal((P // 2, 3)),
+                        rng.uniform(0, L, size=(P - P // 2, 3))])
+    plan = B.Plan(N, order, "f32")
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=order + 500)
+    xt = _dev(x, torch.float64)
+    _, _, gc = plan.spread_adjoint(xt, gu_t, gg_t, u_hat_grad=False)
+    ref = O.spread(x, gu, gg, N, order)
+    assert normwise(gc.cpu().numpy(), ref) < TOL32_SPREAD
+    for k in (40, -40):
+        _, _, gk = plan.spread_adjoint(xt, gu_t * 2.0 ** k, gg_t * 2.0 ** k, u_hat_grad=False)
+        assert torch.isfinite(gk).all()
+        assert normwise(gk.cpu().numpy() * 2.0 ** -k, gc.cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_spread_f32_nonfinite_cotangent(B, det):
+    """A NaN cotangent reaches exactly the nodes of that particle's stencil in its component; every other
+    node keeps the oracle's sums without it (both modes: a non-finite cotangent falls back to FP32 sums)."""
+    N, order, P = 32, 4, 5000
+    x = synth.uniform_particles(P, seed=21)
+    plan = B.Plan(N, order, "f32")
+    plan.set_deterministic(det)
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=22)
+    gu_t[17, 1] = float("nan")
+    _, _, gc = plan.spread_adjoint(_dev(x, torch.float64), gu_t, gg_t, u_hat_grad=False)
+    gc = gc.cpu().numpy()
+    one = np.zeros_like(gu)
+    one[17, 1] = 1.0
+    hit = O.spread(x[17:18], one[17:18], None, N, order) != 0
+    assert np.isnan(gc[hit]).all() and np.isfinite(gc[~hit]).all()
+    gu[17, 1] = 0.0
+    ref = O.spread(x, gu, gg, N, order)
+    assert np.abs(gc[~hit] - ref[~hit]).max() < TOL32_SPREAD * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("order,dtype,with_grad", [(4, "f32", True), (6, "bf16", True), (2, "f32", False),
                                                     (8, "f32", True)])
 def test_deterministic_spread_bit_identical_and_oracle(B, order, dtype, with_grad):
