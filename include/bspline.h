@@ -233,7 +233,10 @@ int bspline_eval(bspline_plan_t plan, const void* u_hat, void* coeffs, const dou
  * calls, unless bspline_plan_set_deterministic turned on exact sums over all
  * items.  Items holding a non-finite cotangent are summed with FP32 atomics,
  * so NaN and infinities reach the nodes of those particles' stencils.
- * FP64 plans sum with FP64 atomics.  Uses the plan's particle and transform
+ * FP64 plans sum with FP64 atomics.  FP32 and BF16 plans keep a copy of the
+ * cotangents in the particles' sorted order (64 bytes a particle, grown on
+ * first use), which the spread and the position gradients read instead of
+ * gathering them from the original indices.  Uses the plan's particle and transform
  * workspaces.  BSPLINE_ERR_INVALID_ARG for a missing required pointer, a bad
  * alignment or P outside [0, 2^31). */
 int bspline_spread_adjoint(bspline_plan_t plan, const void* coeffs, const double* x, int64_t P,

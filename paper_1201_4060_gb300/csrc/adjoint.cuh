@@ -312,9 +312,9 @@ __device__ __forceinline__ void spread_particle(const float (&cu)[3], const floa
 // the tile added to acc_g; otherwise the item's own scales and the tile added to g_coef.
 template <int ORD, typename TR, bool GRAD, bool DET>
 __global__ void __launch_bounds__(kFxThreads, 2)
-spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, const float* __restrict__ g_grad,
-                 float* __restrict__ g_coef, long long* __restrict__ acc_g, const unsigned* __restrict__ bound,
-                 float dscale, float bound_factor, unsigned long long* __restrict__ status) {
+spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float4* __restrict__ cot, float* __restrict__ g_coef,
+                 long long* __restrict__ acc_g, const unsigned* __restrict__ bound, float dscale, float bound_factor,
+                 unsigned long long* __restrict__ status) {
     using F = FxShape<ORD>;
     constexpr int EX = F::EX, EY = F::EY, EZ = F::EZ, E3 = F::E3, BZ = F::BZ, XW = F::XW;
     const unsigned NB = bg.NB;
@@ -355,15 +355,13 @@ spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, c
             if (ok && ox / XW == part) {
                 const unsigned r = (unsigned)(((ox - part * XW) * EY + oy) * EZ + oz) & 31u;
                 packed[k] = (atomicAdd(&s_bucket[r], 1u) << 5) | r;
-                if (!DET) {
-                    if (g_u) {
+                if (!DET && cot) {
+                    const float4* cp4 = cot + 4 * (size_t)(beg + i);
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) gbits = max(gbits, __float_as_uint(fabsf(g_u[3 * idx + c])));
-                    }
-                    if (GRAD) {
-#pragma unroll
-                        for (int e = 0; e < 9; ++e)
-                            gbits = max(gbits, __float_as_uint(fabsf(g_grad[9 * idx + e])));
+                    for (int k4 = 0; k4 < 3; ++k4) {
+                        const float4 v = cp4[k4];
+                        gbits = max(max(gbits, __float_as_uint(fabsf(v.x))), __float_as_uint(fabsf(v.y)));
+                        gbits = max(max(gbits, __float_as_uint(fabsf(v.z))), __float_as_uint(fabsf(v.w)));
                     }
                 }
             }
@@ -396,17 +394,16 @@ spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, c
     const FxScale sc = DET ? fx_det_scale(gmax, bound_factor, w.P) : fx_item_scale(gmax, bound_factor, np);
     const float s1 = ldexpf(1.f, sc.e1), s2 = ldexpf(1.f, sc.e2);
     const int xs = part * XW;
-    auto particle = [&](const Rec<TR>& rc, auto add) {
+    auto particle = [&](const Rec<TR>& rc, unsigned slot, auto add) {
         const int ox = (int)(rc.cell >> (2 * kAnchorBits)) - x0 - xs;
         const int oy = (int)((rc.cell >> kAnchorBits) & 1023u) - y0;
         const int oz = (int)(rc.cell & 1023u) - z0;
-        const size_t idx = rc.idx;
-        // the particle's cotangents, all requested before the reductions (loads cannot move across them)
-        float cu[3], cg[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) cu[c] = g_u ? g_u[3 * idx + c] : 0.f;
-#pragma unroll
-        for (int e = 0; e < 9; ++e) cg[e] = GRAD ? g_grad[9 * idx + e] : 0.f;
+        // the particle's cotangents from its sorted slot, all requested before the reductions (loads cannot
+        // move across them)
+        const float4* cp4 = cot + 4 * (size_t)slot;
+        const float4 v0 = cp4[0], v1 = cp4[1], v2 = cp4[2];
+        const float cu[3] = {v0.x, v0.y, v0.z};
+        const float cg[9] = {v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
         float wx[ORD], dwx[ORD], wy[ORD], dwy[ORD], wz[ORD], dwz[ORD];
         bspline_weights<ORD, float>((float)rc.t[0], wx, dwx);
         bspline_weights<ORD, float>((float)rc.t[1], wy, dwy);
@@ -420,8 +417,9 @@ spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float* __restrict__ g_u, c
         if (threadIdx.x < np) rc_next = w.s_rec[beg + s_order[threadIdx.x]];
         for (unsigned q = threadIdx.x; q < np; q += kFxThreads) {
             const Rec<TR> rc = rc_next;
+            const unsigned slot = beg + s_order[q];
             if (q + kFxThreads < np) rc_next = w.s_rec[beg + s_order[q + kFxThreads]];
-            particle(rc, add);
+            particle(rc, slot, add);
         }
     };
     if (sc.fixed) {
@@ -491,6 +489,7 @@ template <int ORD, typename CT, typename TR, bool HESS>
 __global__ void __launch_bounds__(kAdjThreads)
 gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
           const typename TileT<CT>::T* __restrict__ g_u, const typename TileT<CT>::T* __restrict__ g_grad,
+          const float4* __restrict__ cot,
           double* __restrict__ g_x, typename TileT<CT>::T dscale, const __grid_constant__ CUtensorMap tmap,
           int use_tma, unsigned long long* __restrict__ status) {
     using A = typename TileT<CT>::T;
@@ -568,13 +567,22 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
                              (long long)idx < w.P,
                          status + kStatusBounds))
             continue;
-        // the particle's cotangents, requested before the contractions that they multiply
+        // the particle's cotangents (FP32: from its sorted slot), requested before the contractions that
+        // they multiply
         A gu[3], gg[9];
+        if (sizeof(A) == 4 && cot) {
+            const float4* cp4 = cot + 4 * (size_t)(beg + (kBucket ? (unsigned)s_order[q] : q));
+            const float4 v0 = cp4[0], v1 = cp4[1], v2 = cp4[2];
+            gu[0] = v0.x; gu[1] = v0.y; gu[2] = v0.z;
+            gg[0] = v0.w; gg[1] = v1.x; gg[2] = v1.y; gg[3] = v1.z; gg[4] = v1.w;
+            gg[5] = v2.x; gg[6] = v2.y; gg[7] = v2.z; gg[8] = v2.w;
+        } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) gu[c] = g_u ? g_u[3 * idx + c] : A(0);
-        if (HESS) {
+            for (int c = 0; c < 3; ++c) gu[c] = g_u ? g_u[3 * idx + c] : A(0);
+            if (HESS) {
 #pragma unroll
-            for (int e = 0; e < 9; ++e) gg[e] = g_grad[9 * idx + e];
+                for (int e = 0; e < 9; ++e) gg[e] = g_grad[9 * idx + e];
+            }
         }
         A wx[ORD], dwx[ORD], d2wx[ORD], wy[ORD], dwy[ORD], d2wy[ORD], wz[ORD], dwz[ORD], d2wz[ORD];
         bspline_weights2<ORD, A>((A)rc.t[0], wx, dwx, d2wx);
@@ -646,11 +654,12 @@ gx_kernel(const CT* __restrict__ coef, int N, BrickGrid bg, Ws<TR> w,
 // for one order and coefficient type.  items = upper bound of work items.
 template <int ORD, typename CT, typename TR>
 int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, long long items,
-                const void* g_u, const void* g_grad, void* g_coef, double* g_x) {
+                const void* g_u, const void* g_grad, void* g_coef, double* g_x, const float4* cot) {
     using A = typename TileT<CT>::T;
     const A dscale = (A)((double)p->N / p->L);
     int rc;
     if constexpr (sizeof(A) == 4) {
+        if (g_coef && !cot) g_coef = nullptr;           // no cotangents: nothing to add
         if (g_coef) {
             const size_t sm = fx_tile_bytes<ORD>();
             const unsigned grid = (unsigned)(items * FxShape<ORD>::XP);
@@ -672,17 +681,15 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
                                                                                  bound);
                 auto k = g_grad ? spread_fx_kernel<ORD, TR, true, true> : spread_fx_kernel<ORD, TR, false, true>;
                 if ((rc = set_smem(k, sm))) return rc;
-                k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, (const float*)g_u, (const float*)g_grad,
-                                                       (float*)g_coef, acc_g, bound, (float)dscale, factor,
-                                                       p->d_status);
+                k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, cot, (float*)g_coef, acc_g, bound, (float)dscale,
+                                                       factor, p->d_status);
                 const unsigned fb = (unsigned)std::max(1LL, std::min((nodes + 255) / 256, 16LL * p->sms));
                 det_finish_kernel<<<fb, 256, 0, p->stream>>>(acc_g, (float*)g_coef, nodes, factor, w.P, bound);
             } else {
                 auto k = g_grad ? spread_fx_kernel<ORD, TR, true, false> : spread_fx_kernel<ORD, TR, false, false>;
                 if ((rc = set_smem(k, sm))) return rc;
-                k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, (const float*)g_u, (const float*)g_grad,
-                                                       (float*)g_coef, nullptr, nullptr, (float)dscale, factor,
-                                                       p->d_status);
+                k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, cot, (float*)g_coef, nullptr, nullptr,
+                                                       (float)dscale, factor, p->d_status);
             }
             g_coef = nullptr;                               // done
         }
@@ -708,8 +715,8 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
             use_tma = encode_coef_tmap(&tmap, coeffs, p->N, S::PZ, S::EY, S::EX) == BSPLINE_OK ? kTmaOn : 0;
         if (use_tma && (p->test_hooks & BSPLINE_TEST_SKIP_TMA_ISSUE)) use_tma = kTmaArmOnly;
         k<<<(unsigned)items, kAdjThreads, sm, p->stream>>>((const CT*)coeffs, p->N, g, w, (const A*)g_u,
-                                                            (const A*)g_grad, g_x, dscale, tmap, use_tma,
-                                                            p->d_status);
+                                                            (const A*)g_grad, sizeof(A) == 4 ? cot : nullptr, g_x,
+                                                            dscale, tmap, use_tma, p->d_status);
     }
     return BSPLINE_OK;
 }
@@ -719,10 +726,11 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
 #define BS_ADJOINT_EXTERN(ORD, CT, TR)                                                                          \
     extern template int adjoint_impl::run_adjoint<ORD, CT, TR>(bspline_plan_s*, const void*,                   \
                                                                 gather_impl::Ws<TR>, BrickGrid, long long,       \
-                                                                const void*, const void*, void*, double*);
+                                                                const void*, const void*, void*, double*,        \
+                                                                const float4*);
 #define BS_ADJOINT_INSTANTIATE(ORD, CT, TR)                                                                     \
     template int adjoint_impl::run_adjoint<ORD, CT, TR>(bspline_plan_s*, const void*, gather_impl::Ws<TR>,      \
                                                          BrickGrid, long long, const void*, const void*,        \
-                                                         void*, double*);
+                                                         void*, double*, const float4*);
 
 }  // namespace bs

@@ -230,6 +230,7 @@ void free_plan(bspline_plan_s* p) {
     p->work.release();
     p->pws.release();
     p->det.release();
+    p->cot.release();
     if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->ev_start) cudaEventDestroy(p->ev_start);

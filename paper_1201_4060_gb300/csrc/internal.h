@@ -118,6 +118,7 @@ struct bspline_plan_s {
     int deterministic = 0;  // bspline_plan_set_deterministic: fixed-point spread of the adjoint
     int band = 0;           // bspline_plan_set_band: modes beyond |k_i| <= band taken as zero (0: none)
     bs::DeviceBuffer det;   // its accumulator [3][N][N][N] int64 and the cotangent bound
+    bs::DeviceBuffer cot;   // adjoint, FP32 types: the cotangents in sorted order, [P][16] floats
     // Buffers, second stream and events of bspline_run_host (and the second
     // stream of bspline_eval); the copy stream and its events feed the
     // host-to-device copies of bspline_run_host.

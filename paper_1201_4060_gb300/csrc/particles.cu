@@ -246,11 +246,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
 // of its brick.  Invalid positions get NaN outputs.  SORTED: nothing to do
 // unless the count pass found the order broken.  PERM (bspline_sort_order):
 // every particle, invalid ones included (bin NB, last), gets a slot, and only
-// its original index is written there, to perm.
+// its original index is written there, to perm.  cot (the adjoint of FP32
+// types): each placed particle's cotangents g_u (or zeros) and g_grad (or
+// zeros) also go to its slot, 16 floats (64 bytes: two whole sectors) a slot,
+// so that the adjoint kernels read them in sorted order.
 template <typename TR, typename OT, bool SORTED = false, bool PERM = false>
 __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                                BrickGrid g, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
-                               int aggregate, unsigned long long* __restrict__ status, int* __restrict__ perm = nullptr) {
+                               int aggregate, unsigned long long* __restrict__ status, int* __restrict__ perm = nullptr,
+                               const float* __restrict__ cu = nullptr, const float* __restrict__ cg = nullptr,
+                               float4* __restrict__ cot = nullptr) {
     const unsigned NB = g.NB;
     if constexpr (SORTED) {
         if (*w.unsorted == 0u) return;
@@ -295,6 +300,18 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
             r.idx = (unsigned)p;
             if constexpr (sizeof(TR) == 4) r.pad[0] = r.pad[1] = r.pad[2] = 0u;
             w.s_rec[d] = r;                             // one whole 32-byte sector
+            if (cot) {
+                float v[12];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[i] = cu ? cu[3 * p + i] : 0.f;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) v[3 + i] = cg ? cg[9 * p + i] : 0.f;
+                float4* dst = cot + 4 * (size_t)d;
+                dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+                dst[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
     }
 }
@@ -438,16 +455,16 @@ int run_interp_ws(bspline_plan_s* p, void* ws, unsigned long long* status, const
 
 template <typename CT, typename TR>
 int adjoint_order(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, long long items,
-                  const void* g_u, const void* g_grad, void* g_coef, double* g_x) {
+                  const void* g_u, const void* g_grad, void* g_coef, double* g_x, const float4* cot) {
     using adjoint_impl::run_adjoint;
     switch (p->order) {
-        case 2: return run_adjoint<2, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
-        case 3: return run_adjoint<3, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
-        case 4: return run_adjoint<4, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
-        case 5: return run_adjoint<5, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
-        case 6: return run_adjoint<6, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
-        case 7: return run_adjoint<7, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
-        case 8: return run_adjoint<8, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x);
+        case 2: return run_adjoint<2, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
+        case 3: return run_adjoint<3, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
+        case 4: return run_adjoint<4, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
+        case 5: return run_adjoint<5, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
+        case 6: return run_adjoint<6, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
+        case 7: return run_adjoint<7, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
+        case 8: return run_adjoint<8, CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, g_x, cot);
     }
     return BSPLINE_ERR_UNSUPPORTED_ORDER;
 }
@@ -465,6 +482,13 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     int rc = p->pws.grow(need);
     if (rc) return rc;
     carve<TR>(&w, p->pws.ptr, NB, P);
+    // FP32 types: the placement pass also copies each particle's cotangents to its sorted slot, which the
+    // spread and the position gradients then read in order instead of gathering them from random indices
+    float4* cot = nullptr;
+    if (sizeof(TR) == 4 && (g_u || g_grad) && (g_coef || g_x)) {
+        if ((rc = p->cot.grow(sizeof(float4) * 4 * (size_t)P))) return rc;
+        cot = reinterpret_cast<float4*>(p->cot.ptr);
+    }
     cudaStream_t st = p->stream;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(unsigned) * (NB + 2), st)) != cudaSuccess) return set_cuda_error(e);
@@ -483,7 +507,8 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
         scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, g_x, nullptr, NB < kAggregateBricks,
-                                                                     p->d_status);
+                                                                     p->d_status, nullptr, (const float*)g_u,
+                                                                     (const float*)g_grad, cot);
     }
     const long long items = (long long)NB + (P + kChunk - 1) / kChunk;
     if (g_coef && p->deterministic && sizeof(TR) == 4) {
@@ -492,12 +517,12 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     if (g_coef) {
         StageTimer tm(p, BSPLINE_STAGE_SPREAD);
-        rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, nullptr);
+        rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, g_coef, nullptr, cot);
         if (rc) return rc;
     }
     if (g_x) {
         StageTimer tm(p, BSPLINE_STAGE_GRAD_X);
-        rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, nullptr, g_x);
+        rc = adjoint_order<CT, TR>(p, coeffs, w, g, items, g_u, g_grad, nullptr, g_x, cot);
         if (rc) return rc;
     }
     return set_cuda_error(cudaGetLastError());
