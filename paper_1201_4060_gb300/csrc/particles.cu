@@ -249,7 +249,9 @@ __global__ void __launch_bounds__(1024) scan_kernel(const unsigned* __restrict__
 // its original index is written there, to perm.  cot (the adjoint of FP32
 // types): each placed particle's cotangents g_u (or zeros) and g_grad (or
 // zeros) also go to its slot, 16 floats (64 bytes: two whole sectors) a slot,
-// so that the adjoint kernels read them in sorted order.
+// so that the adjoint kernels read them in sorted order; a warp reads its 32
+// particles' cotangents as whole lines into 12 * 32 floats of dynamic shared
+// memory (the launch gives 12 * 32 * 4 bytes per warp).
 template <typename TR, typename OT, bool SORTED = false, bool PERM = false>
 __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N, double scale, int order,
                                BrickGrid g, Ws<TR> w, OT* __restrict__ out_u, OT* __restrict__ out_grad,
@@ -272,6 +274,8 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
     }
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long lane = threadIdx.x & 31;
+    extern __shared__ float s_cot_stage[];
+    float* sw = s_cot_stage + (threadIdx.x >> 5) * (12 * 32);
     for (long long pw = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; pw < P; pw += stride) {
         const long long p = pw + lane;
         Rec<TR> r;
@@ -289,6 +293,13 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
             }
         }
         const bool place = p < P && k < NB;
+        if (cot) {                                      // the warp's cotangents, coalesced
+            const int nq = (int)min(32LL, P - pw);
+            __syncwarp();                               // the previous iteration's reads are done
+            for (int i = (int)lane; i < 3 * nq; i += 32) sw[i] = cu ? cu[3 * pw + i] : 0.f;
+            for (int i = (int)lane; i < 9 * nq; i += 32) sw[96 + i] = cg ? cg[9 * pw + i] : 0.f;
+            __syncwarp();
+        }
         unsigned d = 0;
         if (aggregate) {
             const unsigned active = __ballot_sync(0xffffffffu, place);
@@ -303,9 +314,9 @@ __global__ void scatter_kernel(const double* __restrict__ x, long long P, int N,
             if (cot) {
                 float v[12];
 #pragma unroll
-                for (int i = 0; i < 3; ++i) v[i] = cu ? cu[3 * p + i] : 0.f;
+                for (int i = 0; i < 3; ++i) v[i] = sw[3 * lane + i];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) v[3 + i] = cg ? cg[9 * p + i] : 0.f;
+                for (int i = 0; i < 9; ++i) v[3 + i] = sw[96 + 9 * lane + i];
                 float4* dst = cot + 4 * (size_t)d;
                 dst[0] = make_float4(v[0], v[1], v[2], v[3]);
                 dst[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -506,7 +517,8 @@ int run_adjoint_particles(bspline_plan_s* p, const void* coeffs, const double* x
     }
     {
         StageTimer tm(p, BSPLINE_STAGE_SCATTER);
-        scatter_kernel<TR, double><<<grid_for(P, 256), 256, 0, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, g_x, nullptr, NB < kAggregateBricks,
+        const size_t cot_smem = cot ? sizeof(float) * 12 * 256 : 0;   // 12 * 32 floats per warp
+        scatter_kernel<TR, double><<<grid_for(P, 256), 256, cot_smem, st>>>(x, P, p->N, (double)p->N / p->L, p->order, g, w, g_x, nullptr, NB < kAggregateBricks,
                                                                      p->d_status, nullptr, (const float*)g_u,
                                                                      (const float*)g_grad, cot);
     }
