@@ -186,7 +186,7 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const double* __restrict__ g_u, con
 // contributions: with G the largest cotangent magnitude and |w|, |w'| <= 1 for
 // a cardinal B-spline, |v| <= Gb = G (1 + 3 N/L); rint is FP32 addition of
 // 1.5 2^23, exact while |x| < 2^22, and no node's sums of at most n terms may
-// leave 2^30.  Per work item (G and n of the item's particles):
+// leave 2^30.  Per CTA (G and n of the particles of its part of a work item):
 //     e1 = min(21 - ceil(log2 Gb), 29 - ceil(log2 (n Gb)), 100),  e2 = min(22, 30 - ceil(log2 (n + 1))),
 // about 40 bits below the largest contribution, then one conversion to FP32
 // and FP32 atomics into g_coef.  Deterministic mode (one scale for every
