@@ -240,6 +240,25 @@ def test_position_gradient_f32(B, order, dtype):
     assert err < (TOL32_GX if dtype == "f32" else 5e-2)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_f32_adjoint_with_one_cotangent_absent(B, dtype):
+    """FP32/BF16 plans copy the cotangents to the sorted order with zeros for an absent g_u or g_grad: the
+    spread and the position gradient with either one missing match the oracle with that one zero."""
+    N, order, P = 32, 4, 4000
+    half = synth.kolmogorov_field(N, seed=11).dense()
+    x = synth.clustered_particles(P, seed=12)
+    plan = B.Plan(N, order, dtype)
+    coef = plan.coeffs(_dev(half, torch.complex64))
+    c64 = coef.double().cpu().numpy()
+    gu_t, gg_t, gu, gg = _cot(plan, P, seed=13)
+    xt = _dev(x, torch.float64)
+    for a_t, b_t, a, b in ((gu_t, None, gu, np.zeros_like(gg)), (None, gg_t, np.zeros_like(gu), gg)):
+        _, gx, gc = plan.spread_adjoint(xt, a_t, b_t, coef=coef, u_hat_grad=False)
+        assert normwise(gc.cpu().numpy(), O.spread(x, a, b, N, order)) < TOL32_SPREAD
+        tol = TOL32_GX if dtype == "f32" else 5e-2
+        assert normwise(gx.cpu().numpy(), O.position_gradient(c64, x, a, b, order)) < tol
+
+
 @pytest.mark.parametrize("order", [4, 6, 8])
 def test_position_gradient_tma_and_cp_async_staging_agree(B, order):
     """The position gradient stages FP32 bricks away from the periodic seams by TMA tensor copies and
