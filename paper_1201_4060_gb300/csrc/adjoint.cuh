@@ -196,7 +196,7 @@ spread_kernel(int N, BrickGrid bg, Ws<TR> w, const double* __restrict__ g_u, con
 // and each node's hi 2^e2 + lo goes to a 64-bit fixed-point accumulator with
 // integer atomics: every contribution is rounded once, rint(v 2^Ef), and all
 // sums are exact, so neither particle order nor atomics order changes a bit;
-// one FP64 multiply by 2^-Ef and one FP32 add take the sums into g_coef.
+// one rounding to FP32 (times 2^-Ef) and one FP32 add take the sums into g_coef.
 // Non-finite cotangents fall back to FP32 reductions (NaN and infinities reach
 // g_coef).  The two-word tile is split along x into XP parts, one CTA each,
 // so that two CTAs share an SM.
@@ -474,13 +474,22 @@ spread_fx_kernel(int N, BrickGrid bg, Ws<TR> w, const float4* __restrict__ cot, 
     }
 }
 
-// g_coef += acc_g 2^-Ef, one thread per node (the one rounding of each node's exact sum).
+// g_coef += acc_g 2^-Ef, two nodes a thread (n is even: 3 N^3): each exact sum rounded once to FP32
+// (the integer-to-float conversion; the power-of-two scale is exact), then added.  No FP64 arithmetic.
 static __global__ void det_finish_kernel(const long long* __restrict__ acc_g, float* __restrict__ g_coef, long long n,
                                          float bound_factor, long long P, const unsigned* __restrict__ bound) {
     const FxScale sc = fx_det_scale(*bound, bound_factor, P);
-    const double inv = ldexp(1.0, -(sc.e1 + sc.e2));
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        g_coef[i] += (float)((double)acc_g[i] * inv);
+    const float inv = ldexpf(1.f, -(sc.e1 + sc.e2));
+    const longlong2* a2 = reinterpret_cast<const longlong2*>(acc_g);
+    float2* g2 = reinterpret_cast<float2*>(g_coef);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2;
+         i += (long long)gridDim.x * blockDim.x) {
+        const longlong2 a = a2[i];
+        float2 g = g2[i];
+        g.x += __ll2float_rn(a.x) * inv;
+        g.y += __ll2float_rn(a.y) * inv;
+        g2[i] = g;
+    }
 }
 
 // Position gradient: one thread per particle of the work item, coefficients
@@ -683,7 +692,7 @@ int run_adjoint(bspline_plan_s* p, const void* coeffs, Ws<TR> w, BrickGrid g, lo
                 if ((rc = set_smem(k, sm))) return rc;
                 k<<<grid, kFxThreads, sm, p->stream>>>(p->N, g, w, cot, (float*)g_coef, acc_g, bound, (float)dscale,
                                                        factor, p->d_status);
-                const unsigned fb = (unsigned)std::max(1LL, std::min((nodes + 255) / 256, 16LL * p->sms));
+                const unsigned fb = (unsigned)std::max(1LL, std::min((nodes / 2 + 255) / 256, 16LL * p->sms));
                 det_finish_kernel<<<fb, 256, 0, p->stream>>>(acc_g, (float*)g_coef, nodes, factor, w.P, bound);
             } else {
                 auto k = g_grad ? spread_fx_kernel<ORD, TR, true, false> : spread_fx_kernel<ORD, TR, false, false>;
