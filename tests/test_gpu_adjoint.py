@@ -7,8 +7,9 @@ inputs; at sizes the oracle cannot follow, the inner-product identities
 of the FP64 forward path.
 
 Tolerances (normwise: max |gpu - oracle| / max |oracle|): 1e-12 for F64
-plans.  F32 plans: the spread sums FP32 products into FP32 (shared-memory
-and global atomics, order not fixed), TOL32_SPREAD; the transposed
+plans.  F32 plans: the spread computes FP32 contributions, sums each work
+item's exactly in two-word fixed point and adds the items with FP32 atomics
+(order not fixed), TOL32_SPREAD; the transposed
 transform has the forward transform's ~log2(N^3) rounding steps,
 TOL32_FFT; the position gradient contracts second-derivative weights that
 sum to zero against FP32 coefficients (cancellation on top of the forward
