@@ -778,6 +778,14 @@ def run_band(B, wl, F, x, xs, device, steps, sample_t, full_sampled):
             "e2e": run_e2e(B, wl, F, xs, device, steps=24, band=K)}
 
 
+def e2e_h2d_bytes(N: int, P: int, band: int = 0) -> int:
+    """Host-to-device bytes of one end-to-end step: the complex64 half spectrum [3][N][N][N/2+1] (with a band K,
+    only the box kx, ky in [0, K] and [N - K, N), kz in [0, K] that bspline_run_host copies) and the FP64
+    positions [P][3]."""
+    modes = 3 * (2 * band + 1) ** 2 * (band + 1) if band else 3 * N * N * (N // 2 + 1)
+    return modes * 8 + P * 3 * 8
+
+
 def run_e2e(B, wl, F, xs, device, steps, band=0):
     """Same metric through the host-buffer API: every step copies u_hat and the positions from pinned
     host memory to the device and u and grad u back, all inside the timed region.  Steps alternate
@@ -818,7 +826,7 @@ def run_e2e(B, wl, F, xs, device, steps, band=0):
     t = statistics.median(seqs)
     for p in plans:
         p.close()
-    h2d = (3 * (2 * band + 1) ** 2 * (band + 1) if band else uh.numel()) * 8 + xh.numel() * 8
+    h2d = e2e_h2d_bytes(N, P, band)
     d2h = outs[0][0].numel() * 4 + outs[0][1].numel() * 4
     del uh, xh, outs
     torch.cuda.empty_cache()

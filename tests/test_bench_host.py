@@ -40,3 +40,17 @@ def test_scan_bytes_follow_the_brick_grid():
     # order 8: 16 x 8 x 16
     nb8 = 32 * 64 * 32
     assert bench.algorithmic_bytes("scan", 512, 0, "f32", 8) == 16 * (nb8 + 1)
+
+
+def test_e2e_host_to_device_bytes_full_and_band_box():
+    # the full half spectrum, or only the modes of the band box (every signed |kx|, |ky| <= K, 0 <= kz <= K),
+    # counted from a mask over the half spectrum's index grid; 8 bytes a complex64 mode, 24 a position
+    import numpy as np
+    for N, K, P in ((16, 5, 7), (48, 16, 100), (64, 21, 1), (32, 0, 3)):
+        idx = np.arange(N)
+        k = np.abs(np.where(idx <= N // 2, idx, idx - N))
+        kz = np.arange(N // 2 + 1)
+        inside = (k[:, None, None] <= K) & (k[None, :, None] <= K) & (kz[None, None, :] <= K)
+        modes = 3 * (int(inside.sum()) if K else N * N * (N // 2 + 1))
+        assert bench.e2e_h2d_bytes(N, P, K) == modes * 8 + P * 24
+    assert bench.e2e_h2d_bytes(512, 1 << 24) == 3 * 512 * 512 * 257 * 8 + (1 << 24) * 24
